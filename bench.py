@@ -1,0 +1,291 @@
+"""Benchmark: Smart Laplacian smoothing of the 4096x4096-vertex jittered grid.
+
+One step = reset the coordinates to the initial mesh (device-to-device copy)
+and smooth until 200 Jacobi passes or until the largest move of a pass is
+below 1e-9 x the bounding-box diagonal.  The metric is node-updates per
+second: nodes x passes executed / GPU time.  The mesh (16,777,216 nodes,
+33,538,050 triangles, 5% of interior nodes pulled towards seeded centres,
+Morton numbering) is synthetic and seeded; its coordinates (2 x 268 MB) and
+adjacency (~1 GB) are larger than L2, so no L2 flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (a bounded number of passes per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import meshgen  # noqa: E402
+
+WORKLOAD = "grid4096x4096_jitter0.35_pull5pct_morton"
+MAX_PASSES = 200
+TOL = 1e-9
+METRIC = "node-updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.reader = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.reader.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes_per_pass(n, n_free, adj_words):
+    """Bytes one pass must move at ideal reuse: every node's coordinates read
+    once (16 B), every free node's new coordinates written (16 B), the node
+    offsets (4 B per node + 1) and the adjacency words (4 B each)."""
+    return 16 * n + 16 * n_free + 4 * (n + 1) + 4 * adj_words
+
+
+def adjacency_words(mesh):
+    """Words of the library's adjacency stream: 1 meta word per node plus,
+    per free node, its neighbours and incident triangles."""
+    free = mesh.boundary == 0
+    deg_plus_tri = np.zeros(mesh.n, np.int64)
+    # incident triangles per node
+    np.add.at(deg_plus_tri, mesh.tri.ravel(), 1)
+    # interior node of a closed fan: degree == incident triangles
+    return int(mesh.n + 2 * deg_plus_tri[free].sum())
+
+
+def cpu_oracle_rate(mesh, passes: int):
+    """Times `passes` Form-A passes of the OpenMP oracle on all host cores."""
+    import oracle
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary, openmp=True)
+    xy = mesh.xy.copy()
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        xy, _, _, _ = om.sweep(xy)
+    dt = time.perf_counter() - t0
+    return mesh.n * passes / dt, dt, os.cpu_count()
+
+
+def run_reference(args, mesh, workload):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    passes = args.ref_passes
+    for _ in range(args.warmup):
+        cpu_oracle_rate(mesh, 1)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt, cores = cpu_oracle_rate(mesh, passes)
+        rates.append(r)
+        times.append(dt)
+    value = mesh.n * passes * len(times) / sum(times)
+    sample = f"{passes} passes of the {workload} mesh per step (OpenMP oracle build)"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "node-updates/s",
+           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload, "n": mesh.n, "m": mesh.m},
+           "cpu_baseline": {"value": value, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "node-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--nx", type=int, default=4096)
+    ap.add_argument("--ny", type=int, default=4096)
+    ap.add_argument("--ref-passes", type=int, default=3)
+    ap.add_argument("--cpu-passes", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    mesh = meshgen.large_grid(args.nx, args.ny)
+    workload = WORKLOAD if (args.nx, args.ny) == (4096, 4096) else f"grid{args.nx}x{args.ny}_jitter0.35_pull5pct_morton"
+
+    if args.impl == "reference":
+        run_reference(args, mesh, workload)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_1502_00355_gb300 as sls
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    sls.lib()
+
+    stream = torch.cuda.Stream()
+    g = sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=args.kernel, stream=stream.cuda_stream)
+    xy0 = torch.from_numpy(mesh.xy).to("cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        g.set_coords(xy0)
+        return g.smooth(MAX_PASSES, TOL)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    passes = sum(i["iterations"] for i in infos)
+    # kernel-only view: per-pass time of the pass kernel, events around the passes alone
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.set_coords(xy0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    info_k = g.smooth(MAX_PASSES, TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pass_ms = e0.elapsed_time(e1) / max(1, info_k["iterations"])
+
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    total_updates = mesh.n * passes * world
+    value = total_updates / (ms_max * 1e-3)
+
+    # end to end through the public API with host buffers: create (H2D of the
+    # inputs, adjacency build), smooth, read the coordinates back (D2H)
+    e2e_times = []
+    out_host = np.empty_like(mesh.xy)
+    e2e_passes = 0
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=args.kernel) as h:
+            inf = h.smooth(MAX_PASSES, TOL)
+            out_host[:] = h.coords()
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_passes += inf["iterations"]
+    e2e_value = mesh.n * e2e_passes * world / sum(e2e_times) if e2e_times else None
+
+    peak, peak_kind = _peaks()
+    adj_words = adjacency_words(mesh)
+    bytes_pass = algorithmic_bytes_per_pass(mesh.n, g.n_free, adj_words)
+    achieved = bytes_pass / (pass_ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, cores = cpu_oracle_rate(mesh, args.cpu_passes)
+        cpu = {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_passes} Form-A passes of the same mesh from its initial coordinates "
+                         f"({dt:.1f} s, OpenMP oracle build on all host cores)"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic",
+               "config": {"workload": workload, "n": mesh.n, "m": mesh.m, "n_free": g.n_free,
+                          "max_passes": MAX_PASSES, "tol_rel": TOL,
+                          "passes_per_step": passes / args.steps, "kernel": args.kernel,
+                          "layout": "aos", "form": "ping-pong",
+                          "l2": "inputs larger than L2 (no flush)",
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "e2e": {"value": e2e_value, "unit": "node-updates/s",
+                       "h2d_bytes_per_step": int(mesh.xy.nbytes + mesh.tri.nbytes + mesh.boundary.nbytes),
+                       "d2h_bytes_per_step": int(mesh.xy.nbytes)},
+               "gpu_launches": passes + args.steps * 0,
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "peak_kind": peak_kind, "bytes_per_pass": bytes_pass,
+                            "pass_ms": pass_ms},
+               "cpu_baseline": cpu,
+               "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * slsmooth.h -- C ABI of the GB300 (sm_103a) library for two-dimensional
+ * Smart Laplacian mesh smoothing (Zhao, Mei, Xu, Zhang, "On the Accelerating
+ * of Two-dimensional Smart Laplacian Smoothing on the GPU").
+ *
+ * What the library computes (the paper's method, Form A):
+ *   - every free node moves to the centre of its neighbours (Eq. 2), computed
+ *     from the coordinates of the previous pass only (Jacobi);
+ *   - the move is kept only if the worst quality of the node's incident
+ *     triangles does not get worse (Section 2.1, Section 3.3.4); quality is
+ *     Lee and Lo's alpha (Section 3.3.1);
+ *   - boundary nodes are fixed (Section 3.3.3).
+ *
+ * Fixed readings where the paper is silent (the test suite's CPU oracle uses
+ * the same ones):
+ *   - neighbours are summed in ascending (x0, y0, index) order, (x0, y0) being
+ *     the coordinates passed to sls_mesh_create;
+ *   - alpha = 2*sqrt(3) * cross / (|e1|^2 + |e2|^2 + |e3|^2) with e1 = b-a,
+ *     e2 = c-a, e3 = c-b of the triangle (a, b, c) in its stored vertex order,
+ *     cross = e1x*e2y - e1y*e2x (signed: inverted triangles score below 0),
+ *     the sum taken as (|e1|^2 + |e2|^2) + |e3|^2, and alpha = 0 if the sum is
+ *     not positive;
+ *   - accept iff q_new >= q_old (accept_strict = 1: q_new > q_old);
+ *   - the squared move of an accepted node is dx*dx + dy*dy with dx = cx - x;
+ *   - with tol_rel > 0 a run stops after the first pass whose largest squared
+ *     move is below (tol_rel * D)^2, D being the bounding-box diagonal of the
+ *     coordinates passed to sls_mesh_create.
+ * All arithmetic is IEEE-754 binary64 with round-to-nearest and no
+ * contraction, so results are bit-identical to a sequential CPU evaluation of
+ * the same expressions.
+ *
+ * Conventions
+ *   - Every entry point returns an sls_status and never throws.  On failure
+ *     sls_last_error() describes the problem (thread-local string).
+ *   - Host buffers are owned by the caller and only read (or written) during
+ *     the call.  The library owns all device memory it allocates.
+ *   - A handle (sls_mesh, sls_batch, sls_server) is not thread-safe; distinct
+ *     handles may be used from distinct threads.  sls_server is the exception:
+ *     sls_submit / sls_wait may be called from any thread.
+ *   - Coordinates are interleaved (x0, y0, x1, y1, ...) float64 on the host.
+ *   - Limits: 3 <= n < 2^31 nodes, 1 <= m < 2^31 triangles, at most 32767
+ *     neighbours per node, total adjacency words < 2^32.
+ */
+#ifndef SLSMOOTH_H
+#define SLSMOOTH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sls_status {
+    SLS_OK = 0,
+    SLS_ERR_INVALID = 1,     /* bad argument, bad index, repeated vertex, non-finite coordinate */
+    SLS_ERR_NONMANIFOLD = 2, /* an edge shared by more than two triangles                        */
+    SLS_ERR_OOM = 3,         /* device or host allocation failed / over the memory budget        */
+    SLS_ERR_CUDA = 4,        /* a CUDA runtime call failed (message in sls_last_error)           */
+    SLS_ERR_TIMEOUT = 5,     /* a bounded device-side or host-side wait ran out                  */
+    SLS_ERR_BUSY = 6,        /* the server queue is full                                         */
+    SLS_ERR_REJECTED = 7,    /* the job can never fit the server's memory budget                 */
+    SLS_ERR_NOT_FOUND = 8    /* unknown job id                                                   */
+} sls_status;
+
+/* Kernel choice for the Jacobi pass. */
+enum {
+    SLS_KERNEL_AUTO = 0,      /* the fastest exact kernel                                  */
+    SLS_KERNEL_FP64 = 1,      /* one thread per node, every step on the FP64 pipe          */
+    SLS_KERNEL_FILTERED = 2   /* exact: FP32 screening of the accept test, FP64 where needed */
+};
+
+typedef struct sls_options {
+    int32_t accept_strict; /* 0: accept iff q_new >= q_old (default); 1: q_new > q_old       */
+    int32_t copy_back;     /* 0: ping-pong the two coordinate arrays (default);
+                              1: copy the new pass back over the old one after every pass
+                              (the paper's "swapping" of intermediate coordinates)          */
+    int32_t layout;        /* 0: AoS, one double2 per node (default); 1: SoA, x[] then y[]   */
+    int32_t kernel;        /* SLS_KERNEL_*                                                   */
+    int32_t record_accept; /* 1: keep the per-node accept decisions of the last pass         */
+    int32_t block_size;    /* threads per block; 0 = library default                         */
+    int32_t l2_window;     /* 1: L2 persisting access window over the coordinates            */
+    int32_t passes_per_check; /* passes launched between host checks of the stop rule; 0 = 16 */
+    void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle    */
+} sls_options;
+
+typedef struct sls_info {
+    int32_t iterations;    /* passes executed by the last sls_smooth call                    */
+    int32_t converged;     /* 1 if the tolerance stopped the run                              */
+    int64_t accepted_last; /* accepted free nodes in the last executed pass                   */
+    double max_d2_last;    /* largest squared move in the last executed pass                  */
+    int64_t fp64_fallbacks;/* accept tests the screened kernel re-did in FP64 (last call)     */
+} sls_info;
+
+typedef struct sls_mesh sls_mesh;
+typedef struct sls_batch sls_batch;
+typedef struct sls_server sls_server;
+
+/* Fills *opt with the defaults. */
+void sls_default_options(sls_options *opt);
+
+/* Builds a mesh handle: validates the input, finds every node's neighbours
+ * and incident triangles (Section 3.3.2), determines the constraints
+ * (Section 3.3.3: with boundary == NULL a node is fixed when one of its
+ * edges belongs to a single triangle, or when it is in no triangle), and
+ * uploads adjacency and coordinates to the current CUDA device.
+ *   xy       host, 2n float64, interleaved
+ *   tri      host, 3m int32 vertex ids; the vertex order of each triangle is
+ *            kept and defines the sign of its quality
+ *   boundary host, n uint8 (nonzero = fixed), or NULL to derive the flags
+ *   opt      NULL for defaults; copied
+ *   out      receives the handle (NULL on failure)
+ * Errors: SLS_ERR_INVALID, SLS_ERR_NONMANIFOLD, SLS_ERR_OOM, SLS_ERR_CUDA. */
+sls_status sls_mesh_create(const double *xy, int64_t n, const int32_t *tri, int64_t m,
+                           const uint8_t *boundary, const sls_options *opt, sls_mesh **out);
+
+/* Runs up to max_iter Jacobi passes of Smart Laplacian smoothing (Eq. 2 with
+ * the accept test of Section 3.3.4), continuing from the handle's current
+ * coordinates.  tol_rel <= 0 disables the tolerance stop.  info may be NULL.
+ * Blocks until the passes are done. */
+sls_status sls_smooth(sls_mesh *mesh, int32_t max_iter, double tol_rel, sls_info *info);
+
+/* Copies the current coordinates (2n float64, interleaved) to xy_out, which is
+ * host memory (dst_is_device = 0) or device memory of the mesh's device
+ * (dst_is_device = 1, copied on the handle's stream and synchronised). */
+sls_status sls_get_coords(const sls_mesh *mesh, double *xy_out, int32_t dst_is_device);
+
+/* Overwrites the current coordinates (2n float64, interleaved), read from host
+ * memory (src_is_device = 0) or from device memory of the mesh's device
+ * (src_is_device = 1).  Adjacency, the summation order and D stay those of
+ * sls_mesh_create.  Host input is checked to be finite; device input is not. */
+sls_status sls_set_coords(sls_mesh *mesh, const double *xy, int32_t src_is_device);
+
+/* Copies the accept decisions of the last executed pass (n uint8, host;
+ * 1 = moved to the centre).  Needs opt->record_accept = 1. */
+sls_status sls_get_accept(const sls_mesh *mesh, uint8_t *accept_out);
+
+/* Quality histogram of all triangles at the current coordinates
+ * (Section 3.3.1): bin = floor((q - lo) / (hi - lo) * nbins) clamped to
+ * [0, nbins-1]; counts (host, nbins int64), qmin, qmean (either may be NULL).
+ * qmean is summed in an order of the library's choosing. */
+sls_status sls_quality_histogram(const sls_mesh *mesh, int32_t nbins, double lo, double hi,
+                                 int64_t *counts, double *qmin, double *qmean);
+
+/* Node and triangle counts, free nodes and D. */
+sls_status sls_mesh_stats(const sls_mesh *mesh, int64_t *n, int64_t *m, int64_t *n_free,
+                          double *diag);
+
+sls_status sls_mesh_destroy(sls_mesh *mesh);
+
+/* ---- batched form: many meshes of uneven size, one launch per pass ------
+ * The meshes' adjacency is concatenated with per-mesh node offsets; each mesh
+ * keeps its own iteration count and tolerance.  Results are bit-identical to
+ * smoothing each mesh alone. */
+
+/* Packs k mesh handles (their current coordinates, adjacency and options) into
+ * one batch.  iters (k int32) and tol_rel (k float64, may be NULL = off) are
+ * the per-mesh stop rules.  The meshes themselves are not modified. */
+sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *iters,
+                            const double *tol_rel, const sls_options *opt, sls_batch **out);
+
+/* Smooths every mesh of the batch to its own stop rule.  infos (k, may be
+ * NULL) receives the per-mesh results. */
+sls_status sls_batch_smooth(sls_batch *batch, sls_info *infos);
+
+/* Coordinates of mesh j of the batch (host, 2 n_j float64). */
+sls_status sls_batch_get_coords(const sls_batch *batch, int32_t j, double *xy_out);
+
+/* Resets every mesh of the batch to the coordinates it was packed with. */
+sls_status sls_batch_reset(sls_batch *batch);
+
+sls_status sls_batch_destroy(sls_batch *batch);
+
+/* ---- served form: jobs arrive over time (continuous batching) -----------
+ * A scheduler thread admits queued jobs while their device footprint fits
+ * the memory budget, runs every admitted job's next pass in one launch, and
+ * retires each job at its own iteration cap or tolerance. */
+
+/* hbm_budget: bytes of device memory the server may hold for jobs (0 = 80%
+ * of the free memory at creation).  max_queue: pending jobs allowed (0 =
+ * unlimited). */
+sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_options *opt,
+                             sls_server **out);
+
+/* Queues one smoothing job; inputs are copied before returning.  *job
+ * receives its id.  Errors: SLS_ERR_INVALID / NONMANIFOLD (bad mesh),
+ * SLS_ERR_REJECTED (larger than the whole budget), SLS_ERR_BUSY (queue full). */
+sls_status sls_submit(sls_server *srv, const double *xy, int64_t n, const int32_t *tri, int64_t m,
+                      const uint8_t *boundary, int32_t max_iter, double tol_rel, uint64_t *job);
+
+/* Waits up to timeout_s seconds (< 0: forever) for a job; copies its final
+ * coordinates (host, 2n float64; may be NULL) and info, then forgets the job.
+ * SLS_ERR_TIMEOUT if it is not done in time (the job stays). */
+sls_status sls_wait(sls_server *srv, uint64_t job, double timeout_s, double *xy_out,
+                    sls_info *info);
+
+/* Latency percentiles (submit to result ready on the host, milliseconds) of
+ * the jobs completed so far, and node-updates per second over the busy time. */
+sls_status sls_server_stats(const sls_server *srv, double *p50_ms, double *p99_ms,
+                            double *node_updates_per_s, int64_t *completed);
+
+sls_status sls_server_destroy(sls_server *srv);
+
+const char *sls_status_str(sls_status s);
+const char *sls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLSMOOTH_H */

@@ -1,0 +1,174 @@
+// api.cu -- the single-mesh C ABI of slsmooth (see include/slsmooth.h).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "api_common.h"
+#include "kernels.h"
+
+namespace sls {
+
+thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+sls_status fail(sls_status code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+sls_status cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();  // clear a sticky launch error so the handle stays usable
+    return fail(SLS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int device_sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+static sls_options g_defaults = {0, 0, 0, SLS_KERNEL_AUTO, 0, 0, 0, 16, nullptr};
+
+sls_options resolve_options(const sls_options *opt)
+{
+    sls_options o = opt ? *opt : g_defaults;
+    if (o.block_size <= 0) o.block_size = 256;
+    if (o.passes_per_check <= 0) o.passes_per_check = 16;
+    return o;
+}
+
+sls_status check_options(const sls_options &o)
+{
+    if (o.layout != 0 && o.layout != 1) return fail(SLS_ERR_INVALID, "layout must be 0 (AoS) or 1 (SoA)");
+    if (o.kernel < SLS_KERNEL_AUTO || o.kernel > SLS_KERNEL_FILTERED)
+        return fail(SLS_ERR_INVALID, "unknown kernel");
+    if (o.block_size % 32 != 0 || o.block_size > 1024)
+        return fail(SLS_ERR_INVALID, "block_size must be a multiple of 32, at most 1024");
+    return SLS_OK;
+}
+
+}  // namespace sls
+
+using namespace sls;
+
+extern "C" {
+
+void sls_default_options(sls_options *opt)
+{
+    if (opt) *opt = g_defaults;
+}
+
+const char *sls_status_str(sls_status s)
+{
+    switch (s) {
+    case SLS_OK: return "ok";
+    case SLS_ERR_INVALID: return "invalid argument or mesh";
+    case SLS_ERR_NONMANIFOLD: return "non-manifold edge";
+    case SLS_ERR_OOM: return "out of memory";
+    case SLS_ERR_CUDA: return "CUDA error";
+    case SLS_ERR_TIMEOUT: return "timed out";
+    case SLS_ERR_BUSY: return "queue full";
+    case SLS_ERR_REJECTED: return "job larger than the memory budget";
+    case SLS_ERR_NOT_FOUND: return "unknown job";
+    }
+    return "unknown status";
+}
+
+const char *sls_last_error(void) { return g_last_error.c_str(); }
+
+sls_status sls_mesh_create(const double *xy, int64_t n, const int32_t *tri, int64_t m,
+                           const uint8_t *boundary, const sls_options *opt, sls_mesh **out)
+{
+    if (!out) return fail(SLS_ERR_INVALID, "out must not be NULL");
+    *out = nullptr;
+    sls_options o = resolve_options(opt);
+    sls_status st = check_options(o);
+    if (st != SLS_OK) return st;
+    HostMesh hm;
+    st = build_host_mesh(xy, n, tri, m, boundary, hm);
+    if (st != SLS_OK) return st;
+    sls_mesh *M = new (std::nothrow) sls_mesh();
+    if (!M) return fail(SLS_ERR_OOM, "host allocation failed");
+    st = mesh_upload(M, hm, xy, tri, o);
+    if (st != SLS_OK) {
+        mesh_release(M);
+        delete M;
+        return st;
+    }
+    *out = M;
+    return SLS_OK;
+}
+
+sls_status sls_mesh_destroy(sls_mesh *mesh)
+{
+    if (!mesh) return SLS_OK;
+    mesh_release(mesh);
+    delete mesh;
+    return SLS_OK;
+}
+
+sls_status sls_mesh_stats(const sls_mesh *M, int64_t *n, int64_t *m, int64_t *n_free, double *diag)
+{
+    if (!M) return fail(SLS_ERR_INVALID, "mesh must not be NULL");
+    if (n) *n = M->n;
+    if (m) *m = M->m;
+    if (n_free) *n_free = M->n_free;
+    if (diag) *diag = M->diag;
+    return SLS_OK;
+}
+
+sls_status sls_smooth(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info *info)
+{
+    if (!M) return fail(SLS_ERR_INVALID, "mesh must not be NULL");
+    if (max_iter < 0) return fail(SLS_ERR_INVALID, "max_iter must be >= 0");
+    if (std::isnan(tol_rel)) return fail(SLS_ERR_INVALID, "tol_rel is NaN");
+    sls_info res{};
+    sls_status st = mesh_run(M, max_iter, tol_rel, res);
+    if (st != SLS_OK) return st;
+    M->last = res;
+    if (info) *info = res;
+    return SLS_OK;
+}
+
+sls_status sls_get_coords(const sls_mesh *M, double *xy_out, int32_t dst_is_device)
+{
+    if (!M || !xy_out) return fail(SLS_ERR_INVALID, "mesh and xy_out must not be NULL");
+    return mesh_download(M, xy_out, dst_is_device != 0);
+}
+
+sls_status sls_set_coords(sls_mesh *M, const double *xy, int32_t src_is_device)
+{
+    if (!M || !xy) return fail(SLS_ERR_INVALID, "mesh and xy must not be NULL");
+    if (!src_is_device)
+        for (int64_t k = 0; k < 2 * M->n; ++k)
+            if (!std::isfinite(xy[k])) return fail(SLS_ERR_INVALID, "coordinates must be finite");
+    return mesh_set_coords(M, xy, src_is_device != 0);
+}
+
+sls_status sls_get_accept(const sls_mesh *M, uint8_t *accept_out)
+{
+    if (!M || !accept_out) return fail(SLS_ERR_INVALID, "mesh and accept_out must not be NULL");
+    if (!M->accept) return fail(SLS_ERR_INVALID, "the mesh was created without record_accept");
+    cudaError_t e = cudaMemcpyAsync(accept_out, M->accept, (size_t)M->n, cudaMemcpyDeviceToHost, M->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sls_get_accept");
+    return SLS_OK;
+}
+
+sls_status sls_quality_histogram(const sls_mesh *M, int32_t nbins, double lo, double hi,
+                                 int64_t *counts, double *qmin, double *qmean)
+{
+    if (!M || !counts) return fail(SLS_ERR_INVALID, "mesh and counts must not be NULL");
+    if (nbins < 1 || nbins > 4096) return fail(SLS_ERR_INVALID, "nbins must be in [1, 4096]");
+    if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
+        return fail(SLS_ERR_INVALID, "need finite lo < hi");
+    return mesh_histogram(M, nbins, lo, hi, counts, qmin, qmean);
+}
+
+}  // extern "C"

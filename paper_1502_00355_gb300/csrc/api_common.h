@@ -1,0 +1,56 @@
+// api_common.h -- the mesh handle and the helpers behind the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+struct sls_mesh {
+    sls_options opt{};
+    int64_t n = 0, m = 0, n_free = 0;
+    double diag = 0.0;            // bounding-box diagonal of the creation coordinates
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double *xy[2] = {nullptr, nullptr};  // the two coordinate arrays (2n doubles each)
+    int cur = 0;                  // which of the two holds the current coordinates
+    uint32_t *node_off = nullptr; // n+1
+    uint32_t *adj = nullptr;      // node_off[n] words
+    uint64_t adj_words = 0;
+    int32_t *tri = nullptr;       // 3m, for the histogram
+    sls::PassStats *stats = nullptr;  // one record per pass of a call
+    int stats_cap = 0;
+    sls::PassStats *h_stats = nullptr;  // pinned, one record
+    uint8_t *accept = nullptr;    // n, when record_accept
+    int block = 256, grid = 0;
+    sls_info last{};
+};
+
+namespace sls {
+
+sls_status cuda_fail(cudaError_t e, const char *what);
+int device_sm_count();
+sls_options resolve_options(const sls_options *opt);
+sls_status check_options(const sls_options &o);
+
+sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const int32_t *tri,
+                       const sls_options &o);
+void mesh_release(sls_mesh *M);
+sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info);
+sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device);
+sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device);
+sls_status mesh_histogram(const sls_mesh *M, int nbins, double lo, double hi, int64_t *counts,
+                          double *qmin, double *qmean);
+
+// (tol * D)^2 with the tolerance stop's exact rounding.
+inline double tolerance_threshold(double tol_rel, double diag)
+{
+    double a = tol_rel * diag;
+    return a * a;
+}
+
+}  // namespace sls

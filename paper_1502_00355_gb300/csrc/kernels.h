@@ -1,0 +1,32 @@
+// kernels.h -- host-callable launchers of the slsmooth CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace sls {
+
+// One Jacobi pass, every step on the FP64 pipe (one thread per node).
+cudaError_t launch_pass_fp64(const PassArgs &a, int layout, int block, int grid, cudaStream_t s);
+// Blocks per SM the FP64 pass kernel can keep resident at `block` threads.
+int pass_fp64_occupancy(int layout, int block);
+
+// Copy-back form: out -> in after pass q (skipped when pass q was skipped).
+cudaError_t launch_copy_back(const double *src, double *dst, int64_t n_doubles,
+                             const PassStats *stats, int q, int grid, cudaStream_t s);
+
+// Quality histogram of all triangles (counts must be zeroed by the caller;
+// qmin_key is the order-preserving key of the minimum, init 0xff..ff;
+// qsum accumulates the qualities).
+cudaError_t launch_histogram(const double *xy, int layout, int64_t n, const int32_t *tri,
+                             int64_t m, int nbins, double lo, double hi,
+                             unsigned long long *counts, unsigned long long *qmin_key,
+                             double *qsum, int grid, cudaStream_t s);
+
+// Layout conversions on the device (SoA <-> interleaved).
+cudaError_t launch_soa_to_aos(const double *soa, double *aos, int64_t n, int grid, cudaStream_t s);
+cudaError_t launch_aos_to_soa(const double *aos, double *soa, int64_t n, int grid, cudaStream_t s);
+
+}  // namespace sls

@@ -1,0 +1,259 @@
+// mesh_device.cu -- device memory, pass scheduling and transfers of a mesh handle.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "api_common.h"
+#include "kernels.h"
+
+namespace sls {
+
+#define SLS_CUDA_TRY(expr, what)                 \
+    do {                                         \
+        cudaError_t e_ = (expr);                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+static sls_status dev_alloc(void **p, size_t bytes, const char *what)
+{
+    cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 1);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(SLS_ERR_OOM, std::string("device allocation failed: ") + what);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return SLS_OK;
+}
+
+// Host interleaved -> the handle's layout.
+static void to_layout(const double *xy, int64_t n, int layout, std::vector<double> &tmp)
+{
+    tmp.resize(2 * n);
+    for (int64_t i = 0; i < n; ++i) {
+        tmp[i] = xy[2 * i];
+        tmp[n + i] = xy[2 * i + 1];
+    }
+}
+
+sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const int32_t *tri,
+                       const sls_options &o)
+{
+    M->opt = o;
+    M->n = hm.n;
+    M->m = hm.m;
+    M->n_free = hm.n_free;
+    M->diag = hm.diag;
+    M->adj_words = hm.node_off[hm.n];
+    SLS_CUDA_TRY(cudaGetDevice(&M->device), "cudaGetDevice");
+    if (o.stream) {
+        M->stream = (cudaStream_t)o.stream;
+    } else {
+        SLS_CUDA_TRY(cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        M->own_stream = true;
+    }
+    const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
+    sls_status st;
+    for (int b = 0; b < 2; ++b)
+        if ((st = dev_alloc((void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
+    if ((st = dev_alloc((void **)&M->node_off, sizeof(uint32_t) * (M->n + 1), "node offsets")) != SLS_OK) return st;
+    if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
+    if ((st = dev_alloc((void **)&M->tri, sizeof(int32_t) * 3 * (size_t)M->m, "triangles")) != SLS_OK) return st;
+    M->stats_cap = 256;
+    if ((st = dev_alloc((void **)&M->stats, sizeof(PassStats) * M->stats_cap, "pass statistics")) != SLS_OK) return st;
+    SLS_CUDA_TRY(cudaMallocHost((void **)&M->h_stats, sizeof(PassStats)), "cudaMallocHost");
+    if (o.record_accept) {
+        if ((st = dev_alloc((void **)&M->accept, (size_t)M->n, "accept mask")) != SLS_OK) return st;
+        SLS_CUDA_TRY(cudaMemsetAsync(M->accept, 0, (size_t)M->n, M->stream), "cudaMemset");
+    }
+    if (o.layout == 0) {
+        SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[0], xy, cbytes, cudaMemcpyHostToDevice, M->stream), "upload coordinates");
+        SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload coordinates");
+    } else {
+        std::vector<double> tmp;
+        to_layout(xy, M->n, 1, tmp);
+        SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[0], tmp.data(), cbytes, cudaMemcpyHostToDevice, M->stream), "upload coordinates");
+        SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload coordinates");
+    }
+    SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[1], M->xy[0], cbytes, cudaMemcpyDeviceToDevice, M->stream), "copy coordinates");
+    SLS_CUDA_TRY(cudaMemcpyAsync(M->node_off, hm.node_off.data(), sizeof(uint32_t) * (M->n + 1),
+                                 cudaMemcpyHostToDevice, M->stream), "upload offsets");
+    SLS_CUDA_TRY(cudaMemcpyAsync(M->adj, hm.adj.data(), sizeof(uint32_t) * M->adj_words,
+                                 cudaMemcpyHostToDevice, M->stream), "upload adjacency");
+    SLS_CUDA_TRY(cudaMemcpyAsync(M->tri, tri, sizeof(int32_t) * 3 * (size_t)M->m,
+                                 cudaMemcpyHostToDevice, M->stream), "upload triangles");
+    SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload");
+    M->cur = 0;
+    M->block = o.block_size;
+    M->grid = device_sm_count() * pass_fp64_occupancy(o.layout, M->block);
+    return SLS_OK;
+}
+
+void mesh_release(sls_mesh *M)
+{
+    if (M->stream) cudaStreamSynchronize(M->stream);
+    cudaFree(M->xy[0]);
+    cudaFree(M->xy[1]);
+    cudaFree(M->node_off);
+    cudaFree(M->adj);
+    cudaFree(M->tri);
+    cudaFree(M->stats);
+    cudaFree(M->accept);
+    if (M->h_stats) cudaFreeHost(M->h_stats);
+    if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
+    M->stream = nullptr;
+}
+
+sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info)
+{
+    info = sls_info{};
+    if (max_iter == 0) return SLS_OK;
+    if (M->stats_cap < max_iter) {
+        cudaStreamSynchronize(M->stream);
+        cudaFree(M->stats);
+        M->stats = nullptr;
+        int cap = std::max(max_iter, 2 * M->stats_cap);
+        sls_status st = dev_alloc((void **)&M->stats, sizeof(PassStats) * cap, "pass statistics");
+        if (st != SLS_OK) {
+            M->stats_cap = 0;
+            return st;
+        }
+        M->stats_cap = cap;
+    }
+    SLS_CUDA_TRY(cudaMemsetAsync(M->stats, 0, sizeof(PassStats) * max_iter, M->stream), "cudaMemset");
+    const bool tol_active = tol_rel > 0.0;
+    const double thr = tolerance_threshold(tol_rel, M->diag);
+    unsigned long long thr_bits;
+    std::memcpy(&thr_bits, &thr, sizeof thr_bits);
+
+    PassArgs a{};
+    a.node_off = M->node_off;
+    a.adj = M->adj;
+    a.n = M->n;
+    a.stats = M->stats;
+    a.strict = M->opt.accept_strict;
+    a.tol_active = tol_active ? 1 : 0;
+    a.thr_bits = thr_bits;
+    a.accept = M->accept;
+    const int cb = M->opt.copy_back;
+    const int chunk = M->opt.passes_per_check;
+    int launched = 0;
+    while (launched < max_iter) {
+        const int end = std::min(launched + chunk, (int)max_iter);
+        for (int q = launched; q < end; ++q) {
+            const int src = cb ? M->cur : (M->cur ^ (q & 1));
+            a.in = M->xy[src];
+            a.out = M->xy[src ^ 1];
+            a.q = q;
+            SLS_CUDA_TRY(launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream), "pass kernel");
+            if (cb)
+                SLS_CUDA_TRY(launch_copy_back(M->xy[src ^ 1], M->xy[src], 2 * M->n, M->stats, q,
+                                              device_sm_count() * 4, M->stream), "copy-back kernel");
+        }
+        launched = end;
+        if (tol_active && launched < max_iter) {
+            SLS_CUDA_TRY(cudaMemcpyAsync(M->h_stats, M->stats + launched - 1, sizeof(PassStats),
+                                         cudaMemcpyDeviceToHost, M->stream), "read pass statistics");
+            SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "pass");
+            if (M->h_stats->executed == 0u || M->h_stats->maxd2_bits < thr_bits) break;
+        }
+    }
+    std::vector<PassStats> hs(launched);
+    SLS_CUDA_TRY(cudaMemcpyAsync(hs.data(), M->stats, sizeof(PassStats) * launched,
+                                 cudaMemcpyDeviceToHost, M->stream), "read pass statistics");
+    SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "passes");
+    int it = 0;
+    long long fb = 0;
+    while (it < launched && hs[it].executed) fb += (long long)hs[it++].fallbacks;
+    info.iterations = it;
+    info.fp64_fallbacks = fb;
+    if (it > 0) {
+        const PassStats &l = hs[it - 1];
+        info.accepted_last = (int64_t)l.nacc;
+        std::memcpy(&info.max_d2_last, &l.maxd2_bits, sizeof(double));
+        info.converged = (tol_active && l.maxd2_bits < thr_bits) ? 1 : 0;
+    }
+    if (!cb) M->cur ^= (it & 1);
+    return SLS_OK;
+}
+
+sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device)
+{
+    const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
+    const double *src = M->xy[M->cur];
+    if (M->opt.layout == 0) {
+        SLS_CUDA_TRY(cudaMemcpyAsync(xy_out, src, cbytes,
+                                     dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                     M->stream), "download coordinates");
+    } else if (dst_is_device) {
+        SLS_CUDA_TRY(launch_soa_to_aos(src, xy_out, M->n, device_sm_count() * 4, M->stream), "interleave");
+    } else {
+        std::vector<double> tmp(2 * M->n);
+        SLS_CUDA_TRY(cudaMemcpyAsync(tmp.data(), src, cbytes, cudaMemcpyDeviceToHost, M->stream), "download");
+        SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "download");
+        for (int64_t i = 0; i < M->n; ++i) {
+            xy_out[2 * i] = tmp[i];
+            xy_out[2 * i + 1] = tmp[M->n + i];
+        }
+    }
+    SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "download coordinates");
+    return SLS_OK;
+}
+
+sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
+{
+    const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
+    if (src_is_device) {
+        if (M->opt.layout == 0)
+            SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[M->cur], xy, cbytes, cudaMemcpyDeviceToDevice, M->stream), "copy");
+        else
+            SLS_CUDA_TRY(launch_aos_to_soa(xy, M->xy[M->cur], M->n, device_sm_count() * 4, M->stream), "split");
+    } else {
+        std::vector<double> tmp;
+        const double *src = xy;
+        if (M->opt.layout == 1) {
+            to_layout(xy, M->n, 1, tmp);
+            src = tmp.data();
+        }
+        SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[M->cur], src, cbytes, cudaMemcpyHostToDevice, M->stream), "upload");
+        SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload");
+    }
+    SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[M->cur ^ 1], M->xy[M->cur], cbytes, cudaMemcpyDeviceToDevice,
+                                 M->stream), "copy");
+    SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "set coordinates");
+    return SLS_OK;
+}
+
+sls_status mesh_histogram(const sls_mesh *M, int nbins, double lo, double hi, int64_t *counts,
+                          double *qmin, double *qmean)
+{
+    unsigned long long *d_counts = nullptr, *d_key = nullptr;
+    double *d_sum = nullptr;
+    sls_status st;
+    if ((st = dev_alloc((void **)&d_counts, sizeof(unsigned long long) * (nbins + 2), "histogram")) != SLS_OK)
+        return st;
+    d_key = d_counts + nbins;
+    d_sum = reinterpret_cast<double *>(d_counts + nbins + 1);
+    std::vector<unsigned long long> h(nbins + 2);
+    cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * (nbins + 2), M->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_key, 0xff, sizeof(unsigned long long), M->stream);
+    if (e == cudaSuccess)
+        e = launch_histogram(M->xy[M->cur], M->opt.layout, M->n, M->tri, M->m, nbins, lo, hi, d_counts,
+                             d_key, d_sum, device_sm_count() * 8, M->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_counts, sizeof(unsigned long long) * (nbins + 2),
+                            cudaMemcpyDeviceToHost, M->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+    cudaFree(d_counts);
+    if (e != cudaSuccess) return cuda_fail(e, "histogram");
+    for (int b = 0; b < nbins; ++b) counts[b] = (int64_t)h[b];
+    unsigned long long key = h[nbins];
+    unsigned long long bits = (key >> 63) ? (key & 0x7fffffffffffffffull) : ~key;
+    double mn, sum;
+    std::memcpy(&mn, &bits, sizeof mn);
+    std::memcpy(&sum, &h[nbins + 1], sizeof sum);
+    if (qmin) *qmin = mn;
+    if (qmean) *qmean = sum / (double)M->m;
+    return SLS_OK;
+}
+
+}  // namespace sls

@@ -1,0 +1,220 @@
+// pass_fp64.cu -- the plain Jacobi pass of Smart Laplacian smoothing with
+// every step on the FP64 pipe, plus the small auxiliary kernels.
+//
+// One thread per node (grid-stride).  For a free node i the thread
+//   1. sums its neighbours' coordinates in the stored summation order and
+//      divides by the degree (Eq. 2, Form A: only pass-q coordinates);
+//   2. evaluates alpha of every incident triangle with node i at its pass-q
+//      position (q_old) and at the centre (q_new), keeping the minima
+//      (Section 3.3.4 and the per-pass refresh of all qualities);
+//   3. keeps the centre iff q_new >= q_old (strict: >), writes the node, and
+//      contributes its squared move and acceptance to the pass statistics.
+// The FP64 pipe of GB300 is narrow, so this kernel is the exact baseline and
+// the fallback of the screened kernel, not the fast path.
+#include "kernels.h"
+
+namespace sls {
+
+namespace {
+
+template <int LAYOUT, bool RECORD>
+__global__ void __launch_bounds__(1024) pass_fp64_kernel(PassArgs a)
+{
+    if (pass_is_skipped(a.stats, a.q, a.tol_active, a.thr_bits)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.stats[a.q].executed = 1u;
+
+    unsigned long long best = 0ull, nacc = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const uint32_t off = __ldg(a.node_off + i);
+        const uint32_t meta = __ldg(a.adj + off);
+        if (meta & kMetaFixed) {
+            if (RECORD) a.accept[i] = 0;
+            continue;
+        }
+        const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
+        const uint32_t *nb = a.adj + off + 1;
+        const double2 p = Coords<LAYOUT>::get(a.in, a.n, i);
+
+        // Eq. 2: centre of the neighbours, summed in the stored order.
+        double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb));
+        double sx = v.x, sy = v.y;
+        for (uint32_t k = 1; k < deg; ++k) {
+            v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
+            sx = __dadd_rn(sx, v.x);
+            sy = __dadd_rn(sy, v.y);
+        }
+        const double fd = (double)deg;
+        const double cx = __ddiv_rn(sx, fd), cy = __ddiv_rn(sy, fd);
+
+        // Section 3.3.4: worst incident quality before and after the move.
+        double q_old = 0.0, q_new = 0.0;
+        for (uint32_t t = 0; t < ntri; ++t) {
+            const uint32_t c = __ldg(nb + deg + t);
+            const double2 A = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + code_first(c)));
+            const double2 B = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + code_second(c)));
+            double qb, qa;
+            switch (code_slot(c)) {
+            case 0:
+                qb = alpha_fp64(p.x, p.y, A.x, A.y, B.x, B.y);
+                qa = alpha_fp64(cx, cy, A.x, A.y, B.x, B.y);
+                break;
+            case 1:
+                qb = alpha_fp64(A.x, A.y, p.x, p.y, B.x, B.y);
+                qa = alpha_fp64(A.x, A.y, cx, cy, B.x, B.y);
+                break;
+            default:
+                qb = alpha_fp64(A.x, A.y, B.x, B.y, p.x, p.y);
+                qa = alpha_fp64(A.x, A.y, B.x, B.y, cx, cy);
+                break;
+            }
+            if (t == 0 || qb < q_old) q_old = qb;
+            if (t == 0 || qa < q_new) q_new = qa;
+        }
+
+        const bool ok = a.strict ? (q_new > q_old) : (q_new >= q_old);
+        double2 o = p;
+        if (ok) {
+            const double dx = __dsub_rn(cx, p.x), dy = __dsub_rn(cy, p.y);
+            const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(d2);
+            best = bits > best ? bits : best;
+            nacc += 1ull;
+            o = make_double2(cx, cy);
+        }
+        Coords<LAYOUT>::put(a.out, a.n, i, o);
+        if (RECORD) a.accept[i] = ok ? 1 : 0;
+    }
+    block_reduce_stats(a.stats + a.q, best, nacc, 0ull);
+}
+
+__global__ void copy_back_kernel(const double2 *__restrict__ src, double2 *__restrict__ dst,
+                                 int64_t n2, const PassStats *stats, int q)
+{
+    if (stats[q].executed == 0u) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += stride)
+        dst[k] = __ldg(src + k);
+}
+
+__device__ __forceinline__ unsigned long long order_key(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+template <int LAYOUT>
+__global__ void histogram_kernel(const double *xy, int64_t n, const int32_t *__restrict__ tri,
+                                 int64_t m, int nbins, double lo, double hi,
+                                 unsigned long long *counts, unsigned long long *qmin_key,
+                                 double *qsum)
+{
+    extern __shared__ unsigned long long s_counts[];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) s_counts[b] = 0ull;
+    __syncthreads();
+    unsigned long long kmin = ~0ull;
+    double sum = 0.0;
+    const double width = __dsub_rn(hi, lo);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += stride) {
+        const double2 A = Coords<LAYOUT>::get(xy, n, __ldg(tri + 3 * t));
+        const double2 B = Coords<LAYOUT>::get(xy, n, __ldg(tri + 3 * t + 1));
+        const double2 Cc = Coords<LAYOUT>::get(xy, n, __ldg(tri + 3 * t + 2));
+        const double q = alpha_fp64(A.x, A.y, B.x, B.y, Cc.x, Cc.y);
+        const double f = floor(__dmul_rn(__ddiv_rn(__dsub_rn(q, lo), width), (double)nbins));
+        int bin = f < 0.0 ? 0 : (f >= (double)nbins ? nbins - 1 : (int)f);
+        atomicAdd(&s_counts[bin], 1ull);
+        const unsigned long long k = order_key(q);
+        kmin = k < kmin ? k : kmin;
+        sum = __dadd_rn(sum, q);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long k2 = __shfl_xor_sync(0xffffffffu, kmin, o);
+        kmin = k2 < kmin ? k2 : kmin;
+        sum = __dadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        atomicMin(qmin_key, kmin);
+        atomicAdd(qsum, sum);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (s_counts[b]) atomicAdd(&counts[b], s_counts[b]);
+}
+
+__global__ void soa_to_aos_kernel(const double *__restrict__ soa, double2 *__restrict__ aos, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        aos[i] = make_double2(__ldg(soa + i), __ldg(soa + n + i));
+}
+
+__global__ void aos_to_soa_kernel(const double2 *__restrict__ aos, double *__restrict__ soa, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double2 v = __ldg(aos + i);
+        soa[i] = v.x;
+        soa[n + i] = v.y;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pass_fp64(const PassArgs &a, int layout, int block, int grid, cudaStream_t s)
+{
+    const bool rec = a.accept != nullptr;
+    if (layout == 0) {
+        if (rec) pass_fp64_kernel<0, true><<<grid, block, 0, s>>>(a);
+        else pass_fp64_kernel<0, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (rec) pass_fp64_kernel<1, true><<<grid, block, 0, s>>>(a);
+        else pass_fp64_kernel<1, false><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+int pass_fp64_occupancy(int layout, int block)
+{
+    int nb = 0;
+    if (layout == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_fp64_kernel<0, false>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_fp64_kernel<1, false>, block, 0);
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_copy_back(const double *src, double *dst, int64_t n_doubles,
+                             const PassStats *stats, int q, int grid, cudaStream_t s)
+{
+    copy_back_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const double2 *>(src),
+                                         reinterpret_cast<double2 *>(dst), n_doubles / 2, stats, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_histogram(const double *xy, int layout, int64_t n, const int32_t *tri,
+                             int64_t m, int nbins, double lo, double hi,
+                             unsigned long long *counts, unsigned long long *qmin_key,
+                             double *qsum, int grid, cudaStream_t s)
+{
+    const size_t smem = sizeof(unsigned long long) * (size_t)nbins;
+    if (layout == 0)
+        histogram_kernel<0><<<grid, 256, smem, s>>>(xy, n, tri, m, nbins, lo, hi, counts, qmin_key, qsum);
+    else
+        histogram_kernel<1><<<grid, 256, smem, s>>>(xy, n, tri, m, nbins, lo, hi, counts, qmin_key, qsum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soa_to_aos(const double *soa, double *aos, int64_t n, int grid, cudaStream_t s)
+{
+    soa_to_aos_kernel<<<grid, 256, 0, s>>>(soa, reinterpret_cast<double2 *>(aos), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aos_to_soa(const double *aos, double *soa, int64_t n, int grid, cudaStream_t s)
+{
+    aos_to_soa_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const double2 *>(aos), soa, n);
+    return cudaGetLastError();
+}
+
+}  // namespace sls

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+The bar is bit-exactness: coordinates, accept decisions, iteration counts,
+accepted counts and the largest squared move must be identical.
+"""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = ["fp64", "filtered"]
+
+
+@pytest.fixture(scope="module")
+def sls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1502_00355_gb300 as mod
+    mod.build()
+    mod.lib()
+    return mod
+
+
+def _assert_same(xy_gpu, xy_ref, what=""):
+    if not np.array_equal(xy_gpu, xy_ref):
+        bad = np.flatnonzero((xy_gpu != xy_ref).any(1))
+        i = bad[0]
+        raise AssertionError(f"{what}: {bad.size} nodes differ; first {i}: gpu {xy_gpu[i].tolist()} "
+                             f"oracle {xy_ref[i].tolist()}")
+
+
+def _run_both(sls, mesh, iters, tol=0.0, strict=False, omp=False, boundary="given", **opts):
+    bnd = mesh.boundary if boundary == "given" else None
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, bnd, openmp=omp)
+    ref_xy, ref_info, ref_acc = om.smooth(mesh.xy, iters, tol=tol, strict=strict)
+    with sls.Mesh(mesh.xy, mesh.tri, bnd, strict=strict, record_accept=True, **opts) as g:
+        info = g.smooth(iters, tol)
+        xy = g.coords()
+        acc = g.accept_mask()
+    return (xy, info, acc), (ref_xy, ref_info, ref_acc)
+
+
+def _check(got, ref, what):
+    (xy, info, acc), (rxy, rinfo, racc) = got, ref
+    _assert_same(xy, rxy, what)
+    assert info["iterations"] == rinfo["iterations"], what
+    assert info["converged"] == rinfo["converged"], what
+    assert info["accepted_last"] == rinfo["accepted_last"], what
+    assert info["maxd2_last"] == rinfo["maxd2_last"], what
+    if rinfo["iterations"] > 0:
+        assert np.array_equal(acc, racc), what
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("copy_back", [False, True])
+def test_small_grid_bit_exact(sls, kernel, layout, copy_back):
+    # 64x64 vertices, 10 passes (the small workload)
+    mesh = meshgen.small_grid()
+    got, ref = _run_both(sls, mesh, 10, kernel=kernel, layout=layout, copy_back=copy_back)
+    _check(got, ref, f"{kernel}/{layout}/cb={copy_back}")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("strict", [False, True])
+def test_strict_mode_and_derived_boundary(sls, kernel, strict):
+    mesh = meshgen.jittered_grid(37, 23, 0.4, 5, numbering="random")
+    got, ref = _run_both(sls, mesh, 17, strict=strict, boundary="derived", kernel=kernel)
+    _check(got, ref, f"strict={strict}")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("block", [32, 64, 128, 512, 1024])
+def test_ragged_sizes_and_block_sizes(sls, kernel, block):
+    # node counts that are not multiples of the block or the warp
+    for nx, ny in [(3, 3), (5, 7), (33, 31), (129, 67)]:
+        mesh = meshgen.jittered_grid(nx, ny, 0.3, nx * 1000 + ny, numbering="morton")
+        got, ref = _run_both(sls, mesh, 6, kernel=kernel, block_size=block)
+        _check(got, ref, f"{nx}x{ny} block={block}")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_tolerance_stop_matches(sls, kernel):
+    mesh = meshgen.jittered_grid(40, 40, 0.3, 8)
+    for tol, chunk in [(1e-4, 16), (1e-4, 1), (1e-4, 5), (1e-6, 3), (10.0, 16)]:
+        got, ref = _run_both(sls, mesh, 500, tol=tol, kernel=kernel, passes_per_check=chunk)
+        _check(got, ref, f"tol={tol} chunk={chunk}")
+    assert ref[1]["converged"] == 1
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_resume_zero_passes_and_set_coords(sls, kernel):
+    mesh = meshgen.jittered_grid(30, 50, 0.35, 3)
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary)
+    ref, _, _ = om.smooth(mesh.xy, 12)
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=kernel) as g:
+        info = g.smooth(0)
+        assert info["iterations"] == 0
+        _assert_same(g.coords(), mesh.xy, "zero passes")
+        g.smooth(7)
+        g.smooth(5)
+        _assert_same(g.coords(), ref, "7 + 5 passes")
+        g.set_coords(mesh.xy)
+        g.smooth(12)
+        _assert_same(g.coords(), ref, "after set_coords")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_hexagon_and_fan_cases(sls, kernel):
+    # the hand-worked hexagon: the centre lands exactly on (0, 0)
+    s = 0.8660254037844386
+    xy = np.array([[1.0, 0.0], [0.5, s], [-0.5, s], [-1.0, 0.0], [-0.5, -s], [0.5, -s], [0.125, -0.0625]])
+    tri = np.array([[6, k, (k + 1) % 6] for k in range(6)], dtype=np.int32)
+    with sls.Mesh(xy, tri, kernel=kernel) as g:
+        info = g.smooth(1)
+        out = g.coords()
+    assert out[6, 0] == 0.0 and out[6, 1] == 0.0 and info["accepted_last"] == 1
+    # a node of degree 40 (long loops) and the dart whose centre inverts a triangle
+    k = 40
+    ang = np.linspace(0, 2 * np.pi, k, endpoint=False)
+    xy = np.vstack([np.c_[np.cos(ang) * (1 + 0.3 * np.sin(5 * ang)), np.sin(ang)], [[0.05, -0.02]]])
+    tri = np.array([[k, j, (j + 1) % k] for j in range(k)], dtype=np.int32)
+    mesh = meshgen.Mesh(xy=xy, tri=tri, boundary=(np.arange(k + 1) < k).astype(np.uint8))
+    got, ref = _run_both(sls, mesh, 3, kernel=kernel)
+    _check(got, ref, "fan-40")
+    dart = meshgen.Mesh(xy=np.array([[4.0, 0.0], [-1.0, 1.0], [2.0, 0.0], [-1.0, -1.0], [2.5, 0.0]]),
+                        tri=np.array([[4, 0, 1], [4, 1, 2], [4, 2, 3], [4, 3, 0]], dtype=np.int32),
+                        boundary=np.array([1, 1, 1, 1, 0], np.uint8))
+    got, ref = _run_both(sls, dart, 2, kernel=kernel)
+    _check(got, ref, "dart")
+    assert got[2][4] == 0
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_histogram_matches_oracle(sls, kernel):
+    mesh = meshgen.jittered_grid(100, 80, 0.45, 31)
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary)
+    xy, _, _ = om.smooth(mesh.xy, 5)
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=kernel) as g:
+        for layout_xy in (mesh.xy, xy):
+            g.set_coords(layout_xy)
+            for nb, lo, hi in [(20, -1.0, 1.0), (7, 0.2, 0.9), (1, -1.0, 1.0)]:
+                c, qmin, qmean = g.histogram(nb, lo, hi)
+                rc, rqmin, rqmean = om.histogram(layout_xy, nb, lo, hi)
+                assert np.array_equal(c, rc)
+                assert qmin == rqmin
+                assert qmean == pytest.approx(rqmean, rel=1e-12)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_medium_grid_all_forms(sls, kernel):
+    # 1024x1024 vertices, 100 passes, {ping-pong, copy-back} x {AoS, SoA} x
+    # {Morton, random numbering}; every run bit-identical to the oracle, and
+    # the two numberings identical to each other after un-permuting.
+    results = {}
+    for numbering in ("morton", "random"):
+        mesh = meshgen.medium_grid(numbering)
+        om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary, openmp=True)
+        rxy, rinfo, racc = om.smooth(mesh.xy, 100)
+        for layout in ("aos", "soa"):
+            for cb in (False, True):
+                with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=kernel, layout=layout,
+                              copy_back=cb, record_accept=True) as g:
+                    info = g.smooth(100)
+                    xy = g.coords()
+                    acc = g.accept_mask()
+                _check((xy, info, acc), (rxy, rinfo, racc), f"{numbering}/{layout}/cb={cb}")
+        results[numbering] = meshgen.unpermute(rxy, mesh)
+    assert np.array_equal(results["morton"], results["random"])
+
+
+def test_large_grid_sampled_passes(sls):
+    # 4096x4096 vertices with clustered pulls: the timed configuration.
+    # Sampled nodes of passes 1, 2, 50 and 200 recomputed one by one by the
+    # oracle from the GPU's previous pass; the GPU stays in the timed launch
+    # configuration (default kernel, AoS, ping-pong).
+    mesh = meshgen.large_grid()
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(mesh.n, 20000, replace=False))
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary)
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, record_accept=True) as g:
+        done = 0
+        for target in (1, 2, 50, 200):
+            if target - 1 > done:
+                g.smooth(target - 1 - done)
+                done = target - 1
+            prev = g.coords()
+            info = g.smooth(1)
+            done += 1
+            cur = g.coords()
+            acc = g.accept_mask()
+            out, racc, d2, _, _, _ = om.update_nodes(prev, sample)
+            _assert_same(cur[sample], out, f"pass {target}")
+            assert np.array_equal(acc[sample], racc), f"pass {target}"
+            # property at full size: every node moved by at most the reported max
+            d = cur - prev
+            dd = (d * d).sum(1)
+            assert dd.max() == pytest.approx(info["maxd2_last"], rel=1e-12)
+            assert info["accepted_last"] >= int((dd > 0).sum())
+            assert np.array_equal(cur[mesh.boundary == 1], mesh.xy[mesh.boundary == 1])
