@@ -27,6 +27,7 @@ struct sls_mesh {
     sls::PassStats *h_stats = nullptr;  // pinned, one record
     uint8_t *accept = nullptr;    // n, when record_accept
     int block = 256, grid = 0;
+    bool screened = true;         // screened kernel (else the plain FP64 kernel)
     sls_info last{};
 };
 

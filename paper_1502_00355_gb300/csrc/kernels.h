@@ -13,6 +13,11 @@ cudaError_t launch_pass_fp64(const PassArgs &a, int layout, int block, int grid,
 // Blocks per SM the FP64 pass kernel can keep resident at `block` threads.
 int pass_fp64_occupancy(int layout, int block);
 
+// One Jacobi pass, screened: integer-pipe sums, FP32 screening of the accept
+// test, FP64 only where the screen cannot decide (bit-identical results).
+cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int grid, cudaStream_t s);
+int pass_screened_occupancy(int layout, int block);
+
 // Copy-back form: out -> in after pass q (skipped when pass q was skipped).
 cudaError_t launch_copy_back(const double *src, double *dst, int64_t n_doubles,
                              const PassStats *stats, int q, int grid, cudaStream_t s);

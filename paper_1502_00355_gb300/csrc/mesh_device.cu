@@ -84,7 +84,10 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload");
     M->cur = 0;
     M->block = o.block_size;
-    M->grid = device_sm_count() * pass_fp64_occupancy(o.layout, M->block);
+    M->screened = o.kernel != SLS_KERNEL_FP64;
+    if (M->screened && (M->block < 64 || M->block > 512)) M->block = 256;
+    M->grid = device_sm_count() * (M->screened ? pass_screened_occupancy(o.layout, M->block)
+                                               : pass_fp64_occupancy(o.layout, M->block));
     return SLS_OK;
 }
 
@@ -144,7 +147,9 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
             a.in = M->xy[src];
             a.out = M->xy[src ^ 1];
             a.q = q;
-            SLS_CUDA_TRY(launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream), "pass kernel");
+            SLS_CUDA_TRY(M->screened ? launch_pass_screened(a, M->opt.layout, M->block, M->grid, M->stream)
+                                     : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream),
+                         "pass kernel");
             if (cb)
                 SLS_CUDA_TRY(launch_copy_back(M->xy[src ^ 1], M->xy[src], 2 * M->n, M->stats, q,
                                               device_sm_count() * 4, M->stream), "copy-back kernel");

@@ -1,0 +1,97 @@
+// node_exact.cuh -- the FP64 node update (Eq. 2 with the accept test of
+// Section 3.3.4), used whole by the plain FP64 kernel and, restricted to the
+// candidate triangles, by the screened kernel for nodes its FP32 screen could
+// not decide.
+#pragma once
+
+#include "device.cuh"
+
+namespace sls {
+
+// Flags of a deferred node (screened kernel -> exact path).
+constexpr uint32_t kHasCentre = 1u;   // cx, cy hold the node's centre
+constexpr uint32_t kSingleOld = 2u;   // only triangle t_old can attain q_old
+constexpr uint32_t kSingleNew = 4u;   // only triangle t_new can attain q_new
+
+struct Deferred {
+    int32_t node;
+    uint32_t flags;  // bits 0..2 as above, bits 8..15 t_old, bits 16..23 t_new
+    double cx, cy;
+};
+
+// alpha of incident triangle `code` of node i with node i placed at (x, y).
+template <int LAYOUT>
+__device__ __forceinline__ double alpha_with(const PassArgs &a, const uint32_t *nb, uint32_t code,
+                                             double x, double y)
+{
+    const double2 A = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + code_first(code)));
+    const double2 B = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + code_second(code)));
+    switch (code_slot(code)) {
+    case 0: return alpha_fp64(x, y, A.x, A.y, B.x, B.y);
+    case 1: return alpha_fp64(A.x, A.y, x, y, B.x, B.y);
+    default: return alpha_fp64(A.x, A.y, B.x, B.y, x, y);
+    }
+}
+
+// Exact update of free node i.  Without kHasCentre the centre is computed
+// here (neighbour sum in stored order, then IEEE division).  q_old / q_new are
+// the minima over all incident triangles, or the single candidate triangle
+// when the flags say the screen proved no other triangle can attain the
+// minimum.  Writes the node and its decision; returns the squared move bits
+// (0 if not accepted) and whether it was accepted.
+template <int LAYOUT>
+__device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint32_t flags, double cx,
+                                             double cy, unsigned long long &d2_bits, bool &accepted)
+{
+    const uint32_t off = __ldg(a.node_off + i);
+    const uint32_t meta = __ldg(a.adj + off);
+    const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
+    const uint32_t *nb = a.adj + off + 1;
+    const double2 p = Coords<LAYOUT>::get(a.in, a.n, i);
+
+    if (!(flags & kHasCentre)) {
+        double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb));
+        double sx = v.x, sy = v.y;
+        for (uint32_t k = 1; k < deg; ++k) {
+            v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
+            sx = __dadd_rn(sx, v.x);
+            sy = __dadd_rn(sy, v.y);
+        }
+        const double fd = (double)deg;
+        cx = __ddiv_rn(sx, fd);
+        cy = __ddiv_rn(sy, fd);
+    }
+
+    double q_old = 0.0, q_new = 0.0;
+    if (flags & kSingleOld) {
+        q_old = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + ((flags >> 8) & 0xffu)), p.x, p.y);
+    } else {
+        for (uint32_t t = 0; t < ntri; ++t) {
+            const double q = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + t), p.x, p.y);
+            if (t == 0 || q < q_old) q_old = q;
+        }
+    }
+    if (flags & kSingleNew) {
+        q_new = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + ((flags >> 16) & 0xffu)), cx, cy);
+    } else {
+        for (uint32_t t = 0; t < ntri; ++t) {
+            const double q = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + t), cx, cy);
+            if (t == 0 || q < q_new) q_new = q;
+        }
+    }
+
+    const bool ok = a.strict ? (q_new > q_old) : (q_new >= q_old);
+    double2 o = p;
+    d2_bits = 0ull;
+    if (ok) {
+        const double dx = __dsub_rn(cx, p.x), dy = __dsub_rn(cy, p.y);
+        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        d2_bits = (unsigned long long)__double_as_longlong(d2);
+        o = make_double2(cx, cy);
+    }
+    Coords<LAYOUT>::put(a.out, a.n, i, o);
+    if (a.accept) a.accept[i] = ok ? 1 : 0;
+    accepted = ok;
+}
+
+}  // namespace sls

@@ -12,12 +12,13 @@
 // The FP64 pipe of GB300 is narrow, so this kernel is the exact baseline and
 // the fallback of the screened kernel, not the fast path.
 #include "kernels.h"
+#include "node_exact.cuh"
 
 namespace sls {
 
 namespace {
 
-template <int LAYOUT, bool RECORD>
+template <int LAYOUT>
 __global__ void __launch_bounds__(1024) pass_fp64_kernel(PassArgs a)
 {
     if (pass_is_skipped(a.stats, a.q, a.tol_active, a.thr_bits)) return;
@@ -26,64 +27,16 @@ __global__ void __launch_bounds__(1024) pass_fp64_kernel(PassArgs a)
     unsigned long long best = 0ull, nacc = 0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const uint32_t off = __ldg(a.node_off + i);
-        const uint32_t meta = __ldg(a.adj + off);
+        const uint32_t meta = __ldg(a.adj + __ldg(a.node_off + i));
         if (meta & kMetaFixed) {
-            if (RECORD) a.accept[i] = 0;
+            if (a.accept) a.accept[i] = 0;
             continue;
         }
-        const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
-        const uint32_t *nb = a.adj + off + 1;
-        const double2 p = Coords<LAYOUT>::get(a.in, a.n, i);
-
-        // Eq. 2: centre of the neighbours, summed in the stored order.
-        double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb));
-        double sx = v.x, sy = v.y;
-        for (uint32_t k = 1; k < deg; ++k) {
-            v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
-            sx = __dadd_rn(sx, v.x);
-            sy = __dadd_rn(sy, v.y);
-        }
-        const double fd = (double)deg;
-        const double cx = __ddiv_rn(sx, fd), cy = __ddiv_rn(sy, fd);
-
-        // Section 3.3.4: worst incident quality before and after the move.
-        double q_old = 0.0, q_new = 0.0;
-        for (uint32_t t = 0; t < ntri; ++t) {
-            const uint32_t c = __ldg(nb + deg + t);
-            const double2 A = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + code_first(c)));
-            const double2 B = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + code_second(c)));
-            double qb, qa;
-            switch (code_slot(c)) {
-            case 0:
-                qb = alpha_fp64(p.x, p.y, A.x, A.y, B.x, B.y);
-                qa = alpha_fp64(cx, cy, A.x, A.y, B.x, B.y);
-                break;
-            case 1:
-                qb = alpha_fp64(A.x, A.y, p.x, p.y, B.x, B.y);
-                qa = alpha_fp64(A.x, A.y, cx, cy, B.x, B.y);
-                break;
-            default:
-                qb = alpha_fp64(A.x, A.y, B.x, B.y, p.x, p.y);
-                qa = alpha_fp64(A.x, A.y, B.x, B.y, cx, cy);
-                break;
-            }
-            if (t == 0 || qb < q_old) q_old = qb;
-            if (t == 0 || qa < q_new) q_new = qa;
-        }
-
-        const bool ok = a.strict ? (q_new > q_old) : (q_new >= q_old);
-        double2 o = p;
-        if (ok) {
-            const double dx = __dsub_rn(cx, p.x), dy = __dsub_rn(cy, p.y);
-            const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(d2);
-            best = bits > best ? bits : best;
-            nacc += 1ull;
-            o = make_double2(cx, cy);
-        }
-        Coords<LAYOUT>::put(a.out, a.n, i, o);
-        if (RECORD) a.accept[i] = ok ? 1 : 0;
+        unsigned long long bits;
+        bool ok;
+        exact_update<LAYOUT>(a, i, 0u, 0.0, 0.0, bits, ok);
+        best = bits > best ? bits : best;
+        nacc += ok ? 1ull : 0ull;
     }
     block_reduce_stats(a.stats + a.q, best, nacc, 0ull);
 }
@@ -163,14 +116,8 @@ __global__ void aos_to_soa_kernel(const double2 *__restrict__ aos, double *__res
 
 cudaError_t launch_pass_fp64(const PassArgs &a, int layout, int block, int grid, cudaStream_t s)
 {
-    const bool rec = a.accept != nullptr;
-    if (layout == 0) {
-        if (rec) pass_fp64_kernel<0, true><<<grid, block, 0, s>>>(a);
-        else pass_fp64_kernel<0, false><<<grid, block, 0, s>>>(a);
-    } else {
-        if (rec) pass_fp64_kernel<1, true><<<grid, block, 0, s>>>(a);
-        else pass_fp64_kernel<1, false><<<grid, block, 0, s>>>(a);
-    }
+    if (layout == 0) pass_fp64_kernel<0><<<grid, block, 0, s>>>(a);
+    else pass_fp64_kernel<1><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -178,9 +125,9 @@ int pass_fp64_occupancy(int layout, int block)
 {
     int nb = 0;
     if (layout == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_fp64_kernel<0, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_fp64_kernel<0>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_fp64_kernel<1, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_fp64_kernel<1>, block, 0);
     return nb > 0 ? nb : 1;
 }
 

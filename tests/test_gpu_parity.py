@@ -202,3 +202,49 @@ def test_large_grid_sampled_passes(sls):
             assert dd.max() == pytest.approx(info["maxd2_last"], rel=1e-12)
             assert info["accepted_last"] >= int((dd > 0).sum())
             assert np.array_equal(cur[mesh.boundary == 1], mesh.xy[mesh.boundary == 1])
+
+
+@pytest.mark.parametrize("transform", ["shift_negative", "tiny", "huge", "far_offset", "signed_zeros",
+                                       "denormal_scale", "mixed_binades"])
+def test_screened_kernel_domain_edges(sls, transform):
+    # the screened kernel's fast path has limits (exponent window, sign,
+    # zeros); every case must stay bit-identical through its fallbacks
+    mesh = meshgen.jittered_grid(45, 38, 0.35, 99, numbering="random")
+    xy = mesh.xy.copy()
+    if transform == "shift_negative":
+        xy -= 0.5
+    elif transform == "tiny":
+        xy *= 1e-9
+    elif transform == "huge":
+        xy *= 1e12
+    elif transform == "far_offset":
+        xy += np.array([1e6, -3e5])
+    elif transform == "signed_zeros":
+        xy -= 0.5
+        xy[np.abs(xy) < 0.05] = -0.0
+    elif transform == "denormal_scale":
+        xy *= 2.0 ** -1040
+    elif transform == "mixed_binades":
+        xy = xy * 3.0 - 1.0
+    mesh.xy = xy
+    for strict in (False, True):
+        got, ref = _run_both(sls, mesh, 12, strict=strict, kernel="filtered")
+        _check(got, ref, f"{transform} strict={strict}")
+
+
+def test_screened_matches_fp64_on_many_meshes(sls):
+    rng = np.random.default_rng(12345)
+    for r in range(25):
+        nx, ny = int(rng.integers(3, 60)), int(rng.integers(3, 60))
+        mesh = meshgen.jittered_grid(nx, ny, float(rng.uniform(0.0, 0.49)), 500 + r,
+                                     numbering=["natural", "morton", "random"][r % 3],
+                                     pull_fraction=0.1 if r % 4 == 0 else 0.0)
+        outs = []
+        for kernel in ("fp64", "filtered"):
+            with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=kernel, record_accept=True) as g:
+                info = g.smooth(30)
+                outs.append((g.coords(), g.accept_mask(), info))
+        _assert_same(outs[1][0], outs[0][0], f"mesh {r}")
+        assert np.array_equal(outs[1][1], outs[0][1])
+        for key in ("iterations", "accepted_last", "maxd2_last"):
+            assert outs[1][2][key] == outs[0][2][key]
