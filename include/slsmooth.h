@@ -148,25 +148,32 @@ sls_status sls_mesh_stats(const sls_mesh *mesh, int64_t *n, int64_t *m, int64_t 
 
 sls_status sls_mesh_destroy(sls_mesh *mesh);
 
-/* ---- batched form: many meshes of uneven size, one launch per pass ------
- * The meshes' adjacency is concatenated with per-mesh node offsets; each mesh
- * keeps its own iteration count and tolerance.  Results are bit-identical to
- * smoothing each mesh alone. */
+/* ---- batched form: many meshes of uneven size, one graph launch --------
+ * Each mesh keeps its own device buffers, iteration count and tolerance; the
+ * batch adds a job table and a list of 32-node work items, and runs round r
+ * (pass r of every mesh with passes left) as one kernel launch; all rounds of
+ * a call are replayed from one CUDA graph.  Results are bit-identical to
+ * smoothing each mesh alone with sls_smooth. */
 
-/* Packs k mesh handles (their current coordinates, adjacency and options) into
- * one batch.  iters (k int32) and tol_rel (k float64, may be NULL = off) are
- * the per-mesh stop rules.  The meshes themselves are not modified. */
+/* Packs k distinct mesh handles (same device, same layout) into one batch.
+ * iters (k int32) and tol_rel (k float64, may be NULL = off) are the per-mesh
+ * stop rules.  The handles must outlive the batch; sls_batch_smooth advances
+ * their coordinates in place.  The coordinates at packing time are saved for
+ * sls_batch_reset.  With opt == NULL or opt->block_size == 0 the block size
+ * is autotuned by timing one full batch smooth per candidate (128, 256, 512
+ * threads), restoring the saved coordinates after each trial. */
 sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *iters,
                             const double *tol_rel, const sls_options *opt, sls_batch **out);
 
-/* Smooths every mesh of the batch to its own stop rule.  infos (k, may be
- * NULL) receives the per-mesh results. */
+/* Smooths every mesh of the batch to its own stop rule (continuing from each
+ * mesh's current coordinates).  infos (k, may be NULL) receives the per-mesh
+ * results in packing order. */
 sls_status sls_batch_smooth(sls_batch *batch, sls_info *infos);
 
 /* Coordinates of mesh j of the batch (host, 2 n_j float64). */
 sls_status sls_batch_get_coords(const sls_batch *batch, int32_t j, double *xy_out);
 
-/* Resets every mesh of the batch to the coordinates it was packed with. */
+/* Restores every mesh of the batch to the coordinates it had when packed. */
 sls_status sls_batch_reset(sls_batch *batch);
 
 sls_status sls_batch_destroy(sls_batch *batch);

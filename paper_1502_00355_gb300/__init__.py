@@ -278,7 +278,8 @@ class Server:
 
     def wait(self, job: int, timeout: float = -1.0, want_coords: bool = True):
         info = Info()
-        out = np.empty((self._sizes[job], 2), np.float64) if want_coords else None
+        n = self._sizes.get(job)
+        out = np.empty((n, 2), np.float64) if (want_coords and n is not None) else None
         _check(lib().sls_wait(self._h, C.c_uint64(job), float(timeout), _p(out), C.byref(info)),
                "sls_wait")
         self._sizes.pop(job, None)

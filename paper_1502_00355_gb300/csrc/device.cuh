@@ -31,6 +31,28 @@ struct PassArgs {
     uint8_t *accept;           // n decisions, or nullptr
 };
 
+// One mesh (job) of the batched and served forms.
+struct JobDesc {
+    double *xy[2];             // the job's two coordinate arrays
+    const uint32_t *node_off;  // n+1
+    const uint32_t *adj;
+    int64_t n;
+    PassStats *stats;          // one record per pass of the job
+    unsigned long long thr_bits;
+    int32_t strict, tol_active;
+    int32_t max_iter;          // passes to run at most
+    int32_t base_round;        // the job's pass q runs in round base_round + q
+    int32_t cur0;              // which array holds the job's starting coordinates
+    int32_t pad;
+    uint8_t *accept;           // n decisions, or nullptr
+};
+
+// 32 consecutive nodes [first, first + 32) of one job.
+struct WarpTask {
+    int32_t job;
+    int32_t first;
+};
+
 constexpr uint32_t kMetaFixed = 0x80000000u;
 
 __device__ __forceinline__ uint32_t meta_degree(uint32_t meta) { return meta & 0xffffu; }

@@ -18,6 +18,11 @@ int pass_fp64_occupancy(int layout, int block);
 cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int grid, cudaStream_t s);
 int pass_screened_occupancy(int layout, int block);
 
+// One round of the batched / served form over all active jobs' tasks.
+cudaError_t launch_batch_pass(const JobDesc *jobs, const WarpTask *tasks, int64_t ntasks, int round,
+                              int layout, int block, int grid, cudaStream_t s);
+int batch_pass_occupancy(int layout, int block);
+
 // Copy-back form: out -> in after pass q (skipped when pass q was skipped).
 cudaError_t launch_copy_back(const double *src, double *dst, int64_t n_doubles,
                              const PassStats *stats, int q, int grid, cudaStream_t s);

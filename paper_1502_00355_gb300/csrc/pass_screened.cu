@@ -23,10 +23,10 @@
 //     wide enough to also cover the FP64 evaluation's own rounding.  When the
 //     intervals of q_new and q_old are disjoint the FP64 decision is known.
 //  5. Nodes the screen cannot decide (near-ties), or whose ring leaves the
-//     fast path's limits, are queued in shared memory and finished by the
-//     exact FP64 update, densely packed so the narrow FP64 pipe is not wasted
-//     on idle lanes; only the triangles the screen could not rule out as the
-//     minimum are evaluated in FP64.
+//     fast path's limits, go to a per-warp queue in shared memory and are
+//     finished by the exact FP64 update 32 at a time, so the narrow FP64
+//     pipe is not wasted on idle lanes; only the triangles the screen could
+//     not rule out as the minimum are evaluated in FP64.
 #include <cfloat>
 
 #include "kernels.h"
@@ -38,6 +38,7 @@ namespace {
 
 constexpr int kFastMax = 16;  // degree and triangle limits of the screened path
 __constant__ double c_recip[kFastMax + 1];  // RN(1/N)
+__constant__ double c_degree[kFastMax + 1]; // N as a double
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
@@ -85,6 +86,15 @@ __device__ __forceinline__ double from_frame(long long S, int F)
     return bitsd(sign | ((unsigned long long)(F + L - 53) << 52) | (m & 0xFFFFFFFFFFFFFull));
 }
 
+// cx - px as FP64 computes it: the frame difference D when it is exactly
+// representable (|D| < 2^53), otherwise one FP64 subtraction.
+__device__ __forceinline__ double exact_diff(long long D, int F, double cx, double px)
+{
+    const unsigned long long a = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
+    if (a >= (1ull << 53)) return __dsub_rn(cx, px);
+    return from_frame(D, F);
+}
+
 // Markstein's correctly rounded division by a small integer N (y = RN(1/N)).
 __device__ __forceinline__ double div_small(double s, double N, double y)
 {
@@ -93,24 +103,38 @@ __device__ __forceinline__ double div_small(double s, double N, double y)
     return __fma_rn(r, y, q0);
 }
 
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+// D * 2^(scale - 1075) as a float, truncated to 24 significant bits
+// (relative error below 2^-23), built with integer operations only: int64 to
+// float conversions would occupy the FP64 pipe.
+__device__ __forceinline__ float scaled_float(long long D, int scale)
+{
+    if (D == 0) return 0.0f;
+    const unsigned sign = D < 0 ? 0x80000000u : 0u;
+    const unsigned long long a = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
+    const int L = 64 - __clzll((long long)a);
+    const unsigned m = L > 24 ? (unsigned)(a >> (L - 24)) : (unsigned)(a << (24 - L));
+    // value = m * 2^(L - 24) * 2^(scale - 1075); m has its top bit at 23
+    const int e = L - 1 + scale - 1075 + 127;
+    return __uint_as_float(sign | ((unsigned)e << 23) | (m & 0x7fffffu));
+}
 
-// Screening constants (unit roundoff e = 2^-24).  For a triangle whose
-// vertices' local coordinates are bounded by R, with g = R^2 / s (s the
+// Screening constants (unit roundoff e = 2^-24).  Local coordinates carry a
+// relative error below 2e (truncation to 24 bits).  For a triangle whose
+// three vertices' local coordinates are bounded by R, with g = R^2 / s (s the
 // computed sum of squared edges), the FP32 alpha differs from the exact alpha
 // of the FP64 inputs by at most
-//   e * (13.2 |a| + (155.9 + 98 |a|) g) * (1 + 1.1 e (6.1 + 98 g)),
-// (edge errors 4.01 e R, cross 45 e R^2, edge sum 6.1 e s + 98 e R^2, FP32
+//   e * (13.2 |a| + (211.3 + 146 |a|) g) * (1 + 1.1 e (6.1 + 146 g)),
+// (edge errors 6.01 e R; cross 61 e R^2; edge sum 6.1 e s + 146 e R^2; FP32
 // constant, products and approximate reciprocal 7.1 e |a|), valid for
-// g <= kGMax.  The constants carry a further factor 1.5.  Because g >= 1/24
-// (every squared edge is at most 8 R^2), half of the resulting bound is at
-// least 3e-7: more than the FP64 evaluation's own error (< 2e-15 for
-// |alpha| <= 1) plus the FP32 rounding of a +- b and of the comparisons, so
-// those need no separate term.
+// g <= kGMax, where the last factor is at most 1.0096.  The constants carry a
+// further factor 1.5.  Because g >= 1/24 (every squared edge is at most
+// 8 R^2), half of the resulting bound exceeds 6e-7: more than the FP64
+// evaluation's own error (< 2e-15 for |alpha| <= 1) plus the FP32 rounding of
+// a +- b and of the comparisons, so those need no separate term.
 constexpr float kEps = 5.9604645e-8f;
-constexpr float kC1 = 1.5f * 1.0065f * 13.2f * kEps;
-constexpr float kC2 = 1.5f * 1.0065f * 155.9f * kEps;
-constexpr float kC3 = 1.5f * 1.0065f * 98.0f * kEps;
+constexpr float kC1 = 1.5f * 1.0096f * 13.2f * kEps;
+constexpr float kC2 = 1.5f * 1.0096f * 211.3f * kEps;
+constexpr float kC3 = 1.5f * 1.0096f * 146.0f * kEps;
 constexpr float kGMax = 1000.0f;
 constexpr float kTwoSqrt3f = 3.46410161514f;
 
@@ -141,7 +165,8 @@ struct MinTrack {
     __device__ __forceinline__ bool single() const { return minLother > minU; }
 };
 
-// FP32 alpha and its bound for the triangle (X, A, B) in that orientation.
+// FP32 alpha and its bound for the triangle (X, A, B) in that orientation;
+// R2 bounds the squared local coordinates of its three vertices.
 __device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float Ay, float Bx, float By,
                                              float ba2, float R2, float sgn, float &a, float &b)
 {
@@ -153,9 +178,168 @@ __device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float
     const float g = R2 * inv;
     const float aa = fabsf(a);
     b = fmaf(kC1, aa, fmaf(kC3, aa, kC2) * g);
-    if (!(s > 0.0f) || !(g <= kGMax)) {  // degenerate or unscreenable: no information
+    // degenerate, unscreenable, or so small / large that FP32 under- or
+    // overflow could escape the relative bound: no information
+    if (!(s > 0.0f) || !(g <= kGMax) || !(R2 >= 1e-28f) || !(R2 <= 1e30f)) {
         a = 0.0f;
         b = FLT_MAX;
+    }
+}
+
+// Screens free or fixed node i of one mesh (Eq. 2 and the accept test of
+// Section 3.3.4).  Decided nodes are written and counted here; returns true
+// when the node must be finished by the exact path (d filled in).  loc is
+// this thread's slice of the shared local-coordinate buffer (stride nthr).
+template <int LAYOUT>
+__device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2 *loc, int nthr, Deferred &d,
+                                            unsigned long long &best, unsigned long long &nacc)
+{
+    bool defer = false;
+    d.node = (int32_t)i;
+    d.flags = 0u;
+    d.cx = 0.0;
+    d.cy = 0.0;
+    const uint32_t off = __ldg(a.node_off + i);
+    const uint32_t meta = __ldg(a.adj + off);
+    if (meta & kMetaFixed) {
+        if (a.accept) a.accept[i] = 0;
+    } else {
+        const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
+        const uint32_t *nb = a.adj + off + 1;
+        const double2 p = Coords<LAYOUT>::get(a.in, a.n, i);
+        const unsigned long long px = dbits(p.x), py = dbits(p.y);
+        bool ok = deg <= (uint32_t)kFastMax && ntri <= (uint32_t)kFastMax && in_domain(px) && in_domain(py);
+        // exponent window of the ring (zeros impose nothing)
+        int hx = px ? bexp(px) : 0, lx = px ? bexp(px) : 2047;
+        int hy = py ? bexp(py) : 0, ly = py ? bexp(py) : 2047;
+        if (ok) {
+            for (uint32_t k = 0; k < deg; ++k) {
+                const double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
+                const unsigned long long vx = dbits(v.x), vy = dbits(v.y);
+                ok = ok && in_domain(vx) && in_domain(vy);
+                if (vx) { hx = max(hx, bexp(vx)); lx = min(lx, bexp(vx)); }
+                if (vy) { hy = max(hy, bexp(vy)); ly = min(ly, bexp(vy)); }
+            }
+        }
+        const int Fx = hx ? hx - 4 : 1019, Fy = hy ? hy - 4 : 1019;
+        ok = ok && lx >= Fx && ly >= Fy && Fx >= 960 && Fx <= 1070 && Fy >= 960 && Fy <= 1070;
+        if (!ok) {
+            defer = true;  // exact path computes everything
+        } else {
+            // Eq. 2 on the integer pipe, in the stored summation order
+            const long long Mx = to_frame(px, Fx), My = to_frame(py, Fy);
+            long long Sx = 0, Sy = 0;
+            for (uint32_t k = 0; k < deg; ++k) {
+                const double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
+                const long long X = to_frame(dbits(v.x), Fx), Y = to_frame(dbits(v.y), Fy);
+                Sx = k ? rn53(Sx + X) : X;
+                Sy = k ? rn53(Sy + Y) : Y;
+                loc[k * nthr] = make_float2(scaled_float(X - Mx, Fx), scaled_float(Y - My, Fy));
+            }
+            const double fd = c_degree[deg], y = c_recip[deg];
+            const double cx = div_small(from_frame(Sx, Fx), fd, y);
+            const double cy = div_small(from_frame(Sy, Fy), fd, y);
+            d.cx = cx;
+            d.cy = cy;
+            d.flags = kHasCentre;
+            const unsigned long long cbx = dbits(cx), cby = dbits(cy);
+            if (cbx == px && cby == py) {
+                // the centre is the node itself: q_new == q_old exactly
+                const bool acc = !a.strict;
+                Coords<LAYOUT>::put(a.out, a.n, i, p);
+                if (a.accept) a.accept[i] = acc ? 1 : 0;
+                nacc += acc ? 1ull : 0ull;
+            } else if (!((cbx == 0ull || bexp(cbx) >= Fx) && (cby == 0ull || bexp(cby) >= Fy))) {
+                defer = true;
+            } else {
+                const long long DCx = to_frame(cbx, Fx) - Mx, DCy = to_frame(cby, Fy) - My;
+                const float Cx = scaled_float(DCx, Fx), Cy = scaled_float(DCy, Fy);
+                const float rC = fmaxf(fabsf(Cx), fabsf(Cy));
+                MinTrack o, nw;
+                o.init();
+                nw.init();
+                for (uint32_t t = 0; t < ntri; ++t) {
+                    const uint32_t c = __ldg(nb + deg + t);
+                    const float2 A = loc[code_first(c) * nthr];
+                    const float2 B = loc[code_second(c) * nthr];
+                    const float sgn = code_slot(c) == 1u ? -1.0f : 1.0f;
+                    const float bax = B.x - A.x, bay = B.y - A.y;
+                    const float ba2 = fmaf(bax, bax, bay * bay);
+                    const float rAB = fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y)));
+                    const float rN = fmaxf(rAB, rC);
+                    float av, bv;
+                    screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, rAB * rAB, sgn, av, bv);
+                    o.add(av, bv, (int)t);
+                    screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, rN * rN, sgn, av, bv);
+                    nw.add(av, bv, (int)t);
+                }
+                // q_new and q_old (FP64) lie in [lo, minU] of their side
+                const float new_lo = nw.lo(), new_hi = nw.minU;
+                const float old_lo = o.lo(), old_hi = o.minU;
+                if (new_lo > old_hi || new_hi < old_lo) {
+                    const bool acc = new_lo > old_hi;
+                    double2 outp = p;
+                    if (acc) {
+                        // cx - px, as FP64 rounds it, from the exact frame difference
+                        const double dx = exact_diff(DCx, Fx, cx, p.x), dy = exact_diff(DCy, Fy, cy, p.y);
+                        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                        const unsigned long long b2 = dbits(d2);
+                        best = b2 > best ? b2 : best;
+                        nacc += 1ull;
+                        outp = make_double2(cx, cy);
+                    }
+                    Coords<LAYOUT>::put(a.out, a.n, i, outp);
+                    if (a.accept) a.accept[i] = acc ? 1 : 0;
+                } else {
+                    defer = true;
+                    d.flags |= (o.single() ? kSingleOld : 0u) | (nw.single() ? kSingleNew : 0u) |
+                               ((uint32_t)o.best << 8) | ((uint32_t)nw.best << 16);
+                }
+            }
+        }
+    }
+    return defer;
+}
+
+// Finishes one full warp's worth of deferred nodes (lane k takes entry k)
+// when the warp's queue holds at least 32, or all remaining entries at the
+// end.  Dense lanes keep the narrow FP64 pipe busy without block barriers.
+template <int LAYOUT>
+__device__ __forceinline__ void drain_queue(const PassArgs &a, Deferred *wq, int &qn, bool all,
+                                            unsigned long long &best, unsigned long long &nacc)
+{
+    const int lane = threadIdx.x & 31;
+    while (qn >= 32 || (all && qn > 0)) {
+        if (lane < qn) {
+            const Deferred e = wq[lane];
+            unsigned long long b2;
+            bool acc;
+            exact_update<LAYOUT>(a, e.node, e.flags, e.cx, e.cy, b2, acc);
+            best = b2 > best ? b2 : best;
+            nacc += acc ? 1ull : 0ull;
+        }
+        const int rest = qn > 32 ? qn - 32 : 0;
+        __syncwarp();
+        if (lane < rest) wq[lane] = wq[32 + lane];
+        __syncwarp();
+        qn = rest;
+    }
+}
+
+// Warp-wide reduction of the statistics into one record (lane 0 writes).
+__device__ __forceinline__ void warp_flush_stats(PassStats *st, unsigned long long best,
+                                                 unsigned long long nacc, unsigned long long nfb)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, best, o);
+        best = m2 > best ? m2 : best;
+        nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+        nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (best) atomicMax(&st->maxd2_bits, best);
+        if (nacc) atomicAdd(&st->nacc, nacc);
+        if (nfb) atomicAdd(&st->fallbacks, nfb);
     }
 }
 
@@ -163,153 +347,109 @@ template <int LAYOUT>
 __global__ void __launch_bounds__(512) pass_screened_kernel(PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_qn;
     const int nthr = blockDim.x;
     float2 *s_loc = reinterpret_cast<float2 *>(smem_raw);                       // [kFastMax][nthr]
-    Deferred *s_q = reinterpret_cast<Deferred *>(s_loc + kFastMax * nthr);      // [2 * nthr]
+    Deferred *s_q = reinterpret_cast<Deferred *>(s_loc + kFastMax * nthr);      // [64] per warp
 
     if (pass_is_skipped(a.stats, a.q, a.tol_active, a.thr_bits)) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (blockIdx.x == 0 && tid == 0) a.stats[a.q].executed = 1u;
-    if (tid == 0) s_qn = 0;
-    __syncthreads();
 
     unsigned long long best = 0ull, nacc = 0ull, nfb = 0ull;
     float2 *loc = s_loc + tid;
-    const int64_t ntiles = (a.n + nthr - 1) / nthr;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t i = tile * nthr + tid;
-        bool defer = false;
+    Deferred *wq = s_q + 64 * warp;
+    int qn = 0;  // warp-uniform queue length
+    const int64_t nwtiles = (a.n + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * (nthr >> 5);
+    for (int64_t wt = (int64_t)blockIdx.x * (nthr >> 5) + warp; wt < nwtiles; wt += wstride) {
+        const int64_t i = wt * 32 + lane;
         Deferred d;
-        d.flags = 0u;
-        d.cx = 0.0;
-        d.cy = 0.0;
-        if (i < a.n) {
-            d.node = (int32_t)i;
-            const uint32_t off = __ldg(a.node_off + i);
-            const uint32_t meta = __ldg(a.adj + off);
-            if (meta & kMetaFixed) {
-                if (a.accept) a.accept[i] = 0;
-            } else {
-                const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
-                const uint32_t *nb = a.adj + off + 1;
-                const double2 p = Coords<LAYOUT>::get(a.in, a.n, i);
-                const unsigned long long px = dbits(p.x), py = dbits(p.y);
-                bool ok = deg <= (uint32_t)kFastMax && ntri <= (uint32_t)kFastMax && in_domain(px) && in_domain(py);
-                // exponent window of the ring (zeros impose nothing)
-                int hx = px ? bexp(px) : 0, lx = px ? bexp(px) : 2047;
-                int hy = py ? bexp(py) : 0, ly = py ? bexp(py) : 2047;
-                if (ok) {
-                    for (uint32_t k = 0; k < deg; ++k) {
-                        const double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
-                        const unsigned long long vx = dbits(v.x), vy = dbits(v.y);
-                        ok = ok && in_domain(vx) && in_domain(vy);
-                        if (vx) { hx = max(hx, bexp(vx)); lx = min(lx, bexp(vx)); }
-                        if (vy) { hy = max(hy, bexp(vy)); ly = min(ly, bexp(vy)); }
-                    }
-                }
-                const int Fx = hx ? hx - 4 : 1019, Fy = hy ? hy - 4 : 1019;
-                ok = ok && lx >= Fx && ly >= Fy && Fx >= 960 && Fx <= 1070 && Fy >= 960 && Fy <= 1070;
-                if (!ok) {
-                    defer = true;  // exact path computes everything
-                } else {
-                    // Eq. 2 on the integer pipe, in the stored summation order
-                    const long long Mx = to_frame(px, Fx), My = to_frame(py, Fy);
-                    const float scx = pow2f(Fx - 1075), scy = pow2f(Fy - 1075);
-                    long long Sx = 0, Sy = 0;
-                    float R = 0.0f;
-                    for (uint32_t k = 0; k < deg; ++k) {
-                        const double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
-                        const long long X = to_frame(dbits(v.x), Fx), Y = to_frame(dbits(v.y), Fy);
-                        Sx = k ? rn53(Sx + X) : X;
-                        Sy = k ? rn53(Sy + Y) : Y;
-                        const float lxf = __ll2float_rn(X - Mx) * scx, lyf = __ll2float_rn(Y - My) * scy;
-                        loc[k * nthr] = make_float2(lxf, lyf);
-                        R = fmaxf(R, fmaxf(fabsf(lxf), fabsf(lyf)));
-                    }
-                    const double fd = (double)deg, y = c_recip[deg];
-                    const double cx = div_small(from_frame(Sx, Fx), fd, y);
-                    const double cy = div_small(from_frame(Sy, Fy), fd, y);
-                    d.cx = cx;
-                    d.cy = cy;
-                    d.flags = kHasCentre;
-                    const unsigned long long cbx = dbits(cx), cby = dbits(cy);
-                    if (cbx == px && cby == py) {
-                        // the centre is the node itself: q_new == q_old exactly
-                        const bool acc = !a.strict;
-                        Coords<LAYOUT>::put(a.out, a.n, i, p);
-                        if (a.accept) a.accept[i] = acc ? 1 : 0;
-                        nacc += acc ? 1ull : 0ull;
-                    } else if (!((cbx == 0ull || bexp(cbx) >= Fx) && (cby == 0ull || bexp(cby) >= Fy))) {
-                        defer = true;
-                    } else {
-                        const float Cx = __ll2float_rn(to_frame(cbx, Fx) - Mx) * scx;
-                        const float Cy = __ll2float_rn(to_frame(cby, Fy) - My) * scy;
-                        R = fmaxf(R, fmaxf(fabsf(Cx), fabsf(Cy)));
-                        const float R2 = R * R;
-                        MinTrack o, nw;
-                        o.init();
-                        nw.init();
-                        for (uint32_t t = 0; t < ntri; ++t) {
-                            const uint32_t c = __ldg(nb + deg + t);
-                            const float2 A = loc[code_first(c) * nthr];
-                            const float2 B = loc[code_second(c) * nthr];
-                            const float sgn = code_slot(c) == 1u ? -1.0f : 1.0f;
-                            const float bax = B.x - A.x, bay = B.y - A.y;
-                            const float ba2 = fmaf(bax, bax, bay * bay);
-                            float av, bv;
-                            screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, R2, sgn, av, bv);
-                            o.add(av, bv, (int)t);
-                            screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, R2, sgn, av, bv);
-                            nw.add(av, bv, (int)t);
-                        }
-                        // q_new and q_old (FP64) lie in [lo, minU] of their side
-                        const float new_lo = nw.lo(), new_hi = nw.minU;
-                        const float old_lo = o.lo(), old_hi = o.minU;
-                        if (R2 >= 1e-30f && R2 <= 1e30f && (new_lo > old_hi || new_hi < old_lo)) {
-                            const bool acc = new_lo > old_hi;
-                            double2 outp = p;
-                            if (acc) {
-                                const double dx = __dsub_rn(cx, p.x), dy = __dsub_rn(cy, p.y);
-                                const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                                const unsigned long long b2 = dbits(d2);
-                                best = b2 > best ? b2 : best;
-                                nacc += 1ull;
-                                outp = make_double2(cx, cy);
-                            }
-                            Coords<LAYOUT>::put(a.out, a.n, i, outp);
-                            if (a.accept) a.accept[i] = acc ? 1 : 0;
-                        } else {
-                            defer = true;
-                            d.flags |= (o.single() ? kSingleOld : 0u) | (nw.single() ? kSingleNew : 0u) |
-                                       ((uint32_t)o.best << 8) | ((uint32_t)nw.best << 16);
-                        }
-                    }
-                }
-            }
-        }
-        if (defer) {
-            const int slot = atomicAdd(&s_qn, 1);
-            s_q[slot] = d;
-            nfb += 1ull;
-        }
-        __syncthreads();
-        const int qn = s_qn;
-        if (qn >= nthr || tile + gridDim.x >= ntiles) {
-            for (int k = tid; k < qn; k += nthr) {
-                const Deferred e = s_q[k];
-                unsigned long long b2;
-                bool acc;
-                exact_update<LAYOUT>(a, e.node, e.flags, e.cx, e.cy, b2, acc);
-                best = b2 > best ? b2 : best;
-                nacc += acc ? 1ull : 0ull;
-            }
-            __syncthreads();
-            if (tid == 0) s_qn = 0;
-            __syncthreads();
-        }
+        const bool defer = i < a.n && screen_node<LAYOUT>(a, i, loc, nthr, d, best, nacc);
+        const unsigned m = __ballot_sync(0xffffffffu, defer);
+        if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
+        qn += __popc(m);
+        nfb += defer ? 1ull : 0ull;
+        __syncwarp();
+        drain_queue<LAYOUT>(a, wq, qn, false, best, nacc);
     }
+    drain_queue<LAYOUT>(a, wq, qn, true, best, nacc);
     block_reduce_stats(a.stats + a.q, best, nacc, nfb);
+}
+
+// ---- batched / served form: many meshes, one launch per round -----------
+// Work is a list of warp tasks (32 consecutive nodes of one job).  Each warp
+// walks a contiguous chunk of tasks; a job takes part in round r as its pass
+// q = r - base_round while q < max_iter and its tolerance is not met.  The
+// deferred queue is drained and the statistics flushed whenever the warp
+// moves to another job, so every record gets exactly its own job's counts.
+template <int LAYOUT>
+__global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restrict__ jobs,
+                                                          const WarpTask *__restrict__ tasks, int64_t ntasks,
+                                                          int round)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nthr = blockDim.x;
+    float2 *s_loc = reinterpret_cast<float2 *>(smem_raw);
+    Deferred *s_q = reinterpret_cast<Deferred *>(s_loc + kFastMax * nthr);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *loc = s_loc + tid;
+    Deferred *wq = s_q + 64 * warp;
+
+    const int64_t nwarps = (int64_t)gridDim.x * (nthr >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (nthr >> 5) + warp;
+    const int64_t per = (ntasks + nwarps - 1) / nwarps;
+    const int64_t t0 = gw * per, t1 = t0 + per < ntasks ? t0 + per : ntasks;
+
+    int cur_job = -1;
+    bool active = false;
+    PassArgs a{};
+    unsigned long long best = 0ull, nacc = 0ull, nfb = 0ull;
+    int qn = 0;
+    for (int64_t t = t0; t <= t1; ++t) {
+        const int job = t < t1 ? tasks[t].job : -2;
+        if (job != cur_job) {
+            if (cur_job >= 0 && active) {
+                drain_queue<LAYOUT>(a, wq, qn, true, best, nacc);
+                warp_flush_stats(a.stats + a.q, best, nacc, nfb);
+            }
+            best = nacc = nfb = 0ull;
+            cur_job = job;
+            if (job < 0) break;
+            const JobDesc *J = jobs + job;
+            const int q = round - J->base_round;
+            PassStats *st = J->stats;
+            const int tol_active = J->tol_active;
+            const unsigned long long thr_bits = J->thr_bits;
+            active = q >= 0 && q < J->max_iter && !pass_is_skipped(st, q, tol_active, thr_bits);
+            if (active) {
+                double *x0 = J->xy[0], *x1 = J->xy[1];
+                const bool odd = ((J->cur0 + q) & 1) != 0;
+                a.in = odd ? x1 : x0;
+                a.out = odd ? x0 : x1;
+                a.node_off = J->node_off;
+                a.adj = J->adj;
+                a.n = J->n;
+                a.stats = st;
+                a.q = q;
+                a.strict = J->strict;
+                a.tol_active = tol_active;
+                a.thr_bits = thr_bits;
+                a.accept = J->accept;
+            }
+        }
+        if (!active) continue;
+        const int64_t first = tasks[t].first;
+        if (first == 0 && lane == 0) a.stats[a.q].executed = 1u;
+        const int64_t i = first + lane;
+        Deferred d;
+        const bool defer = i < a.n && screen_node<LAYOUT>(a, i, loc, nthr, d, best, nacc);
+        const unsigned m = __ballot_sync(0xffffffffu, defer);
+        if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
+        qn += __popc(m);
+        nfb += defer ? 1ull : 0ull;
+        __syncwarp();
+        drain_queue<LAYOUT>(a, wq, qn, false, best, nacc);
+    }
 }
 
 bool g_consts_ready = false;
@@ -318,13 +458,20 @@ cudaError_t ensure_constants()
 {
     if (g_consts_ready) return cudaSuccess;
     double r[kFastMax + 1];
+    double dg[kFastMax + 1];
     r[0] = 0.0;
-    for (int k = 1; k <= kFastMax; ++k) r[k] = 1.0 / (double)k;
+    dg[0] = 0.0;
+    for (int k = 1; k <= kFastMax; ++k) {
+        r[k] = 1.0 / (double)k;
+        dg[k] = (double)k;
+    }
     cudaError_t e = cudaMemcpyToSymbol(c_recip, r, sizeof r);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_degree, dg, sizeof dg);
     if (e != cudaSuccess) return e;
-    for (int L = 0; L < 2; ++L) {
-        e = cudaFuncSetAttribute(L == 0 ? (const void *)pass_screened_kernel<0> : (const void *)pass_screened_kernel<1>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const void *fns[4] = {(const void *)pass_screened_kernel<0>, (const void *)pass_screened_kernel<1>,
+                          (const void *)batch_pass_kernel<0>, (const void *)batch_pass_kernel<1>};
+    for (const void *f : fns) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
     }
     g_consts_ready = true;
@@ -335,7 +482,7 @@ cudaError_t ensure_constants()
 
 size_t screened_smem_bytes(int block)
 {
-    return (size_t)block * (kFastMax * sizeof(float2) + 2 * sizeof(Deferred));
+    return (size_t)block * (kFastMax * sizeof(float2) + 2 * sizeof(Deferred));  // 64 entries per warp
 }
 
 cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int grid, cudaStream_t s)
@@ -346,6 +493,30 @@ cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int g
     if (layout == 0) pass_screened_kernel<0><<<grid, block, smem, s>>>(a);
     else pass_screened_kernel<1><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pass(const JobDesc *jobs, const WarpTask *tasks, int64_t ntasks, int round,
+                              int layout, int block, int grid, cudaStream_t s)
+{
+    cudaError_t e = ensure_constants();
+    if (e != cudaSuccess) return e;
+    if (ntasks <= 0) return cudaSuccess;
+    const size_t smem = screened_smem_bytes(block);
+    if (layout == 0) batch_pass_kernel<0><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round);
+    else batch_pass_kernel<1><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round);
+    return cudaGetLastError();
+}
+
+int batch_pass_occupancy(int layout, int block)
+{
+    if (ensure_constants() != cudaSuccess) return 1;
+    int nb = 0;
+    const size_t smem = screened_smem_bytes(block);
+    if (layout == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_pass_kernel<0>, block, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_pass_kernel<1>, block, smem);
+    return nb > 0 ? nb : 1;
 }
 
 int pass_screened_occupancy(int layout, int block)

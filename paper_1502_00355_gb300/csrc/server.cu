@@ -1,0 +1,529 @@
+// server.cu -- the served form: smoothing jobs arriving over time, run with
+// continuous batching.
+//
+// sls_submit copies a job's inputs and hands them to builder threads, which
+// validate the mesh and build its adjacency on the host.  A scheduler thread
+// admits built jobs in arrival order while their device footprint fits the
+// memory budget, uploads them on a copy stream (overlapping the running
+// round), and runs rounds: one launch of the batched pass kernel over every
+// active job, each at its own pass index.  After each round it reads every
+// active job's statistics record, retires the jobs that reached their
+// iteration cap or tolerance, copies their coordinates back and frees their
+// memory; queued jobs take the freed budget at the next round.  Latency is
+// measured from sls_submit to the moment the result is on the host.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "api_common.h"
+#include "kernels.h"
+
+using namespace sls;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum JobState { kBuilding, kQueued, kUploading, kActive, kDone, kFailed };
+
+struct ServerJob {
+    uint64_t id = 0;
+    // inputs, released once uploaded
+    std::vector<double> xy;
+    std::vector<int32_t> tri;
+    std::vector<uint8_t> boundary;
+    bool has_boundary = false;
+    HostMesh hm;
+    int32_t max_iter = 0;
+    double tol = 0.0;
+    size_t footprint = 0;
+    // device state
+    double *d_xy[2] = {nullptr, nullptr};
+    uint32_t *d_off = nullptr, *d_adj = nullptr;
+    PassStats *d_stats = nullptr;
+    cudaEvent_t uploaded = nullptr;
+    int base_round = 0;
+    int iterations = 0;
+    // result
+    JobState state = kBuilding;
+    sls_status status = SLS_OK;
+    std::string error;
+    std::vector<double> result;
+    sls_info info{};
+    Clock::time_point t_submit, t_done;
+};
+
+}  // namespace
+
+struct sls_server {
+    sls_options opt{};
+    size_t budget = 0, used = 0;
+    int32_t max_queue = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    cudaMemPool_t pool = nullptr;
+
+    std::mutex mu;
+    std::condition_variable cv_build, cv_sched, cv_done;
+    std::deque<std::shared_ptr<ServerJob>> to_build, queued;
+    std::vector<std::shared_ptr<ServerJob>> uploading, active;
+    std::unordered_map<uint64_t, std::shared_ptr<ServerJob>> jobs;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::vector<std::thread> builders;
+    std::thread sched;
+
+    // job table and warp tasks of the active set
+    JobDesc *d_jobs = nullptr, *h_jobs = nullptr;
+    WarpTask *d_tasks = nullptr, *h_tasks = nullptr;
+    size_t jobs_cap = 0, tasks_cap = 0;
+    PassStats *h_round = nullptr;  // pinned: this round's record of each active job
+    size_t round_cap = 0;
+    int64_t ntasks = 0;
+    int block = 256, grid = 0;
+    int round = 0;
+
+    // statistics
+    std::vector<double> latency_ms;
+    double busy_s = 0.0;
+    double node_updates = 0.0;
+    int64_t completed = 0;
+    std::string sched_error;
+};
+
+namespace {
+
+size_t job_footprint(const HostMesh &hm, int32_t max_iter)
+{
+    return 2 * sizeof(double) * 2 * (size_t)hm.n + sizeof(uint32_t) * (size_t)(hm.n + 1) +
+           sizeof(uint32_t) * hm.adj.size() + sizeof(PassStats) * (size_t)std::max(1, max_iter);
+}
+
+void builder_loop(sls_server *S)
+{
+    for (;;) {
+        std::shared_ptr<ServerJob> J;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_build.wait(lk, [S] { return S->stop || !S->to_build.empty(); });
+            if (S->to_build.empty()) return;
+            J = S->to_build.front();
+            S->to_build.pop_front();
+        }
+        const int64_t n = (int64_t)J->xy.size() / 2, m = (int64_t)J->tri.size() / 3;
+        sls_status st = build_host_mesh(J->xy.data(), n, J->tri.data(), m,
+                                        J->has_boundary ? J->boundary.data() : nullptr, J->hm, 4);
+        std::lock_guard<std::mutex> lk(S->mu);
+        J->tri.clear();
+        J->tri.shrink_to_fit();
+        J->boundary.clear();
+        if (st != SLS_OK) {
+            J->state = kFailed;
+            J->status = st;
+            J->error = sls_last_error();
+            J->t_done = Clock::now();
+            S->cv_done.notify_all();
+            continue;
+        }
+        J->footprint = job_footprint(J->hm, J->max_iter);
+        J->state = kQueued;
+        S->queued.push_back(J);
+        S->cv_sched.notify_all();
+    }
+}
+
+void free_job_device(sls_server *S, ServerJob &J)
+{
+    cudaFreeAsync(J.d_xy[0], S->stream);
+    cudaFreeAsync(J.d_xy[1], S->stream);
+    cudaFreeAsync(J.d_off, S->stream);
+    cudaFreeAsync(J.d_adj, S->stream);
+    cudaFreeAsync(J.d_stats, S->stream);
+    if (J.uploaded) cudaEventDestroy(J.uploaded);
+    J.d_xy[0] = J.d_xy[1] = nullptr;
+    J.d_off = J.d_adj = nullptr;
+    J.d_stats = nullptr;
+    J.uploaded = nullptr;
+}
+
+// Allocates (stream-ordered, from the server's pool) and uploads a job on
+// the copy stream; completion is tracked by J.uploaded.
+bool start_upload(sls_server *S, ServerJob &J)
+{
+    const int64_t n = J.hm.n;
+    const size_t cbytes = sizeof(double) * 2 * (size_t)n;
+    cudaStream_t cs = S->copy_stream;
+    bool ok = cudaMallocAsync((void **)&J.d_xy[0], cbytes, cs) == cudaSuccess &&
+              cudaMallocAsync((void **)&J.d_xy[1], cbytes, cs) == cudaSuccess &&
+              cudaMallocAsync((void **)&J.d_off, sizeof(uint32_t) * (n + 1), cs) == cudaSuccess &&
+              cudaMallocAsync((void **)&J.d_adj, sizeof(uint32_t) * std::max<size_t>(1, J.hm.adj.size()), cs) == cudaSuccess &&
+              cudaMallocAsync((void **)&J.d_stats, sizeof(PassStats) * std::max(1, J.max_iter), cs) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(J.d_xy[0], J.xy.data(), cbytes, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+         cudaMemcpyAsync(J.d_xy[1], J.xy.data(), cbytes, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+         cudaMemcpyAsync(J.d_off, J.hm.node_off.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+         cudaMemcpyAsync(J.d_adj, J.hm.adj.data(), sizeof(uint32_t) * J.hm.adj.size(), cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+         cudaMemsetAsync(J.d_stats, 0, sizeof(PassStats) * std::max(1, J.max_iter), cs) == cudaSuccess &&
+         cudaEventCreateWithFlags(&J.uploaded, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventRecord(J.uploaded, cs) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+}
+
+bool grow_host(PassStats *&h, size_t &cap, size_t need)
+{
+    if (need <= cap) return true;
+    const size_t c = std::max<size_t>(need, 2 * cap);
+    cudaFreeHost(h);
+    h = nullptr;
+    cap = 0;
+    if (cudaMallocHost((void **)&h, sizeof(PassStats) * c) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cap = c;
+    return true;
+}
+
+template <class T>
+bool grow_pair(T *&h, T *&d, size_t &cap, size_t need)
+{
+    if (need <= cap) return true;
+    const size_t c = std::max<size_t>(need, 2 * cap);
+    cudaFreeHost(h);
+    cudaFree(d);
+    h = nullptr;
+    d = nullptr;
+    cap = 0;
+    if (cudaMallocHost((void **)&h, sizeof(T) * c) != cudaSuccess || cudaMalloc((void **)&d, sizeof(T) * c) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cap = c;
+    return true;
+}
+
+void fail_job(sls_server *S, ServerJob &J, sls_status st, const char *msg)
+{
+    J.state = kFailed;
+    J.status = st;
+    J.error = msg;
+    J.t_done = Clock::now();
+    S->cv_done.notify_all();
+}
+
+// Rebuilds the job table and the warp-task list of the active set.
+bool rebuild_table(sls_server *S)
+{
+    const size_t na = S->active.size();
+    size_t ntasks = 0;
+    for (auto &J : S->active) ntasks += (size_t)((J->hm.n + 31) / 32);
+    if (!grow_pair(S->h_jobs, S->d_jobs, S->jobs_cap, na) ||
+        !grow_pair(S->h_tasks, S->d_tasks, S->tasks_cap, std::max<size_t>(1, ntasks)))
+        return false;
+    size_t t = 0;
+    for (size_t j = 0; j < na; ++j) {
+        ServerJob &J = *S->active[j];
+        JobDesc &D = S->h_jobs[j];
+        D.xy[0] = J.d_xy[0];
+        D.xy[1] = J.d_xy[1];
+        D.node_off = J.d_off;
+        D.adj = J.d_adj;
+        D.n = J.hm.n;
+        D.stats = J.d_stats;
+        const double thr = tolerance_threshold(J.tol, J.hm.diag);
+        std::memcpy(&D.thr_bits, &thr, sizeof thr);
+        D.strict = S->opt.accept_strict;
+        D.tol_active = J.tol > 0.0 ? 1 : 0;
+        D.max_iter = J.max_iter;
+        D.base_round = J.base_round;
+        D.cur0 = 0;
+        D.pad = 0;
+        D.accept = nullptr;
+        for (int64_t f = 0; f < J.hm.n; f += 32) S->h_tasks[t++] = WarpTask{(int32_t)j, (int32_t)f};
+    }
+    S->ntasks = (int64_t)t;
+    return cudaMemcpyAsync(S->d_jobs, S->h_jobs, sizeof(JobDesc) * na, cudaMemcpyHostToDevice, S->stream) == cudaSuccess &&
+           cudaMemcpyAsync(S->d_tasks, S->h_tasks, sizeof(WarpTask) * t, cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
+}
+
+void scheduler_loop(sls_server *S)
+{
+    cudaSetDevice(S->device);
+    bool dirty = true;
+    for (;;) {
+        std::vector<std::shared_ptr<ServerJob>> admit;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_sched.wait(lk, [S] {
+                return S->stop || !S->active.empty() || !S->uploading.empty() ||
+                       (!S->queued.empty() && S->used + S->queued.front()->footprint <= S->budget);
+            });
+            if (S->stop) break;
+            while (!S->queued.empty() && S->used + S->queued.front()->footprint <= S->budget) {
+                auto J = S->queued.front();
+                S->queued.pop_front();
+                S->used += J->footprint;
+                J->state = kUploading;
+                admit.push_back(J);
+            }
+        }
+        for (auto &J : admit) {
+            if (!start_upload(S, *J)) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                free_job_device(S, *J);
+                S->used -= J->footprint;
+                fail_job(S, *J, SLS_ERR_OOM, "device allocation or upload failed");
+                continue;
+            }
+            S->uploading.push_back(J);
+        }
+        // jobs whose upload has finished join in this round (the copies
+        // overlap the previous round); with nothing running, wait for them
+        for (size_t k = 0; k < S->uploading.size();) {
+            auto J = S->uploading[k];
+            if (S->active.empty()) cudaEventSynchronize(J->uploaded);
+            if (cudaEventQuery(J->uploaded) == cudaSuccess) {
+                J->xy.clear();
+                J->xy.shrink_to_fit();
+                J->base_round = S->round;
+                J->state = kActive;
+                S->active.push_back(J);
+                S->uploading.erase(S->uploading.begin() + k);
+                dirty = true;
+            } else {
+                ++k;
+            }
+        }
+        if (S->active.empty()) continue;
+        const size_t na = S->active.size();
+        if (dirty) {
+            if (!rebuild_table(S)) {
+                S->sched_error = "job table upload failed";
+                break;
+            }
+            dirty = false;
+        }
+        if (!grow_host(S->h_round, S->round_cap, na)) {
+            S->sched_error = "out of pinned host memory";
+            break;
+        }
+        const auto t0 = Clock::now();
+        cudaError_t e = launch_batch_pass(S->d_jobs, S->d_tasks, S->ntasks, S->round, S->opt.layout, S->block,
+                                          S->grid, S->stream);
+        for (size_t j = 0; j < na && e == cudaSuccess; ++j) {
+            ServerJob &J = *S->active[j];
+            const int q = S->round - J.base_round;
+            e = cudaMemcpyAsync(S->h_round + j, J.d_stats + std::min(q, std::max(0, J.max_iter - 1)),
+                                sizeof(PassStats), cudaMemcpyDeviceToHost, S->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        S->busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
+        if (e != cudaSuccess) {
+            S->sched_error = cudaGetErrorString(e);
+            cudaGetLastError();
+            break;
+        }
+        S->round += 1;
+        std::vector<std::shared_ptr<ServerJob>> keep;
+        for (size_t j = 0; j < na; ++j) {
+            auto Jp = S->active[j];
+            ServerJob &J = *Jp;
+            const PassStats &r = S->h_round[j];
+            bool done = true;  // a job with max_iter == 0 runs no pass
+            if (J.max_iter > 0 && r.executed) {
+                J.iterations += 1;
+                J.info.iterations = J.iterations;
+                J.info.accepted_last = (int64_t)r.nacc;
+                std::memcpy(&J.info.max_d2_last, &r.maxd2_bits, sizeof(double));
+                J.info.fp64_fallbacks += (int64_t)r.fallbacks;
+                const double thr = tolerance_threshold(J.tol, J.hm.diag);
+                unsigned long long tb;
+                std::memcpy(&tb, &thr, sizeof tb);
+                const bool conv = J.tol > 0.0 && r.maxd2_bits < tb;
+                J.info.converged = conv ? 1 : 0;
+                done = conv || J.iterations >= J.max_iter;
+            }
+            if (!done) {
+                keep.push_back(Jp);
+                continue;
+            }
+            J.result.resize(2 * (size_t)J.hm.n);
+            cudaMemcpyAsync(J.result.data(), J.d_xy[J.iterations & 1], sizeof(double) * J.result.size(),
+                            cudaMemcpyDeviceToHost, S->stream);
+            cudaStreamSynchronize(S->stream);
+            std::lock_guard<std::mutex> lk(S->mu);
+            free_job_device(S, J);
+            S->used -= J.footprint;
+            J.t_done = Clock::now();
+            J.state = kDone;
+            S->latency_ms.push_back(std::chrono::duration<double, std::milli>(J.t_done - J.t_submit).count());
+            S->node_updates += (double)J.hm.n * (double)J.iterations;
+            S->completed += 1;
+            J.hm = HostMesh();
+            S->cv_done.notify_all();
+            S->cv_sched.notify_all();
+        }
+        if (keep.size() != na) {
+            S->active.swap(keep);
+            dirty = true;
+        }
+    }
+    // cancel what is left
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto *list : {&S->active, &S->uploading}) {
+        for (auto &J : *list) {
+            free_job_device(S, *J);
+            fail_job(S, *J, SLS_ERR_NOT_FOUND, "server destroyed before the job finished");
+        }
+        list->clear();
+    }
+    for (auto &J : S->queued) fail_job(S, *J, SLS_ERR_NOT_FOUND, "server destroyed before the job started");
+    S->queued.clear();
+    if (!S->sched_error.empty())
+        for (auto &kv : S->jobs)
+            if (kv.second->state != kDone && kv.second->state != kFailed)
+                fail_job(S, *kv.second, SLS_ERR_CUDA, "scheduler stopped on a CUDA error");
+    cudaStreamSynchronize(S->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_options *opt, sls_server **out)
+{
+    if (!out) return fail(SLS_ERR_INVALID, "out must not be NULL");
+    *out = nullptr;
+    if (max_queue < 0) return fail(SLS_ERR_INVALID, "max_queue must be >= 0");
+    sls_options o = resolve_options(opt);
+    sls_status st = check_options(o);
+    if (st != SLS_OK) return st;
+    auto S = std::make_unique<sls_server>();
+    S->opt = o;
+    S->max_queue = max_queue;
+    if (cudaGetDevice(&S->device) != cudaSuccess) return fail(SLS_ERR_CUDA, "cudaGetDevice failed");
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(SLS_ERR_CUDA, "cudaMemGetInfo failed");
+    S->budget = hbm_budget ? hbm_budget : (size_t)(0.8 * (double)free_b);
+    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(SLS_ERR_CUDA, "cudaStreamCreate failed");
+    if (cudaDeviceGetDefaultMemPool(&S->pool, S->device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
+        cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    S->block = (o.block_size >= 64 && o.block_size <= 512) ? o.block_size : 256;
+    S->grid = device_sm_count() * batch_pass_occupancy(o.layout, S->block);
+    sls_server *raw = S.release();
+    for (int b = 0; b < 4; ++b) raw->builders.emplace_back(builder_loop, raw);
+    raw->sched = std::thread(scheduler_loop, raw);
+    *out = raw;
+    return SLS_OK;
+}
+
+sls_status sls_submit(sls_server *S, const double *xy, int64_t n, const int32_t *tri, int64_t m,
+                      const uint8_t *boundary, int32_t max_iter, double tol_rel, uint64_t *job)
+{
+    if (!S || !xy || !tri || !job) return fail(SLS_ERR_INVALID, "server, xy, tri and job must not be NULL");
+    if (n < 3 || m < 1 || n >= (int64_t(1) << 31) || m >= (int64_t(1) << 31))
+        return fail(SLS_ERR_INVALID, "bad mesh size");
+    if (max_iter < 0 || std::isnan(tol_rel)) return fail(SLS_ERR_INVALID, "bad stop rule");
+    // quick lower bound of the footprint: coordinates and offsets alone
+    const size_t least = 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1);
+    auto J = std::make_shared<ServerJob>();
+    J->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (least > S->budget) return fail(SLS_ERR_REJECTED, "job larger than the server's memory budget");
+    if (S->max_queue > 0 && (int64_t)(S->to_build.size() + S->queued.size()) >= S->max_queue)
+        return fail(SLS_ERR_BUSY, "server queue is full");
+    J->id = S->next_id++;
+    J->xy.assign(xy, xy + 2 * n);
+    J->tri.assign(tri, tri + 3 * m);
+    if (boundary) {
+        J->boundary.assign(boundary, boundary + n);
+        J->has_boundary = true;
+    }
+    J->max_iter = max_iter;
+    J->tol = tol_rel;
+    S->jobs[J->id] = J;
+    S->to_build.push_back(J);
+    S->cv_build.notify_one();
+    *job = J->id;
+    return SLS_OK;
+}
+
+sls_status sls_wait(sls_server *S, uint64_t job, double timeout_s, double *xy_out, sls_info *info)
+{
+    if (!S) return fail(SLS_ERR_INVALID, "server must not be NULL");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->jobs.find(job);
+    if (it == S->jobs.end()) return fail(SLS_ERR_NOT_FOUND, "unknown job id");
+    std::shared_ptr<ServerJob> J = it->second;
+    auto ready = [&J] { return J->state == kDone || J->state == kFailed; };
+    if (timeout_s < 0.0) {
+        S->cv_done.wait(lk, ready);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
+        return fail(SLS_ERR_TIMEOUT, "job not finished within the timeout");
+    }
+    // an oversized job is only known after its adjacency is built
+    if (J->state == kFailed) {
+        S->jobs.erase(job);
+        return fail(J->status, J->error);
+    }
+    if (xy_out) std::memcpy(xy_out, J->result.data(), sizeof(double) * J->result.size());
+    if (info) *info = J->info;
+    S->jobs.erase(job);
+    return SLS_OK;
+}
+
+sls_status sls_server_stats(const sls_server *Sc, double *p50_ms, double *p99_ms, double *nups, int64_t *completed)
+{
+    if (!Sc) return fail(SLS_ERR_INVALID, "server must not be NULL");
+    sls_server *S = const_cast<sls_server *>(Sc);
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::vector<double> v = S->latency_ms;
+    auto pct = [&v](double p) {
+        if (v.empty()) return 0.0;
+        const size_t k = std::min(v.size() - 1, (size_t)std::ceil(p / 100.0 * (double)v.size()) - (p > 0 ? 1 : 0));
+        std::nth_element(v.begin(), v.begin() + k, v.end());
+        return v[k];
+    };
+    if (p50_ms) *p50_ms = pct(50.0);
+    if (p99_ms) *p99_ms = pct(99.0);
+    if (nups) *nups = S->busy_s > 0.0 ? S->node_updates / S->busy_s : 0.0;
+    if (completed) *completed = S->completed;
+    return SLS_OK;
+}
+
+sls_status sls_server_destroy(sls_server *S)
+{
+    if (!S) return SLS_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_build.notify_all();
+    S->cv_sched.notify_all();
+    for (auto &t : S->builders) t.join();
+    if (S->sched.joinable()) S->sched.join();
+    cudaStreamSynchronize(S->copy_stream);
+    cudaFreeHost(S->h_jobs);
+    cudaFree(S->d_jobs);
+    cudaFreeHost(S->h_tasks);
+    cudaFree(S->d_tasks);
+    cudaFreeHost(S->h_round);
+    cudaStreamDestroy(S->stream);
+    cudaStreamDestroy(S->copy_stream);
+    delete S;
+    return SLS_OK;
+}
+
+}  // extern "C"

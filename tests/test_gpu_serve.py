@@ -1,0 +1,101 @@
+"""GPU parity of the served form (continuous batching): every job's result
+must be bit-identical to the oracle and to smoothing it alone, whatever else
+shares the GPU rounds with it."""
+import threading
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1502_00355_gb300 as mod
+    mod.build()
+    mod.lib()
+    return mod
+
+
+def _jobs(k, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(k):
+        n = int(round(np.exp(rng.uniform(np.log(100), np.log(30000)))))
+        side = max(3, int(round(np.sqrt(n))))
+        cap = int(rng.integers(1, 60))
+        tol = 1e-6 if r % 2 else 0.0
+        out.append((meshgen.jittered_grid(side, side + r % 3, 0.3, 9000 + r, numbering="morton"), cap, tol))
+    return out
+
+
+def test_served_jobs_equal_oracle_in_the_mix(sls):
+    jobs = _jobs(30, 1)
+    srv = sls.Server()
+    ids = [srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=tol) for m, cap, tol in jobs]
+    for (m, cap, tol), jid in zip(jobs, ids):
+        xy, info = srv.wait(jid, timeout=120.0)
+        om = oracle.OracleMesh(m.xy, m.tri, m.boundary)
+        rxy, rinfo, _ = om.smooth(m.xy, cap, tol=tol)
+        assert np.array_equal(xy, rxy)
+        for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
+            assert info[key] == rinfo[key], key
+    st = srv.stats()
+    assert st["completed"] == len(jobs) and st["p99_ms"] >= st["p50_ms"] > 0
+    srv.close()
+
+
+def test_served_concurrent_clients_and_budget(sls):
+    # a small memory budget forces jobs to wait for each other; four client
+    # threads submit and wait concurrently
+    jobs = _jobs(24, 2)
+    srv = sls.Server(hbm_budget=64 * 1024 * 1024)
+    results = {}
+
+    def client(part):
+        for idx in part:
+            m, cap, tol = jobs[idx]
+            jid = srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=tol)
+            results[idx] = srv.wait(jid, timeout=300.0)
+
+    threads = [threading.Thread(target=client, args=(list(range(c, len(jobs), 4)),)) for c in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert len(results) == len(jobs)
+    for idx, (m, cap, tol) in enumerate(jobs):
+        with sls.Mesh(m.xy, m.tri, m.boundary) as g:
+            info = g.smooth(cap, tol)
+            alone = g.coords()
+        xy, sinfo = results[idx]
+        assert np.array_equal(xy, alone)
+        assert sinfo["iterations"] == info["iterations"]
+    srv.close()
+
+
+def test_server_rejects_and_times_out(sls):
+    srv = sls.Server(hbm_budget=1024 * 1024)
+    big = meshgen.jittered_grid(300, 300, 0.3, 5)
+    with pytest.raises(sls.SlsError) as e:
+        srv.submit(big.xy, big.tri, big.boundary, max_iter=5)
+    assert e.value.code == 7
+    bad = np.array([[0, 1, 99]], dtype=np.int32)
+    jid = srv.submit(big.xy[:10], bad, None, max_iter=5)
+    with pytest.raises(sls.SlsError) as e:
+        srv.wait(jid, timeout=30.0)
+    assert e.value.code == 1
+    small = meshgen.jittered_grid(20, 20, 0.3, 6)
+    jid = srv.submit(small.xy, small.tri, small.boundary, max_iter=0)
+    xy, info = srv.wait(jid, timeout=30.0)
+    assert info["iterations"] == 0 and np.array_equal(xy, small.xy)
+    with pytest.raises(sls.SlsError) as e:
+        srv.wait(123456789, timeout=0.1)
+    assert e.value.code == 8
+    srv.close()
