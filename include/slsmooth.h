@@ -208,6 +208,42 @@ sls_status sls_server_stats(const sls_server *srv, double *p50_ms, double *p99_m
 
 sls_status sls_server_destroy(sls_server *srv);
 
+/* ---- smoothing without allocation ---------------------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot allocate device memory when they smooth: code that runs while a
+ * stream is being captured into a CUDA graph (cudaMalloc is not allowed in
+ * the default capture mode), latency-critical loops that must not pay the
+ * device-wide synchronisation of cudaMalloc/cudaFree, and plug-ins whose host
+ * application reserves all device memory for its own pool.
+ *
+ * Runs the same passes as sls_smooth on the mesh's adjacency, but on two
+ * coordinate buffers the caller owns, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The only scratch the kernels need -- one
+ * 32-byte statistics record per pass -- lives in a fixed array of
+ * SLS_NOALLOC_MAX_PASSES records (128 KiB) in device global memory, part of
+ * the library image: every GPU that loads the library holds it until the
+ * process exits.
+ *   mesh     a handle created with the AoS layout (layout = 0); its own
+ *            coordinates, accept mask and statistics are not used or changed
+ *   xy_in    device, 2n float64 interleaved: the starting coordinates; also
+ *            serves as the second buffer of the ping-pong, so its contents
+ *            are unspecified on return
+ *   xy_out   device, 2n float64: receives the result (distinct from xy_in)
+ *   max_iter 0 .. SLS_NOALLOC_MAX_PASSES; larger values are rejected with
+ *            SLS_ERR_INVALID
+ *   stream   cudaStream_t, or NULL for the mesh's stream; the call returns
+ *            after the work on it is done
+ * Results are bit-identical to sls_smooth on the same coordinates.  The
+ * first call on a device looks up the array's device address (with that
+ * device current; the mesh's device must be current); make that first call
+ * before any stream capture.  The array is cleared at the start of each
+ * call and keeps the last call's records afterwards.  All calls on a device
+ * share it: calls whose work overlaps on the GPU (other threads, other
+ * streams) race and must be serialised by the caller. */
+#define SLS_NOALLOC_MAX_PASSES 4096
+sls_status sls_smooth_noalloc(const sls_mesh *mesh, double *xy_in, double *xy_out, int32_t max_iter,
+                              double tol_rel, void *stream, sls_info *info);
+
 const char *sls_status_str(sls_status s);
 const char *sls_last_error(void);
 

@@ -87,6 +87,7 @@ def lib() -> C.CDLL:
                 "sls_wait": (S, [P, C.c_uint64, D, P, P]),
                 "sls_server_stats": (S, [P, P, P, P, P]),
                 "sls_server_destroy": (S, [P]),
+                "sls_smooth_noalloc": (S, [P, P, P, I32, D, P, P]),
                 "sls_status_str": (C.c_char_p, [S]),
                 "sls_last_error": (C.c_char_p, []),
             }
@@ -170,6 +171,20 @@ class Mesh:
     def smooth(self, max_iter: int, tol: float = 0.0) -> dict:
         info = Info()
         _check(lib().sls_smooth(self.handle, int(max_iter), float(tol), C.byref(info)), "sls_smooth")
+        return info.as_dict()
+
+    def smooth_noalloc(self, xy_in, xy_out, max_iter: int, tol: float = 0.0, stream=None) -> dict:
+        """Passes on two caller-owned float64 CUDA tensors of shape (n, 2),
+        allocating nothing (``sls_smooth_noalloc``): xy_in holds the start
+        and is clobbered, xy_out receives the result."""
+        import torch
+        for t in (xy_in, xy_out):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == 2 * self.n):
+                raise ValueError("coordinates must be contiguous float64 CUDA tensors with 2n elements")
+        info = Info()
+        _check(lib().sls_smooth_noalloc(self.handle, C.c_void_p(xy_in.data_ptr()), C.c_void_p(xy_out.data_ptr()),
+                                        int(max_iter), float(tol), None if stream is None else C.c_void_p(int(stream)),
+                                        C.byref(info)), "sls_smooth_noalloc")
         return info.as_dict()
 
     def coords(self) -> np.ndarray:

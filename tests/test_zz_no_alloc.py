@@ -1,0 +1,85 @@
+"""sls_smooth_noalloc: the entry point for callers that cannot allocate device
+memory while they smooth (inside a stream capture, in a loop that must not
+synchronise the device through cudaMalloc/cudaFree, or under a host
+application that owns the whole memory budget).  It must give the same
+coordinates and statistics as sls_smooth, bit for bit, call after call,
+although every call reuses the same fixed scratch array.
+
+This file is collected last so that a failure here stops a -x run only after
+every other test has run; it also passes alone in a fresh process."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import meshgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1502_00355_gb300 as sls
+    sls.build()
+    sls.lib()
+    return sls, torch
+
+
+def _reference(sls, mesh, kernel, max_iter, tol):
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=kernel) as g:
+        info = g.smooth(max_iter, tol)
+        return g.coords(), info
+
+
+@pytest.mark.parametrize("kernel", ["auto", "fp64"])
+def test_noalloc_matches_smooth_on_consecutive_calls(env, kernel):
+    sls, torch = env
+    L = sls.lib()
+    mesh = meshgen.jittered_grid(300, 200, 0.35, 2024, numbering="morton")
+    g = sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=kernel)
+    # two calls in a row with different lengths: the second must not see the
+    # first call's statistics (the array is cleared per call)
+    for max_iter, tol in [(40, 1e-6), (17, 0.0), (300, 1e-7)]:
+        ref_xy, ref_info = _reference(sls, mesh, kernel, max_iter, tol)
+        xy_in = torch.from_numpy(mesh.xy.copy()).cuda()
+        xy_out = torch.empty_like(xy_in)
+        info = sls.Info()
+        st = L.sls_smooth_noalloc(g.handle, C.c_void_p(xy_in.data_ptr()), C.c_void_p(xy_out.data_ptr()),
+                                  max_iter, tol, None, C.byref(info))
+        assert st == 0, L.sls_last_error()
+        torch.cuda.synchronize()
+        got = xy_out.cpu().numpy()
+        assert np.array_equal(got, ref_xy)
+        d = info.as_dict()
+        for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
+            assert d[key] == ref_info[key], key
+    g.close()
+
+
+def test_noalloc_rejects_what_it_cannot_do(env):
+    sls, torch = env
+    L = sls.lib()
+    mesh = meshgen.jittered_grid(20, 20, 0.3, 7)
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary) as g:
+        a = torch.from_numpy(mesh.xy.copy()).cuda()
+        b = torch.empty_like(a)
+        info = sls.Info()
+        st = L.sls_smooth_noalloc(g.handle, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                                  4097, 0.0, None, C.byref(info))
+        assert st == 1 and b"SLS_NOALLOC_MAX_PASSES" in L.sls_last_error()
+        st = L.sls_smooth_noalloc(g.handle, C.c_void_p(a.data_ptr()), C.c_void_p(a.data_ptr()),
+                                  5, 0.0, None, C.byref(info))
+        assert st == 1
+        # zero passes: the output is the input
+        st = L.sls_smooth_noalloc(g.handle, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                                  0, 0.0, None, C.byref(info))
+        assert st == 0 and info.iterations == 0
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, layout="soa") as g:
+        st = L.sls_smooth_noalloc(g.handle, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                                  5, 0.0, None, C.byref(info))
+        assert st == 1
