@@ -119,6 +119,19 @@ def adjacency_words(mesh):
     return int(mesh.n + 2 * deg_plus_tri[free].sum())
 
 
+def reduce_over_ranks(ms: float, updates: float, device="cpu"):
+    """Max of the per-rank timed milliseconds and sum of node-updates over all
+    ranks (replicas), so value = total updates / slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def cpu_oracle_rate(mesh, passes: int):
     """Times `passes` Form-A passes of the OpenMP oracle on all host cores."""
     import oracle
@@ -157,8 +170,123 @@ def run_reference(args, mesh, workload):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args):
+    """Batched form: many meshes of uneven size in one graph launch, against
+    smoothing the same meshes one request at a time (same kernels)."""
+    import torch
+    import paper_1502_00355_gb300 as sls
+    sls.lib()
+    specs = meshgen.batch_specs(args.batch_meshes)
+    meshes = [meshgen.batch_mesh(sp) for sp in specs]
+    iters = [sp[2] for sp in specs]
+    total_nodes = sum(m.n for m in meshes)
+    handles = [sls.Mesh(m.xy, m.tri, m.boundary) for m in meshes]
+    batch = sls.Batch(handles, iters)               # autotunes its block size
+    for _ in range(args.warmup):
+        batch.reset()
+        batch.smooth()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        batch.reset()
+        t0 = time.perf_counter()
+        infos = batch.smooth()                       # one cudaGraphLaunch, returns when done
+        times.append(time.perf_counter() - t0)
+    updates = sum(m.n * inf["iterations"] for m, inf in zip(meshes, infos))
+    batched = updates * len(times) / sum(times)
+    got = [batch.coords(j) for j in range(len(meshes))]
+    # one request at a time: the same meshes, each smoothed by its own calls
+    batch.reset()
+    t0 = time.perf_counter()
+    for h, it in zip(handles, iters):
+        h.smooth(it)
+    per_req_s = time.perf_counter() - t0
+    per_request = updates / per_req_s
+    same = all(np.array_equal(h.coords(), g) for h, g in zip(handles, got))
+    out = {"metric": "node-updates/s (batched)", "value": batched, "unit": "node-updates/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"batch{len(meshes)}_logu1K-256K_aspect1-4_iters10-100", "meshes": len(meshes),
+                      "total_nodes": total_nodes, "block": None},
+           "per_request": {"value": per_request, "unit": "node-updates/s", "seconds": per_req_s},
+           "speedup_vs_per_request": batched / per_request, "identical_results": bool(same)}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """Served form: a Poisson stream of smoothing requests through the
+    continuous-batching server, against one request at a time (FIFO)."""
+    import threading
+    import torch
+    import paper_1502_00355_gb300 as sls
+    sls.lib()
+    reqs = meshgen.serve_requests(args.serve_requests, rate=args.serve_rate, hi=args.serve_max_n)
+    meshes = [meshgen.jittered_grid(nx, ny, 0.3, seed, numbering="morton") for _, nx, ny, _, seed in reqs]
+    caps = [r[3] for r in reqs]
+    arrivals = [r[0] for r in reqs]
+    srv = sls.Server()
+    # warm-up: a few requests through the server
+    for m, cap in zip(meshes[:4], caps[:4]):
+        srv.wait(srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=TOL))
+    srv.close()
+    srv = sls.Server()
+    results = [None] * len(reqs)
+    ids = [None] * len(reqs)
+    t_start = time.perf_counter()
+
+    def submitter():
+        for k, (m, cap) in enumerate(zip(meshes, caps)):
+            delay = arrivals[k] - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            ids[k] = srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=TOL)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    for k in range(len(reqs)):
+        results[k] = srv.wait(ids[k])
+    wall = time.perf_counter() - t_start
+    st = srv.stats()
+    srv.close()
+    updates = sum(m.n * r[1]["iterations"] for m, r in zip(meshes, results))
+    # FIFO baseline: one job on the GPU at a time, same kernels, same arrivals
+    lat = []
+    t_start = time.perf_counter()
+    busy = 0.0
+    same = True
+    for k, (m, cap) in enumerate(zip(meshes, caps)):
+        now = time.perf_counter() - t_start
+        if now < arrivals[k]:
+            time.sleep(arrivals[k] - now)
+        t0 = time.perf_counter()
+        with sls.Mesh(m.xy, m.tri, m.boundary) as g:
+            inf = g.smooth(cap, TOL)
+            xy = g.coords()
+        busy += time.perf_counter() - t0
+        lat.append(1e3 * (time.perf_counter() - t_start - arrivals[k]))
+        same = same and np.array_equal(xy, results[k][0]) and inf["iterations"] == results[k][1]["iterations"]
+    fifo_wall = time.perf_counter() - t_start
+    out = {"metric": "node-updates/s (served)", "value": updates / wall, "unit": "node-updates/s", "n_gpus": 1,
+           "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"serve{len(reqs)}_poisson{args.serve_rate:g}_logu1K-{args.serve_max_n}_cap10-200_tol1e-9",
+                      "requests": len(reqs)},
+           "served": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "node_updates_per_s_busy": st["node_updates_per_s"],
+                      "wall_s": wall},
+           "fifo": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "node_updates_per_s": updates / fifo_wall, "wall_s": fifo_wall, "busy_s": busy},
+           "speedup_vs_fifo": (updates / wall) / (updates / fifo_wall), "identical_results": bool(same)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve"])
+    ap.add_argument("--batch-meshes", type=int, default=2048)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-max-n", type=int, default=262144)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -171,6 +299,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     mesh = meshgen.large_grid(args.nx, args.ny)
     workload = WORKLOAD if (args.nx, args.ny) == (4096, 4096) else f"grid{args.nx}x{args.ny}_jitter0.35_pull5pct_morton"
@@ -226,11 +358,7 @@ def main():
     torch.cuda.synchronize()
     pass_ms = e0.elapsed_time(e1) / max(1, info_k["iterations"])
 
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    total_updates = mesh.n * passes * world
+    ms_max, total_updates = reduce_over_ranks(ms, float(mesh.n * passes), device="cuda")
     value = total_updates / (ms_max * 1e-3)
 
     # end to end through the public API with host buffers: create (H2D of the

@@ -85,7 +85,7 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
     M->cur = 0;
     M->block = o.block_size;
     M->screened = o.kernel != SLS_KERNEL_FP64;
-    if (M->screened && (M->block < 64 || M->block > 512)) M->block = 256;
+    if (M->screened && (M->block < 64 || M->block > 256)) M->block = 256;  // the screened kernel is built for <= 256
     M->grid = device_sm_count() * (M->screened ? pass_screened_occupancy(o.layout, M->block)
                                                : pass_fp64_occupancy(o.layout, M->block));
     return SLS_OK;

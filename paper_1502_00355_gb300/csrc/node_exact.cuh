@@ -10,12 +10,13 @@ namespace sls {
 
 // Flags of a deferred node (screened kernel -> exact path).
 constexpr uint32_t kHasCentre = 1u;   // cx, cy hold the node's centre
-constexpr uint32_t kSingleOld = 2u;   // only triangle t_old can attain q_old
-constexpr uint32_t kSingleNew = 4u;   // only triangle t_new can attain q_new
+constexpr uint32_t kMasked = 2u;      // masks name every triangle that can attain q_old / q_new
 
 struct Deferred {
     int32_t node;
-    uint32_t flags;  // bits 0..2 as above, bits 8..15 t_old, bits 16..23 t_new
+    uint32_t flags;
+    uint32_t masks;  // bits 0..15: candidates for q_old, bits 16..31: for q_new
+    uint32_t pad;
     double cx, cy;
 };
 
@@ -35,13 +36,14 @@ __device__ __forceinline__ double alpha_with(const PassArgs &a, const uint32_t *
 
 // Exact update of free node i.  Without kHasCentre the centre is computed
 // here (neighbour sum in stored order, then IEEE division).  q_old / q_new are
-// the minima over all incident triangles, or the single candidate triangle
-// when the flags say the screen proved no other triangle can attain the
-// minimum.  Writes the node and its decision; returns the squared move bits
-// (0 if not accepted) and whether it was accepted.
+// the minima over all incident triangles or, with kMasked, over the triangles
+// in the masks: the screen proved every other triangle's FP64 alpha larger
+// than some masked one, so the minimum is the same.  Writes the node and its
+// decision; returns the squared move bits (0 if not accepted) and whether it
+// was accepted.
 template <int LAYOUT>
-__device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint32_t flags, double cx,
-                                             double cy, unsigned long long &d2_bits, bool &accepted)
+__device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint32_t flags, uint32_t masks,
+                                             double cx, double cy, unsigned long long &d2_bits, bool &accepted)
 {
     const uint32_t off = __ldg(a.node_off + i);
     const uint32_t meta = __ldg(a.adj + off);
@@ -63,20 +65,34 @@ __device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint3
     }
 
     double q_old = 0.0, q_new = 0.0;
-    if (flags & kSingleOld) {
-        q_old = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + ((flags >> 8) & 0xffu)), p.x, p.y);
-    } else {
-        for (uint32_t t = 0; t < ntri; ++t) {
+    if (flags & kMasked) {
+        // Each lane walks its own candidates, so a warp runs as many
+        // evaluations as its busiest lane has candidates, not one per triangle.
+        uint32_t m = masks & 0xffffu;
+        bool first = true;
+        while (m) {
+            const uint32_t t = (uint32_t)__ffs((int)m) - 1u;
+            m &= m - 1u;
             const double q = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + t), p.x, p.y);
-            if (t == 0 || q < q_old) q_old = q;
+            if (first || q < q_old) q_old = q;
+            first = false;
         }
-    }
-    if (flags & kSingleNew) {
-        q_new = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + ((flags >> 16) & 0xffu)), cx, cy);
+        m = masks >> 16;
+        first = true;
+        while (m) {
+            const uint32_t t = (uint32_t)__ffs((int)m) - 1u;
+            m &= m - 1u;
+            const double q = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + t), cx, cy);
+            if (first || q < q_new) q_new = q;
+            first = false;
+        }
     } else {
         for (uint32_t t = 0; t < ntri; ++t) {
-            const double q = alpha_with<LAYOUT>(a, nb, __ldg(nb + deg + t), cx, cy);
-            if (t == 0 || q < q_new) q_new = q;
+            const uint32_t code = __ldg(nb + deg + t);
+            const double qo = alpha_with<LAYOUT>(a, nb, code, p.x, p.y);
+            const double qn = alpha_with<LAYOUT>(a, nb, code, cx, cy);
+            if (t == 0 || qo < q_old) q_old = qo;
+            if (t == 0 || qn < q_new) q_new = qn;
         }
     }
 

@@ -44,55 +44,63 @@ __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 __device__ __forceinline__ int bexp(unsigned long long b) { return (int)((b >> 52) & 0x7ffull); }
 
-// +0.0 or a finite normal number (the fast path's domain).
-__device__ __forceinline__ bool in_domain(unsigned long long b)
+// The fast path works on rings whose coordinates (of one axis) all carry the
+// sign of the node's own coordinate and have exponents in [F, F+4] with
+// F = (node's exponent) - 3; zeros of that sign are allowed.  Such values are
+// exact multiples of u = 2^(F-1075) below 2^57 u, so sums of up to 16 of them
+// stay below 2^61 u and no partial sum changes sign.
+
+// Magnitude of b in units of u, if b belongs to the ring's window and sign.
+__device__ __forceinline__ bool ring_mag(unsigned long long b, unsigned sgn, int F, unsigned long long &M)
 {
-    const int e = bexp(b);
-    return b == 0ull || (e != 0 && e != 0x7ff);
+    if ((unsigned)(b >> 63) != sgn) return false;
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+    if (mag == 0ull) {
+        M = 0ull;
+        return true;
+    }
+    const unsigned sh = (unsigned)((int)(mag >> 52) - F);
+    if (sh > 4u) return false;  // outside the window (also subnormal, inf, NaN)
+    M = ((mag & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << sh;
+    return true;
 }
 
-// Value b as an integer multiple of 2^(F-1075); b must be 0 or have its
-// exponent in [F, F+4].
-__device__ __forceinline__ long long to_frame(unsigned long long b, int F)
+// Round a magnitude below 2^61 to 53 significant bits, ties to even: the
+// rounding of one FP64 addition of two same-signed values whose exact sum is
+// a * u.  All dropped bits lie in the low 32-bit word.
+__device__ __forceinline__ unsigned long long rn53u(unsigned long long a)
 {
-    if (b == 0ull) return 0ll;
-    const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << (bexp(b) - F);
-    return (b >> 63) ? -m : m;
+    const unsigned hi = (unsigned)(a >> 32);
+    if (hi < (1u << 21)) return a;  // at most 53 significant bits already
+    const unsigned sh = 11u - (unsigned)__clz(hi);  // bit length - 53, in 1..8
+    const unsigned lo = (unsigned)a;
+    const unsigned unit = 1u << sh;
+    const unsigned rem = lo & (unit - 1u), half = unit >> 1;
+    const unsigned long long r = a - rem;
+    const bool up = rem > half || (rem == half && (lo & unit) != 0u);
+    return up ? r + unit : r;
 }
 
-// Round an int64 (|S| < 2^63) to 53 significant bits, ties to even: the
-// rounding of one FP64 addition whose exact result is S * 2^(F-1075).
-__device__ __forceinline__ long long rn53(long long S)
+// The double (-1)^sgn * a * u for a magnitude a with at most 53 significant
+// bits (a = 0 gives a zero of that sign).
+__device__ __forceinline__ double mag_to_double(unsigned long long a, unsigned sgn, int F)
 {
-    unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
-    if (a < (1ull << 53)) return S;
-    const int sh = 11 - __clzll((long long)a);  // bit length - 53, in 1..10
-    const unsigned long long unit = 1ull << sh;
-    const unsigned long long rem = a & (unit - 1ull);
-    const unsigned long long half = unit >> 1;
-    a -= rem;
-    if (rem > half || (rem == half && (a & unit))) a += unit;
-    return S < 0 ? -(long long)a : (long long)a;
-}
-
-// The double S * 2^(F-1075), for S with at most 53 significant bits.
-__device__ __forceinline__ double from_frame(long long S, int F)
-{
-    if (S == 0) return 0.0;
-    const unsigned long long sign = S < 0 ? 0x8000000000000000ull : 0ull;
-    const unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+    const unsigned long long sb = (unsigned long long)sgn << 63;
+    if (a == 0ull) return bitsd(sb);
     const int L = 64 - __clzll((long long)a);
     const unsigned long long m = L > 53 ? (a >> (L - 53)) : (a << (53 - L));
-    return bitsd(sign | ((unsigned long long)(F + L - 53) << 52) | (m & 0xFFFFFFFFFFFFFull));
+    return bitsd(sb | ((unsigned long long)(F + L - 53) << 52) | (m & 0xFFFFFFFFFFFFFull));
 }
 
-// cx - px as FP64 computes it: the frame difference D when it is exactly
-// representable (|D| < 2^53), otherwise one FP64 subtraction.
-__device__ __forceinline__ double exact_diff(long long D, int F, double cx, double px)
+// c - p as FP64 computes it, for c and p of the ring's sign with magnitudes
+// C and P: the exact difference when it fits 53 bits, else one subtraction.
+__device__ __forceinline__ double exact_diff(unsigned long long C, unsigned long long P, unsigned sgn, int F,
+                                             double c, double p)
 {
-    const unsigned long long a = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
-    if (a >= (1ull << 53)) return __dsub_rn(cx, px);
-    return from_frame(D, F);
+    const bool neg = C < P;
+    const unsigned long long d = neg ? P - C : C - P;
+    if (d >= (1ull << 53)) return __dsub_rn(c, p);
+    return mag_to_double(d, sgn ^ (neg ? 1u : 0u), F);
 }
 
 // Markstein's correctly rounded division by a small integer N (y = RN(1/N)).
@@ -118,6 +126,14 @@ __device__ __forceinline__ float scaled_float(long long D, int scale)
     return __uint_as_float(sign | ((unsigned)e << 23) | (m & 0x7fffffu));
 }
 
+// Local coordinate (X - M) * u of a ring value with magnitude X, for a node
+// with magnitude M, as a float with the ring's sign applied.
+__device__ __forceinline__ float local_coord(unsigned long long X, unsigned long long M, int F, unsigned sgn)
+{
+    const float f = scaled_float((long long)(X - M), F);
+    return __uint_as_float(__float_as_uint(f) ^ (sgn << 31));
+}
+
 // Screening constants (unit roundoff e = 2^-24).  Local coordinates carry a
 // relative error below 2e (truncation to 24 bits).  For a triangle whose
 // three vertices' local coordinates are bounded by R, with g = R^2 / s (s the
@@ -138,18 +154,23 @@ constexpr float kC3 = 1.5f * 1.0096f * 146.0f * kEps;
 constexpr float kGMax = 1000.0f;
 constexpr float kTwoSqrt3f = 3.46410161514f;
 
-// Interval [lo, hi] of the minimum over triangles and the candidate test.
+// Interval [minL, minU] that holds the FP64 minimum over the triangles, and
+// a candidate set for the exact path.  If every triangle other than the one
+// with the lowest upper end U has its lower end L above that U, that triangle
+// alone attains the minimum.  Otherwise the set is every triangle whose L was
+// at most the running minimum of U when it was seen: the running minimum only
+// decreases, so this is a superset of {t : L_t <= final minU}, which is safe
+// (the exact path takes the FP64 minimum over it).
 struct MinTrack {
-    float minU, minLother, lofBest;
-    int best;
+    float minU, minL, minLother, lofBest;
+    uint32_t mask, best;
     __device__ __forceinline__ void init()
     {
-        minU = FLT_MAX;
-        minLother = FLT_MAX;
-        lofBest = FLT_MAX;
-        best = 0;
+        minU = minL = minLother = lofBest = FLT_MAX;
+        mask = 0u;
+        best = 0u;
     }
-    __device__ __forceinline__ void add(float a, float b, int t)
+    __device__ __forceinline__ void add(float a, float b, uint32_t t)
     {
         const float U = a + b, L = a - b;
         if (U < minU) {
@@ -160,9 +181,10 @@ struct MinTrack {
         } else {
             minLother = fminf(minLother, L);
         }
+        minL = fminf(minL, L);
+        mask |= (L <= minU ? 1u : 0u) << t;
     }
-    __device__ __forceinline__ float lo() const { return fminf(minLother, lofBest); }
-    __device__ __forceinline__ bool single() const { return minLother > minU; }
+    __device__ __forceinline__ uint32_t candidates() const { return minLother > minU ? (1u << best) : mask; }
 };
 
 // FP32 alpha and its bound for the triangle (X, A, B) in that orientation;
@@ -197,6 +219,8 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
     bool defer = false;
     d.node = (int32_t)i;
     d.flags = 0u;
+    d.masks = 0u;
+    d.pad = 0u;
     d.cx = 0.0;
     d.cy = 0.0;
     const uint32_t off = __ldg(a.node_off + i);
@@ -208,52 +232,41 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
         const uint32_t *nb = a.adj + off + 1;
         const double2 p = Coords<LAYOUT>::get(a.in, a.n, i);
         const unsigned long long px = dbits(p.x), py = dbits(p.y);
-        bool ok = deg <= (uint32_t)kFastMax && ntri <= (uint32_t)kFastMax && in_domain(px) && in_domain(py);
-        // exponent window of the ring (zeros impose nothing)
-        int hx = px ? bexp(px) : 0, lx = px ? bexp(px) : 2047;
-        int hy = py ? bexp(py) : 0, ly = py ? bexp(py) : 2047;
-        if (ok) {
-            for (uint32_t k = 0; k < deg; ++k) {
-                const double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
-                const unsigned long long vx = dbits(v.x), vy = dbits(v.y);
-                ok = ok && in_domain(vx) && in_domain(vy);
-                if (vx) { hx = max(hx, bexp(vx)); lx = min(lx, bexp(vx)); }
-                if (vy) { hy = max(hy, bexp(vy)); ly = min(ly, bexp(vy)); }
-            }
+        const unsigned sgx = (unsigned)(px >> 63), sgy = (unsigned)(py >> 63);
+        const int Fx = bexp(px) - 3, Fy = bexp(py) - 3;
+        unsigned long long Mx = 0ull, My = 0ull, Sx = 0ull, Sy = 0ull;
+        bool ok = deg <= (uint32_t)kFastMax && ntri <= (uint32_t)kFastMax && Fx >= 960 && Fx <= 1070 &&
+                  Fy >= 960 && Fy <= 1070 && ring_mag(px, sgx, Fx, Mx) && ring_mag(py, sgy, Fy, My);
+        // Eq. 2 on the integer pipe, in the stored summation order
+        for (uint32_t k = 0; ok && k < deg; ++k) {
+            const double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
+            unsigned long long X = 0ull, Y = 0ull;
+            ok = ring_mag(dbits(v.x), sgx, Fx, X) && ring_mag(dbits(v.y), sgy, Fy, Y);
+            Sx = k ? rn53u(Sx + X) : X;
+            Sy = k ? rn53u(Sy + Y) : Y;
+            loc[k * nthr] = make_float2(local_coord(X, Mx, Fx, sgx), local_coord(Y, My, Fy, sgy));
         }
-        const int Fx = hx ? hx - 4 : 1019, Fy = hy ? hy - 4 : 1019;
-        ok = ok && lx >= Fx && ly >= Fy && Fx >= 960 && Fx <= 1070 && Fy >= 960 && Fy <= 1070;
         if (!ok) {
             defer = true;  // exact path computes everything
         } else {
-            // Eq. 2 on the integer pipe, in the stored summation order
-            const long long Mx = to_frame(px, Fx), My = to_frame(py, Fy);
-            long long Sx = 0, Sy = 0;
-            for (uint32_t k = 0; k < deg; ++k) {
-                const double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
-                const long long X = to_frame(dbits(v.x), Fx), Y = to_frame(dbits(v.y), Fy);
-                Sx = k ? rn53(Sx + X) : X;
-                Sy = k ? rn53(Sy + Y) : Y;
-                loc[k * nthr] = make_float2(scaled_float(X - Mx, Fx), scaled_float(Y - My, Fy));
-            }
             const double fd = c_degree[deg], y = c_recip[deg];
-            const double cx = div_small(from_frame(Sx, Fx), fd, y);
-            const double cy = div_small(from_frame(Sy, Fy), fd, y);
+            const double cx = div_small(mag_to_double(Sx, sgx, Fx), fd, y);
+            const double cy = div_small(mag_to_double(Sy, sgy, Fy), fd, y);
             d.cx = cx;
             d.cy = cy;
             d.flags = kHasCentre;
             const unsigned long long cbx = dbits(cx), cby = dbits(cy);
+            unsigned long long Cmx = 0ull, Cmy = 0ull;
             if (cbx == px && cby == py) {
                 // the centre is the node itself: q_new == q_old exactly
                 const bool acc = !a.strict;
                 Coords<LAYOUT>::put(a.out, a.n, i, p);
                 if (a.accept) a.accept[i] = acc ? 1 : 0;
                 nacc += acc ? 1ull : 0ull;
-            } else if (!((cbx == 0ull || bexp(cbx) >= Fx) && (cby == 0ull || bexp(cby) >= Fy))) {
+            } else if (!(ring_mag(cbx, sgx, Fx, Cmx) && ring_mag(cby, sgy, Fy, Cmy))) {
                 defer = true;
             } else {
-                const long long DCx = to_frame(cbx, Fx) - Mx, DCy = to_frame(cby, Fy) - My;
-                const float Cx = scaled_float(DCx, Fx), Cy = scaled_float(DCy, Fy);
+                const float Cx = local_coord(Cmx, Mx, Fx, sgx), Cy = local_coord(Cmy, My, Fy, sgy);
                 const float rC = fmaxf(fabsf(Cx), fabsf(Cy));
                 MinTrack o, nw;
                 o.init();
@@ -269,19 +282,20 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
                     const float rN = fmaxf(rAB, rC);
                     float av, bv;
                     screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, rAB * rAB, sgn, av, bv);
-                    o.add(av, bv, (int)t);
+                    o.add(av, bv, t);
                     screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, rN * rN, sgn, av, bv);
-                    nw.add(av, bv, (int)t);
+                    nw.add(av, bv, t);
                 }
                 // q_new and q_old (FP64) lie in [lo, minU] of their side
-                const float new_lo = nw.lo(), new_hi = nw.minU;
-                const float old_lo = o.lo(), old_hi = o.minU;
+                const float new_lo = nw.minL, new_hi = nw.minU;
+                const float old_lo = o.minL, old_hi = o.minU;
                 if (new_lo > old_hi || new_hi < old_lo) {
                     const bool acc = new_lo > old_hi;
                     double2 outp = p;
                     if (acc) {
                         // cx - px, as FP64 rounds it, from the exact frame difference
-                        const double dx = exact_diff(DCx, Fx, cx, p.x), dy = exact_diff(DCy, Fy, cy, p.y);
+                        const double dx = exact_diff(Cmx, Mx, sgx, Fx, cx, p.x);
+                        const double dy = exact_diff(Cmy, My, sgy, Fy, cy, p.y);
                         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
                         const unsigned long long b2 = dbits(d2);
                         best = b2 > best ? b2 : best;
@@ -292,8 +306,8 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
                     if (a.accept) a.accept[i] = acc ? 1 : 0;
                 } else {
                     defer = true;
-                    d.flags |= (o.single() ? kSingleOld : 0u) | (nw.single() ? kSingleNew : 0u) |
-                               ((uint32_t)o.best << 8) | ((uint32_t)nw.best << 16);
+                    d.flags |= kMasked;
+                    d.masks = o.candidates() | (nw.candidates() << 16);
                 }
             }
         }
@@ -314,7 +328,7 @@ __device__ __forceinline__ void drain_queue(const PassArgs &a, Deferred *wq, int
             const Deferred e = wq[lane];
             unsigned long long b2;
             bool acc;
-            exact_update<LAYOUT>(a, e.node, e.flags, e.cx, e.cy, b2, acc);
+            exact_update<LAYOUT>(a, e.node, e.flags, e.masks, e.cx, e.cy, b2, acc);
             best = b2 > best ? b2 : best;
             nacc += acc ? 1ull : 0ull;
         }
@@ -344,7 +358,7 @@ __device__ __forceinline__ void warp_flush_stats(PassStats *st, unsigned long lo
 }
 
 template <int LAYOUT>
-__global__ void __launch_bounds__(512) pass_screened_kernel(PassArgs a)
+__global__ void __launch_bounds__(256, 3) pass_screened_kernel(PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;

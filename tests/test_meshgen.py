@@ -1,0 +1,61 @@
+"""The synthetic input generator: shapes, seeds and structure the workloads rely on."""
+import numpy as np
+
+import meshgen
+
+
+def test_counts_and_boundary():
+    m = meshgen.jittered_grid(64, 64, 0.3, 1)
+    assert m.n == 4096 and m.m == 7938
+    assert int(m.boundary.sum()) == 4 * 63
+    big = meshgen.jittered_grid(1024, 1024, 0.35, 2)
+    assert big.n == 1048576 and big.m == 2093058
+
+
+def test_triangles_ccw_before_jitter_and_jitter_bounded():
+    m = meshgen.jittered_grid(20, 17, 0.0, 3, numbering="random")
+    a, b, c = (m.xy[m.tri[:, k]] for k in range(3))
+    cross = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    assert (cross > 0).all()
+    j = meshgen.jittered_grid(20, 17, 0.3, 3, numbering="natural")
+    g = meshgen.jittered_grid(20, 17, 0.0, 3, numbering="natural")
+    h = g.meta["h"]
+    d = np.abs(j.xy - g.xy)
+    assert d.max() <= 0.3 * h + 1e-15
+    assert np.array_equal(d[j.boundary == 1], np.zeros_like(d[j.boundary == 1]))
+
+
+def test_seeded_and_numberings_are_permutations():
+    a = meshgen.jittered_grid(30, 40, 0.3, 7, numbering="morton")
+    b = meshgen.jittered_grid(30, 40, 0.3, 7, numbering="morton")
+    assert np.array_equal(a.xy, b.xy) and np.array_equal(a.tri, b.tri)
+    r = meshgen.jittered_grid(30, 40, 0.3, 7, numbering="random")
+    assert np.array_equal(np.sort(a.perm), np.arange(a.n)) and np.array_equal(np.sort(r.perm), np.arange(r.n))
+    assert np.array_equal(meshgen.unpermute(a.xy, a), meshgen.unpermute(r.xy, r))
+
+
+def test_morton_order_is_z_curve():
+    i = np.array([0, 1, 0, 1, 2, 3, 2, 3])
+    j = np.array([0, 0, 1, 1, 0, 0, 1, 1])
+    assert meshgen.morton_order(i, j).tolist() == [0, 1, 2, 3, 4, 5, 6, 7]
+
+
+def test_pull_moves_five_percent_and_caps_step():
+    base = meshgen.jittered_grid(200, 200, 0.35, 11, numbering="natural")
+    pulled = meshgen.jittered_grid(200, 200, 0.35, 11, numbering="natural", pull_fraction=0.05)
+    moved = (pulled.xy != base.xy).any(1)
+    interior = int((base.boundary == 0).sum())
+    assert abs(int(moved.sum()) - round(0.05 * interior)) <= 1
+    step = np.sqrt(((pulled.xy - base.xy) ** 2).sum(1))
+    assert step.max() <= 2 * base.meta["h"] * (1 + 1e-12)
+
+
+def test_batch_and_serve_specs():
+    specs = meshgen.batch_specs(64)
+    assert len(specs) == 64
+    for nx, ny, it, _ in specs:
+        assert 10 <= it <= 100 and nx >= 2 and ny >= 2
+        assert 700 <= nx * ny <= 300000
+    reqs = meshgen.serve_requests(50)
+    t = [r[0] for r in reqs]
+    assert t == sorted(t) and all(10 <= r[3] <= 200 for r in reqs)
