@@ -184,7 +184,8 @@ struct MinTrack {
         minL = fminf(minL, L);
         mask |= (L <= minU ? 1u : 0u) << t;
     }
-    __device__ __forceinline__ uint32_t candidates() const { return minLother > minU ? (1u << best) : mask; }
+    __device__ __forceinline__ bool single() const { return minLother > minU; }
+    __device__ __forceinline__ uint32_t candidates() const { return single() ? (1u << best) : mask; }
 };
 
 // FP32 alpha and its bound for the triangle (X, A, B) in that orientation;
@@ -212,6 +213,52 @@ __device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float
 // Section 3.3.4).  Decided nodes are written and counted here; returns true
 // when the node must be finished by the exact path (d filled in).  loc is
 // this thread's slice of the shared local-coordinate buffer (stride nthr).
+// Second screen, for a node whose two minima are attained by the same single
+// triangle (X, A, B) (X = 0 before the move, X = C after it; sgn gives the
+// stored orientation).  Then q_new - q_old (FP64) differs from the exact
+// alpha(C) - alpha(0) by at most 2 * kE64, and that exact difference is
+//   sgn * K * N / (s_new * s_old),  N = dcr * s_old - cr_old * ds,
+// with dcr = C x (A - B) and ds = 2|C|^2 - 2 C.(A + B) computed directly from
+// the move (no cancellation between two nearly equal qualities).  Error
+// budget (e = 2^-24, local coordinates within 2e of exact, R >= all of
+// |A|, |B|, |C| components, r >= |C| components): dcr 27 e r R, ds 90 e r R,
+// cr_old 12 e R^2, s_old 140 e R^2, s_new 250 e R^2, and the roundings of N.
+// kE64 bounds |FP64 alpha - exact alpha| (about 14.2 units of 2^-53 for
+// |alpha| <= 1, second-order terms included with margin).  Returns +1 when
+// q_new > q_old certainly, -1 when q_new < q_old certainly, 0 otherwise.
+constexpr float kE64 = 4e-15f;
+
+__device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float Cy, float sgn)
+{
+    const float R = fmaxf(fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y))),
+                          fmaxf(fabsf(Cx), fabsf(Cy)));
+    const float r = fmaxf(fabsf(Cx), fabsf(Cy));
+    if (!(R >= 1e-6f && R <= 1e7f)) return 0;  // keep every product a normal float
+    const float bax = B.x - A.x, bay = B.y - A.y;
+    const float ba2 = fmaf(bax, bax, bay * bay);
+    const float cro = fmaf(A.x, B.y, -(A.y * B.x));
+    const float so = fmaf(A.x, A.x, fmaf(A.y, A.y, fmaf(B.x, B.x, fmaf(B.y, B.y, ba2))));
+    const float ax = A.x - Cx, ay = A.y - Cy, bx = B.x - Cx, by = B.y - Cy;
+    const float sn = fmaf(ax, ax, fmaf(ay, ay, fmaf(bx, bx, fmaf(by, by, ba2))));
+    const float dabx = A.x - B.x, daby = A.y - B.y;
+    const float dcr = fmaf(Cx, daby, -(Cy * dabx));
+    const float sabx = A.x + B.x, saby = A.y + B.y;
+    const float t = fmaf(Cx, sabx, Cy * saby);
+    const float c2 = fmaf(Cx, Cx, Cy * Cy);
+    const float ds = 2.0f * (c2 - t);
+    const float N = fmaf(dcr, so, -(cro * ds));
+    const float rR = r * R, R2 = R * R;
+    const float e_dcr = 27.0f * kEps * rR, e_ds = 90.0f * kEps * rR;
+    const float e_cro = 12.0f * kEps * R2, e_so = 140.0f * kEps * R2, e_sn = 250.0f * kEps * R2;
+    if (!(so > e_so && sn > e_sn)) return 0;  // degenerate: no information
+    const float adcr = fabsf(dcr), ads = fabsf(ds), acro = fabsf(cro);
+    const float eN = e_dcr * so + (adcr + e_dcr) * e_so + e_cro * ads + (acro + e_cro) * e_ds +
+                     kEps * (adcr * so + 2.0f * acro * ads);
+    const float need = (2.02f * kE64 / kTwoSqrt3f) * (sn + e_sn) * (so + e_so);
+    if (!(fabsf(N) - 2.0f * eN > need)) return 0;
+    return ((N > 0.0f) == (sgn > 0.0f)) ? 1 : -1;
+}
+
 template <int LAYOUT>
 __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2 *loc, int nthr, Deferred &d,
                                             unsigned long long &best, unsigned long long &nacc)
@@ -289,8 +336,14 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
                 // q_new and q_old (FP64) lie in [lo, minU] of their side
                 const float new_lo = nw.minL, new_hi = nw.minU;
                 const float old_lo = o.minL, old_hi = o.minU;
-                if (new_lo > old_hi || new_hi < old_lo) {
-                    const bool acc = new_lo > old_hi;
+                int verdict = new_lo > old_hi ? 1 : (new_hi < old_lo ? -1 : 0);
+                if (verdict == 0 && o.single() && nw.single() && o.best == nw.best) {
+                    const uint32_t c = __ldg(nb + deg + o.best);
+                    verdict = diff_screen(loc[code_first(c) * nthr], loc[code_second(c) * nthr], Cx, Cy,
+                                          code_slot(c) == 1u ? -1.0f : 1.0f);
+                }
+                if (verdict != 0) {
+                    const bool acc = verdict > 0;
                     double2 outp = p;
                     if (acc) {
                         // cx - px, as FP64 rounds it, from the exact frame difference
