@@ -100,6 +100,39 @@ struct Coords<1> {  // SoA: x[n] then y[n]
     }
 };
 
+// The same coordinates as raw 64-bit patterns.  Code that only moves or
+// inspects coordinates uses these, so no value is ever held in an FP64
+// register (the compiler copies FP64 registers with FP64-pipe instructions).
+template <int LAYOUT>
+struct CoordBits;
+
+template <>
+struct CoordBits<0> {
+    static __device__ __forceinline__ ulonglong2 get(const double *p, int64_t, int64_t i)
+    {
+        return __ldg(reinterpret_cast<const ulonglong2 *>(p) + i);
+    }
+    static __device__ __forceinline__ void put(double *p, int64_t, int64_t i, ulonglong2 v)
+    {
+        reinterpret_cast<ulonglong2 *>(p)[i] = v;
+    }
+};
+
+template <>
+struct CoordBits<1> {
+    static __device__ __forceinline__ ulonglong2 get(const double *p, int64_t n, int64_t i)
+    {
+        const unsigned long long *q = reinterpret_cast<const unsigned long long *>(p);
+        return make_ulonglong2(__ldg(q + i), __ldg(q + n + i));
+    }
+    static __device__ __forceinline__ void put(double *p, int64_t n, int64_t i, ulonglong2 v)
+    {
+        unsigned long long *q = reinterpret_cast<unsigned long long *>(p);
+        q[i] = v.x;
+        q[n + i] = v.y;
+    }
+};
+
 // Lee and Lo's alpha of the triangle (a, b, c) in its stored vertex order:
 // 2*sqrt(3) * cross / ((|e1|^2 + |e2|^2) + |e3|^2), e1 = b-a, e2 = c-a,
 // e3 = c-b, cross = e1x*e2y - e1y*e2x; 0 when the edge sum is not positive.

@@ -17,7 +17,7 @@ struct Deferred {
     uint32_t flags;
     uint32_t masks;  // bits 0..15: candidates for q_old, bits 16..31: for q_new
     uint32_t pad;
-    double cx, cy;
+    unsigned long long cx, cy;  // the centre, as FP64 bit patterns
 };
 
 // alpha of incident triangle `code` of node i with node i placed at (x, y).
@@ -43,8 +43,10 @@ __device__ __forceinline__ double alpha_with(const PassArgs &a, const uint32_t *
 // was accepted.
 template <int LAYOUT>
 __device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint32_t flags, uint32_t masks,
-                                             double cx, double cy, unsigned long long &d2_bits, bool &accepted)
+                                             unsigned long long cxb, unsigned long long cyb,
+                                             unsigned long long &d2_bits, bool &accepted)
 {
+    double cx = __longlong_as_double((long long)cxb), cy = __longlong_as_double((long long)cyb);
     const uint32_t off = __ldg(a.node_off + i);
     const uint32_t meta = __ldg(a.adj + off);
     const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(1024) pass_fp64_kernel(PassArgs a)
         }
         unsigned long long bits;
         bool ok;
-        exact_update<LAYOUT>(a, i, 0u, 0u, 0.0, 0.0, bits, ok);
+        exact_update<LAYOUT>(a, i, 0u, 0u, 0ull, 0ull, bits, ok);
         best = bits > best ? bits : best;
         nacc += ok ? 1ull : 0ull;
     }

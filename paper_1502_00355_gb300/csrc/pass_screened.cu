@@ -1,15 +1,13 @@
 // pass_screened.cu -- the fast exact Jacobi pass of Smart Laplacian smoothing.
 //
 // Same results, bit for bit, as the FP64 pass (Eq. 2 with the accept test of
-// Section 3.3.4); what changes is which pipe does the work.  GB300 issues about
-// two FP64 operations per SM per clock against ~128 FP32/INT32, so:
+// Section 3.3.4); what changes is which pipe does which work.  GB300 issues
+// about two FP64 operations per SM per clock against ~128 FP32/INT32, so the
+// FP64 pipe does only what decides the result's bits, and the rest moves to
+// the FP32 and integer pipes:
 //
-//  1. The neighbour sums (Eq. 2) are carried out exactly on the integer pipe.
-//     Every coordinate of the node's one-ring is a multiple of one power of two
-//     u = 2^(F-1075) when the ring's exponents lie in [F, F+4]; the running sum
-//     is an int64 multiple of u, rounded to 53 significant bits
-//     (round-to-nearest-even) after every addition -- exactly what each FP64
-//     addition does.
+//  1. The neighbour sums (Eq. 2) are the FP64 additions themselves, in the
+//     stored summation order.
 //  2. The division by the degree uses Markstein's correction (Markstein, IBM J.
 //     Res. Dev. 34(1), 1990): q0 = s*y with y = RN(1/N), r = fma(-q0, N, s)
 //     (exact), q = fma(r, y, q0), which is the correctly rounded s/N.  Three
@@ -17,16 +15,22 @@
 //  3. If the centre equals the node's position bit for bit, q_new == q_old
 //     exactly and no quality needs evaluating.
 //  4. Otherwise alpha of every incident triangle, before and after the move, is
-//     evaluated in FP32 in a frame centred on the node (local coordinates are
-//     exact integer differences, rounded once to FP32) together with a
-//     rigorous bound on its distance to the exact alpha of the FP64 inputs,
-//     wide enough to also cover the FP64 evaluation's own rounding.  When the
-//     intervals of q_new and q_old are disjoint the FP64 decision is known.
-//  5. Nodes the screen cannot decide (near-ties), or whose ring leaves the
-//     fast path's limits, go to a per-warp queue in shared memory and are
-//     finished by the exact FP64 update 32 at a time, so the narrow FP64
-//     pipe is not wasted on idle lanes; only the triangles the screen could
-//     not rule out as the minimum are evaluated in FP64.
+//     evaluated in FP32 in a frame centred on the node, with a rigorous bound
+//     on its distance to the exact alpha of the FP64 inputs, wide enough to
+//     also cover the FP64 evaluation's own rounding.  The neighbours' local
+//     coordinates come from float head/tail splits of the doubles; the
+//     centre's offset from one exact FP64 subtraction.  When the intervals of
+//     q_new and q_old are disjoint the FP64 decision is known.
+//  5. If one triangle alone attains both minima, a second screen takes the
+//     sign of alpha(centre) - alpha(node) from a formula in the move itself
+//     (no cancellation) and decides all but rounding-level ties.
+//  6. What is left goes to a per-warp queue in shared memory and is finished
+//     by the exact FP64 update 32 nodes at a time (dense lanes on the narrow
+//     FP64 pipe), on the triangles the screen could not rule out.
+//
+// Coordinates are moved as 64-bit patterns, never held in FP64 registers
+// unless they take part in FP64 arithmetic: the compiler copies FP64
+// registers with FP64-pipe instructions.
 #include <cfloat>
 
 #include "kernels.h"
@@ -42,117 +46,76 @@ __constant__ double c_degree[kFastMax + 1]; // N as a double
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
-__device__ __forceinline__ int bexp(unsigned long long b) { return (int)((b >> 52) & 0x7ffull); }
 
-// The fast path works on rings whose coordinates (of one axis) all carry the
-// sign of the node's own coordinate and have exponents in [F, F+4] with
-// F = (node's exponent) - 3; zeros of that sign are allowed.  Such values are
-// exact multiples of u = 2^(F-1075) below 2^57 u, so sums of up to 16 of them
-// stay below 2^61 u and no partial sum changes sign.
-
-// Magnitude of b in units of u, if b belongs to the ring's window and sign.
-__device__ __forceinline__ bool ring_mag(unsigned long long b, unsigned sgn, int F, unsigned long long &M)
-{
-    if ((unsigned)(b >> 63) != sgn) return false;
-    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
-    if (mag == 0ull) {
-        M = 0ull;
-        return true;
-    }
-    const unsigned sh = (unsigned)((int)(mag >> 52) - F);
-    if (sh > 4u) return false;  // outside the window (also subnormal, inf, NaN)
-    M = ((mag & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << sh;
-    return true;
-}
-
-// Round a magnitude below 2^61 to 53 significant bits, ties to even: the
-// rounding of one FP64 addition of two same-signed values whose exact sum is
-// a * u.  All dropped bits lie in the low 32-bit word.
-__device__ __forceinline__ unsigned long long rn53u(unsigned long long a)
-{
-    const unsigned hi = (unsigned)(a >> 32);
-    if (hi < (1u << 21)) return a;  // at most 53 significant bits already
-    const unsigned sh = 11u - (unsigned)__clz(hi);  // bit length - 53, in 1..8
-    const unsigned lo = (unsigned)a;
-    const unsigned unit = 1u << sh;
-    const unsigned rem = lo & (unit - 1u), half = unit >> 1;
-    const unsigned long long r = a - rem;
-    const bool up = rem > half || (rem == half && (lo & unit) != 0u);
-    return up ? r + unit : r;
-}
-
-// The double (-1)^sgn * a * u for a magnitude a with at most 53 significant
-// bits (a = 0 gives a zero of that sign).
-__device__ __forceinline__ double mag_to_double(unsigned long long a, unsigned sgn, int F)
-{
-    const unsigned long long sb = (unsigned long long)sgn << 63;
-    if (a == 0ull) return bitsd(sb);
-    const int L = 64 - __clzll((long long)a);
-    const unsigned long long m = L > 53 ? (a >> (L - 53)) : (a << (53 - L));
-    return bitsd(sb | ((unsigned long long)(F + L - 53) << 52) | (m & 0xFFFFFFFFFFFFFull));
-}
-
-// c - p as FP64 computes it, for c and p of the ring's sign with magnitudes
-// C and P: the exact difference when it fits 53 bits, else one subtraction.
-__device__ __forceinline__ double exact_diff(unsigned long long C, unsigned long long P, unsigned sgn, int F,
-                                             double c, double p)
-{
-    const bool neg = C < P;
-    const unsigned long long d = neg ? P - C : C - P;
-    if (d >= (1ull << 53)) return __dsub_rn(c, p);
-    return mag_to_double(d, sgn ^ (neg ? 1u : 0u), F);
-}
-
-// Markstein's correctly rounded division by a small integer N (y = RN(1/N)).
+// Correctly rounded s / N for a small integer N (y = RN(1/N)): Markstein's
+// correction when nothing can underflow or overflow (s's biased exponent in
+// [63, 2000]), IEEE division otherwise (subnormal or huge sums, inf, NaN).
 __device__ __forceinline__ double div_small(double s, double N, double y)
 {
+    const unsigned e = (unsigned)(dbits(s) >> 52) & 0x7ffu;
+    if (e - 63u > 1937u) return __ddiv_rn(s, N);
     const double q0 = __dmul_rn(s, y);
     const double r = __fma_rn(-q0, N, s);
     return __fma_rn(r, y, q0);
 }
 
-// D * 2^(scale - 1075) as a float, truncated to 24 significant bits
-// (relative error below 2^-23), built with integer operations only: int64 to
-// float conversions would occupy the FP64 pipe.
-__device__ __forceinline__ float scaled_float(long long D, int scale)
+// Splits the double with bit pattern b into a float head (its sign, exponent
+// and top 24 significant bits) and a float tail (the next 23 bits), with
+// integer operations only; head + tail is within 2^-46 |x| of x.  Returns
+// false outside [2^-80, 2^127) in magnitude (zero is allowed) or for
+// subnormal, infinite or NaN values.
+__device__ __forceinline__ bool head_tail(unsigned long long b, float &hd, float &tl)
 {
-    if (D == 0) return 0.0f;
-    const unsigned sign = D < 0 ? 0x80000000u : 0u;
-    const unsigned long long a = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
-    const int L = 64 - __clzll((long long)a);
-    const unsigned m = L > 24 ? (unsigned)(a >> (L - 24)) : (unsigned)(a << (24 - L));
-    // value = m * 2^(L - 24) * 2^(scale - 1075); m has its top bit at 23
-    const int e = L - 1 + scale - 1075 + 127;
-    return __uint_as_float(sign | ((unsigned)e << 23) | (m & 0x7fffffu));
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    if ((hw & 0x7fffffffu) == 0u && lw == 0u) {
+        hd = 0.0f;
+        tl = 0.0f;
+        return true;
+    }
+    if (e < 943u || e > 1149u) return false;
+    const unsigned sign = hw & 0x80000000u;
+    hd = __uint_as_float(sign | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    // tail bits 28..6 of the low word, value t * 2^(E - 46): exact in FP32
+    const float t = __uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)) - 8388608.0f;
+    tl = __uint_as_float(__float_as_uint(t * __uint_as_float((e - 942u) << 23)) | sign);
+    return true;
 }
 
-// Local coordinate (X - M) * u of a ring value with magnitude X, for a node
-// with magnitude M, as a float with the ring's sign applied.
-__device__ __forceinline__ float local_coord(unsigned long long X, unsigned long long M, int F, unsigned sgn)
+// FP32 value of a double, truncated to 24 significant bits (relative error
+// below 2^-23), built with integer operations; zero outside the float range.
+__device__ __forceinline__ float trunc_float(double v)
 {
-    const float f = scaled_float((long long)(X - M), F);
-    return __uint_as_float(__float_as_uint(f) ^ (sgn << 31));
+    const unsigned long long b = dbits(v);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    if (e < 897u || e > 1150u) return 0.0f;
+    return __uint_as_float((hw & 0x80000000u) | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
 }
 
-// Screening constants (unit roundoff e = 2^-24).  Local coordinates carry a
-// relative error below 2e (truncation to 24 bits).  For a triangle whose
-// three vertices' local coordinates are bounded by R, with g = R^2 / s (s the
-// computed sum of squared edges), the FP32 alpha differs from the exact alpha
-// of the FP64 inputs by at most
-//   e * (13.2 |a| + (211.3 + 146 |a|) g) * (1 + 1.1 e (6.1 + 146 g)),
-// (edge errors 6.01 e R; cross 61 e R^2; edge sum 6.1 e s + 146 e R^2; FP32
+// Screening constants (unit roundoff e = 2^-24).  A local coordinate of a
+// neighbour carries an error below 2e|X| + 2^-44 M (head/tail truncation; M
+// bounds the node's coordinate magnitude plus the ring's extent), which is
+// below 3e R wherever R >= 2^-20 M; the screen requires that.  The centre's
+// local coordinate is within 2e of its exact value (relative).  For a
+// triangle whose three vertices' local coordinates are bounded by R, with
+// g = R^2 / s (s the computed sum of squared edges), the FP32 alpha differs
+// from the exact alpha of the FP64 inputs by at most
+//   e * (13.2 |a| + (264.6 + 194 |a|) g) * (1 + 1.1 e (6.1 + 194 g)),
+// (edge errors 8 e R; cross 76.4 e R^2; edge sum 6.1 e s + 194 e R^2; FP32
 // constant, products and approximate reciprocal 7.1 e |a|), valid for
-// g <= kGMax, where the last factor is at most 1.0096.  The constants carry a
+// g <= kGMax, where the last factor is at most 1.0128.  The constants carry a
 // further factor 1.5.  Because g >= 1/24 (every squared edge is at most
-// 8 R^2), half of the resulting bound exceeds 6e-7: more than the FP64
+// 8 R^2), half of the resulting bound exceeds 8e-7: more than the FP64
 // evaluation's own error (< 2e-15 for |alpha| <= 1) plus the FP32 rounding of
 // a +- b and of the comparisons, so those need no separate term.
 constexpr float kEps = 5.9604645e-8f;
-constexpr float kC1 = 1.5f * 1.0096f * 13.2f * kEps;
-constexpr float kC2 = 1.5f * 1.0096f * 211.3f * kEps;
-constexpr float kC3 = 1.5f * 1.0096f * 146.0f * kEps;
+constexpr float kC1 = 1.5f * 1.0128f * 13.2f * kEps;
+constexpr float kC2 = 1.5f * 1.0128f * 264.6f * kEps;
+constexpr float kC3 = 1.5f * 1.0128f * 194.0f * kEps;
 constexpr float kGMax = 1000.0f;
 constexpr float kTwoSqrt3f = 3.46410161514f;
+constexpr float kLocalRange = 1048576.0f;  // 2^20: R * 2^20 >= M keeps the head/tail error below e R
 
 // Interval [minL, minU] that holds the FP64 minimum over the triangles, and
 // a candidate set for the exact path.  If every triangle other than the one
@@ -189,9 +152,10 @@ struct MinTrack {
 };
 
 // FP32 alpha and its bound for the triangle (X, A, B) in that orientation;
-// R2 bounds the squared local coordinates of its three vertices.
+// R2 bounds the squared local coordinates of its three vertices, M2 the
+// squared coordinate magnitude of the node.
 __device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float Ay, float Bx, float By,
-                                             float ba2, float R2, float sgn, float &a, float &b)
+                                             float ba2, float R2, float M2, float sgn, float &a, float &b)
 {
     const float e1x = Ax - Xx, e1y = Ay - Xy, e2x = Bx - Xx, e2y = By - Xy;
     const float cr = fmaf(e1x, e2y, -(e1y * e2x));
@@ -201,18 +165,15 @@ __device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float
     const float g = R2 * inv;
     const float aa = fabsf(a);
     b = fmaf(kC1, aa, fmaf(kC3, aa, kC2) * g);
-    // degenerate, unscreenable, or so small / large that FP32 under- or
-    // overflow could escape the relative bound: no information
-    if (!(s > 0.0f) || !(g <= kGMax) || !(R2 >= 1e-28f) || !(R2 <= 1e30f)) {
+    // degenerate, unscreenable, too small against the coordinates, or so
+    // small / large that FP32 under- or overflow could escape the bound
+    if (!(s > 0.0f) || !(g <= kGMax) || !(R2 >= 1e-28f) || !(R2 <= 1e30f) ||
+        !(R2 * (kLocalRange * kLocalRange) >= M2)) {
         a = 0.0f;
         b = FLT_MAX;
     }
 }
 
-// Screens free or fixed node i of one mesh (Eq. 2 and the accept test of
-// Section 3.3.4).  Decided nodes are written and counted here; returns true
-// when the node must be finished by the exact path (d filled in).  loc is
-// this thread's slice of the shared local-coordinate buffer (stride nthr).
 // Second screen, for a node whose two minima are attained by the same single
 // triangle (X, A, B) (X = 0 before the move, X = C after it; sgn gives the
 // stored orientation).  Then q_new - q_old (FP64) differs from the exact
@@ -220,20 +181,22 @@ __device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float
 //   sgn * K * N / (s_new * s_old),  N = dcr * s_old - cr_old * ds,
 // with dcr = C x (A - B) and ds = 2|C|^2 - 2 C.(A + B) computed directly from
 // the move (no cancellation between two nearly equal qualities).  Error
-// budget (e = 2^-24, local coordinates within 2e of exact, R >= all of
-// |A|, |B|, |C| components, r >= |C| components): dcr 27 e r R, ds 90 e r R,
-// cr_old 12 e R^2, s_old 140 e R^2, s_new 250 e R^2, and the roundings of N.
-// kE64 bounds |FP64 alpha - exact alpha| (about 14.2 units of 2^-53 for
-// |alpha| <= 1, second-order terms included with margin).  Returns +1 when
-// q_new > q_old certainly, -1 when q_new < q_old certainly, 0 otherwise.
+// budget (e = 2^-24; A, B within 3 e R, C within 2 e |C|; R >= every local
+// coordinate of the triangle and the centre, r >= |C| components): dcr
+// 32 e r R, ds 100 e r R, cr_old 16 e R^2, s_old 170 e R^2, s_new 280 e R^2,
+// and the roundings of N.  kE64 bounds |FP64 alpha - exact alpha| (about 14.2
+// units of 2^-53 for |alpha| <= 1, second-order terms included with margin).
+// Returns +1 when q_new > q_old certainly, -1 when q_new < q_old certainly,
+// 0 otherwise.
 constexpr float kE64 = 4e-15f;
 
-__device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float Cy, float sgn)
+__device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float Cy, float sgn, float M2)
 {
     const float R = fmaxf(fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y))),
                           fmaxf(fabsf(Cx), fabsf(Cy)));
     const float r = fmaxf(fabsf(Cx), fabsf(Cy));
     if (!(R >= 1e-6f && R <= 1e7f)) return 0;  // keep every product a normal float
+    if (!(R * R * (kLocalRange * kLocalRange) >= M2)) return 0;
     const float bax = B.x - A.x, bay = B.y - A.y;
     const float ba2 = fmaf(bax, bax, bay * bay);
     const float cro = fmaf(A.x, B.y, -(A.y * B.x));
@@ -248,8 +211,8 @@ __device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float C
     const float ds = 2.0f * (c2 - t);
     const float N = fmaf(dcr, so, -(cro * ds));
     const float rR = r * R, R2 = R * R;
-    const float e_dcr = 27.0f * kEps * rR, e_ds = 90.0f * kEps * rR;
-    const float e_cro = 12.0f * kEps * R2, e_so = 140.0f * kEps * R2, e_sn = 250.0f * kEps * R2;
+    const float e_dcr = 32.0f * kEps * rR, e_ds = 100.0f * kEps * rR;
+    const float e_cro = 16.0f * kEps * R2, e_so = 170.0f * kEps * R2, e_sn = 280.0f * kEps * R2;
     if (!(so > e_so && sn > e_sn)) return 0;  // degenerate: no information
     const float adcr = fabsf(dcr), ads = fabsf(ds), acro = fabsf(cro);
     const float eN = e_dcr * so + (adcr + e_dcr) * e_so + e_cro * ads + (acro + e_cro) * e_ds +
@@ -259,113 +222,110 @@ __device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float C
     return ((N > 0.0f) == (sgn > 0.0f)) ? 1 : -1;
 }
 
+// Screens free or fixed node i of one mesh (Eq. 2 and the accept test of
+// Section 3.3.4).  Decided nodes are written and counted here; returns true
+// when the node must be finished by the exact path (d filled in).  loc is
+// this thread's slice of the shared local-coordinate buffer (stride nthr).
 template <int LAYOUT>
 __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2 *loc, int nthr, Deferred &d,
                                             unsigned long long &best, unsigned long long &nacc)
 {
-    bool defer = false;
     d.node = (int32_t)i;
     d.flags = 0u;
     d.masks = 0u;
     d.pad = 0u;
-    d.cx = 0.0;
-    d.cy = 0.0;
+    d.cx = 0ull;
+    d.cy = 0ull;
     const uint32_t off = __ldg(a.node_off + i);
     const uint32_t meta = __ldg(a.adj + off);
     if (meta & kMetaFixed) {
         if (a.accept) a.accept[i] = 0;
-    } else {
-        const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
-        const uint32_t *nb = a.adj + off + 1;
-        const double2 p = Coords<LAYOUT>::get(a.in, a.n, i);
-        const unsigned long long px = dbits(p.x), py = dbits(p.y);
-        const unsigned sgx = (unsigned)(px >> 63), sgy = (unsigned)(py >> 63);
-        const int Fx = bexp(px) - 3, Fy = bexp(py) - 3;
-        unsigned long long Mx = 0ull, My = 0ull, Sx = 0ull, Sy = 0ull;
-        bool ok = deg <= (uint32_t)kFastMax && ntri <= (uint32_t)kFastMax && Fx >= 960 && Fx <= 1070 &&
-                  Fy >= 960 && Fy <= 1070 && ring_mag(px, sgx, Fx, Mx) && ring_mag(py, sgy, Fy, My);
-        // Eq. 2 on the integer pipe, in the stored summation order
-        for (uint32_t k = 0; ok && k < deg; ++k) {
-            const double2 v = Coords<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
-            unsigned long long X = 0ull, Y = 0ull;
-            ok = ring_mag(dbits(v.x), sgx, Fx, X) && ring_mag(dbits(v.y), sgy, Fy, Y);
-            Sx = k ? rn53u(Sx + X) : X;
-            Sy = k ? rn53u(Sy + Y) : Y;
-            loc[k * nthr] = make_float2(local_coord(X, Mx, Fx, sgx), local_coord(Y, My, Fy, sgy));
-        }
-        if (!ok) {
-            defer = true;  // exact path computes everything
-        } else {
-            const double fd = c_degree[deg], y = c_recip[deg];
-            const double cx = div_small(mag_to_double(Sx, sgx, Fx), fd, y);
-            const double cy = div_small(mag_to_double(Sy, sgy, Fy), fd, y);
-            d.cx = cx;
-            d.cy = cy;
-            d.flags = kHasCentre;
-            const unsigned long long cbx = dbits(cx), cby = dbits(cy);
-            unsigned long long Cmx = 0ull, Cmy = 0ull;
-            if (cbx == px && cby == py) {
-                // the centre is the node itself: q_new == q_old exactly
-                const bool acc = !a.strict;
-                Coords<LAYOUT>::put(a.out, a.n, i, p);
-                if (a.accept) a.accept[i] = acc ? 1 : 0;
-                nacc += acc ? 1ull : 0ull;
-            } else if (!(ring_mag(cbx, sgx, Fx, Cmx) && ring_mag(cby, sgy, Fy, Cmy))) {
-                defer = true;
-            } else {
-                const float Cx = local_coord(Cmx, Mx, Fx, sgx), Cy = local_coord(Cmy, My, Fy, sgy);
-                const float rC = fmaxf(fabsf(Cx), fabsf(Cy));
-                MinTrack o, nw;
-                o.init();
-                nw.init();
-                for (uint32_t t = 0; t < ntri; ++t) {
-                    const uint32_t c = __ldg(nb + deg + t);
-                    const float2 A = loc[code_first(c) * nthr];
-                    const float2 B = loc[code_second(c) * nthr];
-                    const float sgn = code_slot(c) == 1u ? -1.0f : 1.0f;
-                    const float bax = B.x - A.x, bay = B.y - A.y;
-                    const float ba2 = fmaf(bax, bax, bay * bay);
-                    const float rAB = fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y)));
-                    const float rN = fmaxf(rAB, rC);
-                    float av, bv;
-                    screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, rAB * rAB, sgn, av, bv);
-                    o.add(av, bv, t);
-                    screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, rN * rN, sgn, av, bv);
-                    nw.add(av, bv, t);
-                }
-                // q_new and q_old (FP64) lie in [lo, minU] of their side
-                const float new_lo = nw.minL, new_hi = nw.minU;
-                const float old_lo = o.minL, old_hi = o.minU;
-                int verdict = new_lo > old_hi ? 1 : (new_hi < old_lo ? -1 : 0);
-                if (verdict == 0 && o.single() && nw.single() && o.best == nw.best) {
-                    const uint32_t c = __ldg(nb + deg + o.best);
-                    verdict = diff_screen(loc[code_first(c) * nthr], loc[code_second(c) * nthr], Cx, Cy,
-                                          code_slot(c) == 1u ? -1.0f : 1.0f);
-                }
-                if (verdict != 0) {
-                    const bool acc = verdict > 0;
-                    double2 outp = p;
-                    if (acc) {
-                        // cx - px, as FP64 rounds it, from the exact frame difference
-                        const double dx = exact_diff(Cmx, Mx, sgx, Fx, cx, p.x);
-                        const double dy = exact_diff(Cmy, My, sgy, Fy, cy, p.y);
-                        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                        const unsigned long long b2 = dbits(d2);
-                        best = b2 > best ? b2 : best;
-                        nacc += 1ull;
-                        outp = make_double2(cx, cy);
-                    }
-                    Coords<LAYOUT>::put(a.out, a.n, i, outp);
-                    if (a.accept) a.accept[i] = acc ? 1 : 0;
-                } else {
-                    defer = true;
-                    d.flags |= kMasked;
-                    d.masks = o.candidates() | (nw.candidates() << 16);
-                }
-            }
-        }
+        return false;
     }
-    return defer;
+    const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
+    if (deg > (uint32_t)kFastMax || ntri > (uint32_t)kFastMax) return true;  // exact path does it all
+    const uint32_t *nb = a.adj + off + 1;
+    const ulonglong2 pb = CoordBits<LAYOUT>::get(a.in, a.n, i);
+    float phx, plx, phy, ply;
+    bool ok = head_tail(pb.x, phx, plx) && head_tail(pb.y, phy, ply);
+
+    // Eq. 2: FP64 sums in the stored order; local coordinates on the side
+    ulonglong2 v = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb));
+    double sx = bitsd(v.x), sy = bitsd(v.y);
+    float rn = 0.0f;
+    for (uint32_t k = 0;;) {
+        float hx, lx, hy, ly;
+        ok = ok && head_tail(v.x, hx, lx) && head_tail(v.y, hy, ly);
+        const float2 L = make_float2((hx - phx) + (lx - plx), (hy - phy) + (ly - ply));
+        loc[k * nthr] = L;
+        rn = fmaxf(rn, fmaxf(fabsf(L.x), fabsf(L.y)));
+        if (++k >= deg) break;
+        v = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
+        sx = __dadd_rn(sx, bitsd(v.x));
+        sy = __dadd_rn(sy, bitsd(v.y));
+    }
+    const double fd = c_degree[deg], y = c_recip[deg];
+    const double cxd = div_small(sx, fd, y), cyd = div_small(sy, fd, y);
+    const unsigned long long cbx = dbits(cxd), cby = dbits(cyd);
+    d.cx = cbx;
+    d.cy = cby;
+    d.flags = kHasCentre;
+    if (cbx == pb.x && cby == pb.y) {
+        // the centre is the node itself: q_new == q_old exactly
+        const bool acc = !a.strict;
+        CoordBits<LAYOUT>::put(a.out, a.n, i, pb);
+        if (a.accept) a.accept[i] = acc ? 1 : 0;
+        nacc += acc ? 1ull : 0ull;
+        return false;
+    }
+    if (!ok) return true;
+    // c - p exactly as FP64 rounds it (also the move used for d2)
+    const double dx = __dsub_rn(cxd, bitsd(pb.x)), dy = __dsub_rn(cyd, bitsd(pb.y));
+    const float Cx = trunc_float(dx), Cy = trunc_float(dy);
+    const float rC = fmaxf(fabsf(Cx), fabsf(Cy));
+    const float M = fmaxf(fabsf(phx), fabsf(phy)) * 1.0001f + fmaxf(rn, rC);
+    const float M2 = M * M;
+    MinTrack o, nw;
+    o.init();
+    nw.init();
+    for (uint32_t t = 0; t < ntri; ++t) {
+        const uint32_t c = __ldg(nb + deg + t);
+        const float2 A = loc[code_first(c) * nthr];
+        const float2 B = loc[code_second(c) * nthr];
+        const float sgn = code_slot(c) == 1u ? -1.0f : 1.0f;
+        const float bax = B.x - A.x, bay = B.y - A.y;
+        const float ba2 = fmaf(bax, bax, bay * bay);
+        const float rAB = fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y)));
+        const float rN = fmaxf(rAB, rC);
+        float av, bv;
+        screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, rAB * rAB, M2, sgn, av, bv);
+        o.add(av, bv, t);
+        screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, rN * rN, M2, sgn, av, bv);
+        nw.add(av, bv, t);
+    }
+    // q_new and q_old (FP64) lie in [minL, minU] of their side
+    int verdict = nw.minL > o.minU ? 1 : (nw.minU < o.minL ? -1 : 0);
+    if (verdict == 0 && o.single() && nw.single() && o.best == nw.best) {
+        const uint32_t c = __ldg(nb + deg + o.best);
+        verdict = diff_screen(loc[code_first(c) * nthr], loc[code_second(c) * nthr], Cx, Cy,
+                              code_slot(c) == 1u ? -1.0f : 1.0f, M2);
+    }
+    if (verdict == 0) {
+        d.flags |= kMasked;
+        d.masks = o.candidates() | (nw.candidates() << 16);
+        return true;
+    }
+    const bool acc = verdict > 0;
+    ulonglong2 outp = pb;
+    if (acc) {
+        const unsigned long long b2 = dbits(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        best = b2 > best ? b2 : best;
+        nacc += 1ull;
+        outp = make_ulonglong2(cbx, cby);
+    }
+    CoordBits<LAYOUT>::put(a.out, a.n, i, outp);
+    if (a.accept) a.accept[i] = acc ? 1 : 0;
+    return false;
 }
 
 // Finishes one full warp's worth of deferred nodes (lane k takes entry k)
