@@ -67,9 +67,12 @@ __device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint3
     }
 
     double q_old = 0.0, q_new = 0.0;
-    if (flags & kMasked) {
+    if ((flags & kMasked) && ntri <= 16u) {
         // Each lane walks its own candidates, so a warp runs as many
         // evaluations as its busiest lane has candidates, not one per triangle.
+        // Bits at or above ntri never name a triangle of this node.
+        const uint32_t valid = (1u << ntri) - 1u;
+        masks &= valid | (valid << 16);
         uint32_t m = masks & 0xffffu;
         bool first = true;
         while (m) {

@@ -117,20 +117,15 @@ constexpr float kGMax = 1000.0f;
 constexpr float kTwoSqrt3f = 3.46410161514f;
 constexpr float kLocalRange = 1048576.0f;  // 2^20: R * 2^20 >= M keeps the head/tail error below e R
 
-// Interval [minL, minU] that holds the FP64 minimum over the triangles, and
-// a candidate set for the exact path.  If every triangle other than the one
-// with the lowest upper end U has its lower end L above that U, that triangle
-// alone attains the minimum.  Otherwise the set is every triangle whose L was
-// at most the running minimum of U when it was seen: the running minimum only
-// decreases, so this is a superset of {t : L_t <= final minU}, which is safe
-// (the exact path takes the FP64 minimum over it).
+// Interval [minL, minU] that holds the FP64 minimum over the triangles.  If
+// every triangle other than the one with the lowest upper end U has its lower
+// end L above that U, that triangle alone attains the minimum (single()).
 struct MinTrack {
     float minU, minL, minLother, lofBest;
-    uint32_t mask, best;
+    uint32_t best;
     __device__ __forceinline__ void init()
     {
         minU = minL = minLother = lofBest = FLT_MAX;
-        mask = 0u;
         best = 0u;
     }
     __device__ __forceinline__ void add(float a, float b, uint32_t t)
@@ -145,30 +140,31 @@ struct MinTrack {
             minLother = fminf(minLother, L);
         }
         minL = fminf(minL, L);
-        mask |= (L <= minU ? 1u : 0u) << t;
     }
     __device__ __forceinline__ bool single() const { return minLother > minU; }
-    __device__ __forceinline__ uint32_t candidates() const { return single() ? (1u << best) : mask; }
+    // candidate set for the exact path: the single triangle, or all ntri of them
+    __device__ __forceinline__ uint32_t candidates(uint32_t ntri) const
+    {
+        return single() ? (1u << best) : ((1u << ntri) - 1u);
+    }
 };
 
 // FP32 alpha and its bound for the triangle (X, A, B) in that orientation;
-// R2 bounds the squared local coordinates of its three vertices, M2 the
-// squared coordinate magnitude of the node.
+// R2 bounds the squared local coordinates of its three vertices; sk is the
+// orientation sign times 2 sqrt(3).  The caller has checked that every local
+// coordinate lies in the range where the bound holds (see screen_node).
 __device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float Ay, float Bx, float By,
-                                             float ba2, float R2, float M2, float sgn, float &a, float &b)
+                                             float ba2, float R2, float sk, float &a, float &b)
 {
     const float e1x = Ax - Xx, e1y = Ay - Xy, e2x = Bx - Xx, e2y = By - Xy;
     const float cr = fmaf(e1x, e2y, -(e1y * e2x));
     const float s = fmaf(e1x, e1x, fmaf(e1y, e1y, fmaf(e2x, e2x, fmaf(e2y, e2y, ba2))));
     const float inv = __fdividef(1.0f, s);
-    a = sgn * kTwoSqrt3f * cr * inv;
+    a = sk * cr * inv;
     const float g = R2 * inv;
     const float aa = fabsf(a);
     b = fmaf(kC1, aa, fmaf(kC3, aa, kC2) * g);
-    // degenerate, unscreenable, too small against the coordinates, or so
-    // small / large that FP32 under- or overflow could escape the bound
-    if (!(s > 0.0f) || !(g <= kGMax) || !(R2 >= 1e-28f) || !(R2 <= 1e30f) ||
-        !(R2 * (kLocalRange * kLocalRange) >= M2)) {
+    if (!(s > 0.0f) || !(g <= kGMax)) {  // degenerate or unscreenable: no information
         a = 0.0f;
         b = FLT_MAX;
     }
@@ -252,13 +248,15 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
     // Eq. 2: FP64 sums in the stored order; local coordinates on the side
     ulonglong2 v = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb));
     double sx = bitsd(v.x), sy = bitsd(v.y);
-    float rn = 0.0f;
+    float rn = 0.0f, rmin = FLT_MAX;  // largest / smallest neighbour offset (max norm)
     for (uint32_t k = 0;;) {
         float hx, lx, hy, ly;
         ok = ok && head_tail(v.x, hx, lx) && head_tail(v.y, hy, ly);
         const float2 L = make_float2((hx - phx) + (lx - plx), (hy - phy) + (ly - ply));
         loc[k * nthr] = L;
-        rn = fmaxf(rn, fmaxf(fabsf(L.x), fabsf(L.y)));
+        const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
+        rn = fmaxf(rn, rl);
+        rmin = fminf(rmin, rl);
         if (++k >= deg) break;
         v = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
         sx = __dadd_rn(sx, bitsd(v.x));
@@ -285,6 +283,10 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
     const float rC = fmaxf(fabsf(Cx), fabsf(Cy));
     const float M = fmaxf(fabsf(phx), fabsf(phy)) * 1.0001f + fmaxf(rn, rC);
     const float M2 = M * M;
+    // Every triangle's R is at least rmin and at most max(rn, rC): inside this
+    // range FP32 products neither under- nor overflow and the head/tail error
+    // stays below e R, so the per-triangle bounds hold.
+    if (!(rmin >= 1e-14f && fmaxf(rn, rC) <= 1e15f && rmin * kLocalRange >= M)) return true;
     MinTrack o, nw;
     o.init();
     nw.init();
@@ -292,15 +294,15 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
         const uint32_t c = __ldg(nb + deg + t);
         const float2 A = loc[code_first(c) * nthr];
         const float2 B = loc[code_second(c) * nthr];
-        const float sgn = code_slot(c) == 1u ? -1.0f : 1.0f;
+        const float sk = code_slot(c) == 1u ? -kTwoSqrt3f : kTwoSqrt3f;
         const float bax = B.x - A.x, bay = B.y - A.y;
         const float ba2 = fmaf(bax, bax, bay * bay);
         const float rAB = fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y)));
         const float rN = fmaxf(rAB, rC);
         float av, bv;
-        screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, rAB * rAB, M2, sgn, av, bv);
+        screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, rAB * rAB, sk, av, bv);
         o.add(av, bv, t);
-        screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, rN * rN, M2, sgn, av, bv);
+        screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, rN * rN, sk, av, bv);
         nw.add(av, bv, t);
     }
     // q_new and q_old (FP64) lie in [minL, minU] of their side
@@ -312,7 +314,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
     }
     if (verdict == 0) {
         d.flags |= kMasked;
-        d.masks = o.candidates() | (nw.candidates() << 16);
+        d.masks = o.candidates(ntri) | (nw.candidates(ntri) << 16);
         return true;
     }
     const bool acc = verdict > 0;
