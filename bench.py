@@ -364,14 +364,16 @@ def main():
     # end to end through the public API with host buffers: create (H2D of the
     # inputs, adjacency build), smooth, read the coordinates back (D2H)
     e2e_times = []
-    out_host = np.empty_like(mesh.xy)
+    pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    xy_h, tri_h, bnd_h = pinned(mesh.xy), pinned(mesh.tri), pinned(mesh.boundary)
+    out_host = torch.empty(mesh.xy.shape, dtype=torch.float64).pin_memory().numpy()
     e2e_passes = 0
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=args.kernel) as h:
+        with sls.Mesh(xy_h, tri_h, bnd_h, kernel=args.kernel) as h:
             inf = h.smooth(MAX_PASSES, TOL)
-            out_host[:] = h.coords()
+            h.coords(out=out_host)
         e2e_times.append(time.perf_counter() - t0)
         e2e_passes += inf["iterations"]
     e2e_value = mesh.n * e2e_passes * world / sum(e2e_times) if e2e_times else None

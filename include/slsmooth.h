@@ -81,6 +81,9 @@ typedef struct sls_options {
     int32_t block_size;    /* threads per block; 0 = library default                         */
     int32_t l2_window;     /* 1: L2 persisting access window over the coordinates            */
     int32_t passes_per_check; /* passes launched between host checks of the stop rule; 0 = 16 */
+    int32_t host_build;    /* 1: build the adjacency on the host; 0: on the device (default;
+                              the host build is still used for nodes in more than 32
+                              triangles)                                                     */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle    */
 } sls_options;
 

@@ -33,7 +33,8 @@ STATUS_NAMES = {0: "ok", 1: "invalid", 2: "nonmanifold", 3: "oom", 4: "cuda", 5:
 class Options(C.Structure):
     _fields_ = [("accept_strict", C.c_int32), ("copy_back", C.c_int32), ("layout", C.c_int32),
                 ("kernel", C.c_int32), ("record_accept", C.c_int32), ("block_size", C.c_int32),
-                ("l2_window", C.c_int32), ("passes_per_check", C.c_int32), ("stream", C.c_void_p)]
+                ("l2_window", C.c_int32), ("passes_per_check", C.c_int32), ("host_build", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -110,7 +111,7 @@ def _p(a: np.ndarray | None):
 
 
 def make_options(*, strict=False, copy_back=False, layout="aos", kernel="auto", record_accept=False,
-                 block_size=0, l2_window=False, passes_per_check=0, stream=None) -> Options:
+                 block_size=0, l2_window=False, passes_per_check=0, host_build=False, stream=None) -> Options:
     o = Options()
     lib().sls_default_options(C.byref(o))
     o.accept_strict = int(bool(strict))
@@ -121,6 +122,7 @@ def make_options(*, strict=False, copy_back=False, layout="aos", kernel="auto", 
     o.block_size = int(block_size)
     o.l2_window = int(bool(l2_window))
     o.passes_per_check = int(passes_per_check)
+    o.host_build = int(bool(host_build))
     o.stream = None if stream is None else C.c_void_p(int(stream))
     return o
 
@@ -187,8 +189,13 @@ class Mesh:
                                         C.byref(info)), "sls_smooth_noalloc")
         return info.as_dict()
 
-    def coords(self) -> np.ndarray:
-        out = np.empty((self.n, 2), np.float64)
+    def coords(self, out=None) -> np.ndarray:
+        """Current coordinates as a (n, 2) float64 array (written into `out`
+        when given, e.g. a pinned buffer)."""
+        if out is None:
+            out = np.empty((self.n, 2), np.float64)
+        elif not (out.dtype == np.float64 and out.flags.c_contiguous and out.size == 2 * self.n):
+            raise ValueError("out must be a contiguous float64 array with 2n elements")
         _check(lib().sls_get_coords(self.handle, _p(out), 0), "sls_get_coords")
         return out
 

@@ -33,7 +33,7 @@ int device_sm_count()
     return sms > 0 ? sms : 1;
 }
 
-static sls_options g_defaults = {0, 0, 0, SLS_KERNEL_AUTO, 0, 0, 0, 16, nullptr};
+static sls_options g_defaults = {0, 0, 0, SLS_KERNEL_AUTO, 0, 0, 0, 16, 0, nullptr};
 
 sls_options resolve_options(const sls_options *opt)
 {
@@ -90,12 +90,20 @@ sls_status sls_mesh_create(const double *xy, int64_t n, const int32_t *tri, int6
     sls_options o = resolve_options(opt);
     sls_status st = check_options(o);
     if (st != SLS_OK) return st;
-    HostMesh hm;
-    st = build_host_mesh(xy, n, tri, m, boundary, hm);
-    if (st != SLS_OK) return st;
+    if (!xy || !tri) return fail(SLS_ERR_INVALID, "xy and tri must not be NULL");
+    if (n < 3) return fail(SLS_ERR_INVALID, "a mesh needs at least 3 nodes");
+    if (m < 1) return fail(SLS_ERR_INVALID, "a mesh needs at least 1 triangle");
+    if (n >= (int64_t(1) << 31) || m >= (int64_t(1) << 31))
+        return fail(SLS_ERR_INVALID, "n and m must be below 2^31");
     sls_mesh *M = new (std::nothrow) sls_mesh();
     if (!M) return fail(SLS_ERR_OOM, "host allocation failed");
-    st = mesh_upload(M, hm, xy, tri, o);
+    if (o.host_build) {
+        HostMesh hm;
+        st = build_host_mesh(xy, n, tri, m, boundary, hm);
+        if (st == SLS_OK) st = mesh_upload(M, hm, xy, tri, o);
+    } else {
+        st = mesh_create_on_device(M, xy, n, tri, m, boundary, o);
+    }
     if (st != SLS_OK) {
         mesh_release(M);
         delete M;

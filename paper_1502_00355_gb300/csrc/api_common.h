@@ -40,6 +40,13 @@ sls_status check_options(const sls_options &o);
 
 sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const int32_t *tri,
                        const sls_options &o);
+// Uploads coordinates and triangles and builds the adjacency on the device
+// (host build as a fallback for very high-valence nodes).
+sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const int32_t *tri, int64_t m,
+                                 const uint8_t *boundary, const sls_options &o);
+// Device adjacency build (mesh_build_gpu.cu); SLS_ERR_NOT_FOUND = use the host build.
+sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
+                             cudaStream_t s);
 void mesh_release(sls_mesh *M);
 sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info);
 sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device);

@@ -43,6 +43,9 @@ struct HostMesh {
     std::vector<uint8_t> fixed;        // n
 };
 
+// sqrt((xmax - xmin)^2 + (ymax - ymin)^2), the bounding-box diagonal D.
+double bbox_diagonal(double xmin, double xmax, double ymin, double ymax);
+
 // Validates the mesh and builds the adjacency stream (neighbour finding and
 // constraints).  Uses up to `threads` host threads (0 = hardware concurrency).
 sls_status build_host_mesh(const double *xy, int64_t n, const int32_t *tri, int64_t m,

@@ -51,6 +51,13 @@ void parallel_for_nodes(int64_t n, int threads, F &&body)
 
 }  // namespace
 
+double bbox_diagonal(double xmin, double xmax, double ymin, double ymax)
+{
+    const double wx = xmax - xmin, wy = ymax - ymin;
+    const double wx2 = wx * wx, wy2 = wy * wy;
+    return std::sqrt(wx2 + wy2);
+}
+
 sls_status build_host_mesh(const double *xy, int64_t n, const int32_t *tri, int64_t m,
                            const uint8_t *boundary, HostMesh &out, int threads)
 {
@@ -188,9 +195,7 @@ sls_status build_host_mesh(const double *xy, int64_t n, const int32_t *tri, int6
         ymin = y < ymin ? y : ymin;
         ymax = y > ymax ? y : ymax;
     }
-    double wx = xmax - xmin, wy = ymax - ymin;
-    double wx2 = wx * wx, wy2 = wy * wy;
-    out.diag = std::sqrt(wx2 + wy2);
+    out.diag = bbox_diagonal(xmin, xmax, ymin, ymax);
     out.n = n;
     out.m = m;
     out.n_free = n_free;

@@ -1,0 +1,460 @@
+// mesh_build_gpu.cu -- the adjacency build of sls_mesh_create on the device.
+//
+// Same output, word for word, as the host build in mesh_build.cpp (Section
+// 3.3.2: neighbours and incident triangles; Section 3.3.3: constraints), with
+// the work spread over one thread per triangle or per node instead of the
+// paper's single GPU thread:
+//   1. validate triangles and coordinates;
+//   2. count the incidences of every node, exclusive scan;
+//   3. scatter (node, triangle) incidences;
+//   4. per node: sort its incident triangles, collect the other vertices of
+//      each, sort and de-duplicate them while counting how many triangles
+//      share each edge (1 = boundary edge, > 2 = non-manifold), order the
+//      neighbours for summation (ascending x, y, id) and size its word group;
+//   5. exclusive scan of the word counts -> node offsets;
+//   6. per node: write the meta word, the neighbours and the triangle codes;
+//   7. bounding box and free-node count.
+// Nodes with more than kMaxInc incident triangles are left to the host build
+// (the whole mesh then takes the host path).
+#include <cstring>
+#include <vector>
+
+#include "api_common.h"
+#include "kernels.h"
+
+namespace sls {
+
+namespace {
+
+constexpr int kMaxInc = 32;  // incident triangles per node handled on the device
+
+enum : unsigned { kErrRange = 1u, kErrRepeat = 2u, kErrFinite = 4u, kErrManifold = 8u, kErrTooMany = 16u };
+
+__global__ void validate_tri_kernel(const int32_t *__restrict__ tri, int64_t m, int64_t n, unsigned *flags,
+                                    unsigned long long *first)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += stride) {
+        const int32_t a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+        const bool range = a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n;
+        const bool rep = a == b || a == c || b == c;
+        if (range || rep) {
+            atomicOr(flags, range ? kErrRange : kErrRepeat);
+            // the first bad triangle; at equal index the range error comes first
+            atomicMin(first, (unsigned long long)t * 2ull + (range ? 0ull : 1ull));
+        }
+    }
+}
+
+__global__ void validate_xy_kernel(const unsigned long long *__restrict__ xy, int64_t n2, unsigned *flags,
+                                   unsigned long long *first)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += stride) {
+        if (((xy[k] >> 52) & 0x7ffull) == 0x7ffull) {
+            atomicOr(flags, kErrFinite);
+            atomicMin(first, (unsigned long long)k);
+        }
+    }
+}
+
+__global__ void count_kernel(const int32_t *__restrict__ tri, int64_t m3, unsigned *cnt)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m3; k += stride)
+        atomicAdd(cnt + tri[k], 1u);
+}
+
+__global__ void scatter_kernel(const int32_t *__restrict__ tri, int64_t m3, const unsigned *__restrict__ ptr,
+                               unsigned *cursor, int32_t *inc)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m3; k += stride) {
+        const int32_t v = tri[k];
+        const unsigned slot = atomicAdd(cursor + v, 1u);
+        inc[ptr[v] + slot] = (int32_t)(k / 3);
+    }
+}
+
+// Ascending (x, y, id) with the comparisons of the host build.
+__device__ __forceinline__ bool canon_less(double xa, double ya, int32_t a, double xb, double yb, int32_t b)
+{
+    if (xa < xb) return true;
+    if (xb < xa) return false;
+    if (ya < yb) return true;
+    if (yb < ya) return false;
+    return a < b;
+}
+
+__global__ void node_pass1_kernel(int64_t n, const double2 *__restrict__ xy, const int32_t *__restrict__ tri,
+                                  const unsigned *__restrict__ ptr, int32_t *inc, const uint8_t *boundary,
+                                  int32_t *nbtmp, unsigned *words, uint8_t *fixed_out, unsigned *deg_out,
+                                  unsigned *flags)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned s = ptr[i], e = ptr[i + 1], nt = e - s;
+        if (nt > (unsigned)kMaxInc) {
+            atomicOr(flags, kErrTooMany);
+            words[i] = 1u;
+            fixed_out[i] = 1;
+            deg_out[i] = 0u;
+            continue;
+        }
+        int32_t tl[kMaxInc];
+        for (unsigned k = 0; k < nt; ++k) {
+            const int32_t t = inc[s + k];
+            unsigned j = k;
+            while (j > 0 && tl[j - 1] > t) {
+                tl[j] = tl[j - 1];
+                --j;
+            }
+            tl[j] = t;
+        }
+        for (unsigned k = 0; k < nt; ++k) inc[s + k] = tl[k];
+        // the other two vertices of every incident triangle, sorted by id
+        int32_t rec[2 * kMaxInc];
+        unsigned r = 0;
+        for (unsigned k = 0; k < nt; ++k) {
+            for (int c = 0; c < 3; ++c) {
+                const int32_t v = tri[3 * (int64_t)tl[k] + c];
+                if (v == (int32_t)i) continue;
+                unsigned j = r++;
+                while (j > 0 && rec[j - 1] > v) {
+                    rec[j] = rec[j - 1];
+                    --j;
+                }
+                rec[j] = v;
+            }
+        }
+        bool open_edge = r == 0;
+        unsigned deg = 0;
+        int32_t uq[2 * kMaxInc];
+        for (unsigned k = 0; k < r;) {
+            unsigned f = k;
+            while (f < r && rec[f] == rec[k]) ++f;
+            const unsigned times = f - k;
+            if (times == 1u) open_edge = true;
+            if (times > 2u) atomicOr(flags, kErrManifold);
+            uq[deg++] = rec[k];
+            k = f;
+        }
+        // summation order: ascending (x, y, id) of the creation coordinates
+        double ux[2 * kMaxInc], uy[2 * kMaxInc];
+        for (unsigned k = 0; k < deg; ++k) {
+            const double2 p = xy[uq[k]];
+            const int32_t id = uq[k];
+            unsigned j = k;
+            while (j > 0 && canon_less(p.x, p.y, id, ux[j - 1], uy[j - 1], uq[j - 1])) {
+                ux[j] = ux[j - 1];
+                uy[j] = uy[j - 1];
+                uq[j] = uq[j - 1];
+                --j;
+            }
+            ux[j] = p.x;
+            uy[j] = p.y;
+            uq[j] = id;
+        }
+        for (unsigned k = 0; k < deg; ++k) nbtmp[2ull * s + k] = uq[k];
+        const bool fx = boundary ? (boundary[i] != 0 || r == 0) : open_edge;
+        fixed_out[i] = fx ? 1 : 0;
+        deg_out[i] = deg;
+        words[i] = fx ? 1u : 1u + deg + nt;
+    }
+}
+
+__global__ void node_pass2_kernel(int64_t n, const int32_t *__restrict__ tri, const unsigned *__restrict__ ptr,
+                                  const int32_t *__restrict__ inc, const int32_t *__restrict__ nbtmp,
+                                  const unsigned *__restrict__ deg_in, const uint8_t *__restrict__ fixed_in,
+                                  const uint32_t *__restrict__ node_off, uint32_t *adj)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t *w = adj + node_off[i];
+        if (fixed_in[i]) {
+            w[0] = 0x80000000u;
+            continue;
+        }
+        const unsigned s = ptr[i], nt = ptr[i + 1] - s, deg = deg_in[i];
+        w[0] = (nt << 16) | deg;
+        const int32_t *list = nbtmp + 2ull * s;
+        for (unsigned k = 0; k < deg; ++k) w[1 + k] = (uint32_t)list[k];
+        for (unsigned k = 0; k < nt; ++k) {
+            const int32_t *v = tri + 3 * (int64_t)inc[s + k];
+            uint32_t slot = 0, pos[2] = {0u, 0u}, np = 0;
+            for (int c = 0; c < 3; ++c) {
+                if (v[c] == (int32_t)i) {
+                    slot = (uint32_t)c;
+                    continue;
+                }
+                uint32_t p = 0;
+                while (p + 1 < deg && list[p] != v[c]) ++p;
+                pos[np++] = p;
+            }
+            w[1 + deg + k] = (slot << 30) | (pos[0] << 15) | pos[1];
+        }
+    }
+}
+
+// Order-preserving 64-bit keys of finite doubles, for min / max with atomics.
+__device__ __forceinline__ unsigned long long okey(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void bbox_kernel(const double2 *__restrict__ xy, int64_t n, const uint8_t *__restrict__ fixed,
+                            unsigned long long *keys /* xmin, ymin, xmax, ymax */, unsigned long long *nfree)
+{
+    unsigned long long lo_x = ~0ull, lo_y = ~0ull, hi_x = 0ull, hi_y = 0ull, free_cnt = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double2 p = xy[i];
+        const unsigned long long kx = okey(p.x), ky = okey(p.y);
+        lo_x = kx < lo_x ? kx : lo_x;
+        lo_y = ky < lo_y ? ky : lo_y;
+        hi_x = kx > hi_x ? kx : hi_x;
+        hi_y = ky > hi_y ? ky : hi_y;
+        free_cnt += fixed[i] ? 0ull : 1ull;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t;
+        t = __shfl_xor_sync(0xffffffffu, lo_x, o); lo_x = t < lo_x ? t : lo_x;
+        t = __shfl_xor_sync(0xffffffffu, lo_y, o); lo_y = t < lo_y ? t : lo_y;
+        t = __shfl_xor_sync(0xffffffffu, hi_x, o); hi_x = t > hi_x ? t : hi_x;
+        t = __shfl_xor_sync(0xffffffffu, hi_y, o); hi_y = t > hi_y ? t : hi_y;
+        free_cnt += __shfl_xor_sync(0xffffffffu, free_cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(keys + 0, lo_x);
+        atomicMin(keys + 1, lo_y);
+        atomicMax(keys + 2, hi_x);
+        atomicMax(keys + 3, hi_y);
+        atomicAdd(nfree, free_cnt);
+    }
+}
+
+// Exclusive scan of cnt[0..len) into out[0..len] (out[len] = total), in three
+// steps: per-block sums, a single-block scan of those sums, per-block scans.
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;  // per thread
+
+__global__ void scan_sums_kernel(const unsigned *__restrict__ in, int64_t len, unsigned long long *sums)
+{
+    __shared__ unsigned long long s[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock * kScanItems;
+    unsigned long long acc = 0ull;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t j = base + (int64_t)k * kScanBlock + threadIdx.x;
+        if (j < len) acc += in[j];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = s[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = acc;
+    }
+}
+
+__global__ void scan_offsets_kernel(unsigned long long *sums, int64_t nblocks)
+{
+    // one thread: the block count is small (len / 4096)
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    unsigned long long run = 0ull;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const unsigned long long v = sums[b];
+        sums[b] = run;
+        run += v;
+    }
+    sums[nblocks] = run;
+}
+
+__global__ void scan_final_kernel(const unsigned *__restrict__ in, int64_t len,
+                                  const unsigned long long *__restrict__ offs, uint32_t *out)
+{
+    __shared__ unsigned long long warp_tot[32];
+    __shared__ unsigned long long carry;
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock * kScanItems;
+    if (threadIdx.x == 0) carry = offs[blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t j = base + (int64_t)k * kScanBlock + threadIdx.x;
+        const unsigned long long v = j < len ? in[j] : 0ull;
+        unsigned long long x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long t = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;  // inclusive over warps
+        }
+        __syncthreads();
+        const unsigned long long before = carry + (warp ? warp_tot[warp - 1] : 0ull) + x - v;
+        if (j < len) out[j] = (uint32_t)before;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[31];
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[len] = (uint32_t)offs[gridDim.x];
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { cudaFree(p); }
+};
+
+#define GB_TRY(expr, what)                                  \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+template <class T>
+sls_status dalloc(DevBuf &b, size_t count, T **out, const char *what)
+{
+    cudaError_t e = cudaMalloc(&b.p, sizeof(T) * (count > 0 ? count : 1));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(SLS_ERR_OOM, std::string("device allocation failed: ") + what);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    *out = static_cast<T *>(b.p);
+    return SLS_OK;
+}
+
+// scan of len uint32 values into len+1 offsets; total returned (uint64)
+sls_status scan_u32(const unsigned *in, int64_t len, uint32_t *out, unsigned long long *total, cudaStream_t s)
+{
+    const int64_t per_block = (int64_t)kScanBlock * kScanItems;
+    const int64_t nblocks = (len + per_block - 1) / per_block;
+    DevBuf sb;
+    unsigned long long *sums = nullptr;
+    sls_status st = dalloc(sb, (size_t)nblocks + 1, &sums, "scan");
+    if (st != SLS_OK) return st;
+    if (nblocks > 0) {
+        scan_sums_kernel<<<(unsigned)nblocks, kScanBlock, 0, s>>>(in, len, sums);
+        scan_offsets_kernel<<<1, 1, 0, s>>>(sums, nblocks);
+        scan_final_kernel<<<(unsigned)nblocks, kScanBlock, 0, s>>>(in, len, sums, out);
+        GB_TRY(cudaGetLastError(), "scan");
+        GB_TRY(cudaMemcpyAsync(total, sums + nblocks, sizeof *total, cudaMemcpyDeviceToHost, s), "scan total");
+    } else {
+        GB_TRY(cudaMemsetAsync(out, 0, sizeof(uint32_t), s), "scan");
+        *total = 0ull;
+    }
+    GB_TRY(cudaStreamSynchronize(s), "scan");
+    return SLS_OK;
+}
+
+}  // namespace
+
+// Builds the adjacency of a mesh whose coordinates (AoS) and triangles are
+// already on the device.  On success fills M->node_off, M->adj, n_free and
+// diag.  Returns SLS_ERR_NOT_FOUND (with nothing allocated) when a node has
+// more incident triangles than the device build handles, so the caller can
+// use the host build instead.
+sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
+                             cudaStream_t s)
+{
+    const int64_t n = M->n, m = M->m;
+    if (3 * m >= (int64_t(1) << 32)) return SLS_ERR_NOT_FOUND;
+    const int sms = device_sm_count();
+    const int grid = sms * 8, block = 256;
+
+    DevBuf b_flags, b_cnt, b_ptr, b_inc, b_nbtmp, b_words, b_fixed, b_deg, b_bnd, b_keys;
+    unsigned *flags = nullptr, *cnt = nullptr, *words = nullptr, *deg = nullptr;
+    uint32_t *ptr = nullptr;
+    int32_t *inc = nullptr, *nbtmp = nullptr;
+    uint8_t *fixed = nullptr, *bnd = nullptr;
+    unsigned long long *keys = nullptr;
+    sls_status st;
+    if ((st = dalloc(b_flags, 2, &flags, "build flags")) != SLS_OK) return st;
+    if ((st = dalloc(b_keys, 8, &keys, "build keys")) != SLS_OK) return st;
+    // keys: [0] first bad triangle, [1] first bad coordinate, [2..5] bbox, [6] free count
+    GB_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), s), "build");
+    GB_TRY(cudaMemsetAsync(keys, 0xff, 2 * sizeof(unsigned long long), s), "build");
+    validate_xy_kernel<<<grid, block, 0, s>>>(reinterpret_cast<const unsigned long long *>(d_xy), 2 * n, flags,
+                                              keys + 1);
+    validate_tri_kernel<<<grid, block, 0, s>>>(d_tri, m, n, flags, keys);
+    GB_TRY(cudaGetLastError(), "validate");
+    unsigned hflags = 0;
+    unsigned long long hfirst[2] = {0, 0};
+    GB_TRY(cudaMemcpyAsync(&hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, s), "validate");
+    GB_TRY(cudaMemcpyAsync(hfirst, keys, sizeof hfirst, cudaMemcpyDeviceToHost, s), "validate");
+    GB_TRY(cudaStreamSynchronize(s), "validate");
+    if (hflags & kErrFinite)
+        return fail(SLS_ERR_INVALID, "coordinate " + std::to_string(hfirst[1]) + " is not finite");
+    if (hflags & (kErrRange | kErrRepeat)) {
+        const unsigned long long t = hfirst[0] >> 1;
+        return fail(SLS_ERR_INVALID, "triangle " + std::to_string(t) +
+                                         ((hfirst[0] & 1ull) ? " repeats a vertex" : " has a vertex id out of range"));
+    }
+
+    if ((st = dalloc(b_cnt, (size_t)n + 1, &cnt, "incidence counts")) != SLS_OK) return st;
+    if ((st = dalloc(b_ptr, (size_t)n + 1, &ptr, "incidence offsets")) != SLS_OK) return st;
+    if ((st = dalloc(b_inc, (size_t)(3 * m), &inc, "incidences")) != SLS_OK) return st;
+    GB_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (n + 1), s), "build");
+    count_kernel<<<grid, block, 0, s>>>(d_tri, 3 * m, cnt);
+    GB_TRY(cudaGetLastError(), "count");
+    unsigned long long total = 0ull;
+    if ((st = scan_u32(cnt, n, ptr, &total, s)) != SLS_OK) return st;
+    GB_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (n + 1), s), "build");
+    scatter_kernel<<<grid, block, 0, s>>>(d_tri, 3 * m, ptr, cnt, inc);
+    GB_TRY(cudaGetLastError(), "scatter");
+
+    if ((st = dalloc(b_nbtmp, (size_t)(6 * m), &nbtmp, "neighbour scratch")) != SLS_OK) return st;
+    if ((st = dalloc(b_words, (size_t)n + 1, &words, "word counts")) != SLS_OK) return st;
+    if ((st = dalloc(b_fixed, (size_t)n, &fixed, "fixed flags")) != SLS_OK) return st;
+    if ((st = dalloc(b_deg, (size_t)n, &deg, "degrees")) != SLS_OK) return st;
+    if (h_boundary) {
+        if ((st = dalloc(b_bnd, (size_t)n, &bnd, "boundary flags")) != SLS_OK) return st;
+        GB_TRY(cudaMemcpyAsync(bnd, h_boundary, (size_t)n, cudaMemcpyHostToDevice, s), "upload flags");
+    }
+    node_pass1_kernel<<<grid, block, 0, s>>>(n, reinterpret_cast<const double2 *>(d_xy), d_tri, ptr, inc, bnd,
+                                             nbtmp, words, fixed, deg, flags);
+    GB_TRY(cudaGetLastError(), "node pass 1");
+    GB_TRY(cudaMemcpyAsync(&hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, s), "build");
+    GB_TRY(cudaStreamSynchronize(s), "node pass 1");
+    if (hflags & kErrManifold) return fail(SLS_ERR_NONMANIFOLD, "an edge is shared by more than two triangles");
+    if (hflags & kErrTooMany) return SLS_ERR_NOT_FOUND;
+
+    uint32_t *node_off = nullptr;
+    GB_TRY(cudaMalloc(&node_off, sizeof(uint32_t) * (n + 1)), "node offsets");
+    M->node_off = node_off;
+    unsigned long long wtotal = 0ull;
+    if ((st = scan_u32(words, n, node_off, &wtotal, s)) != SLS_OK) return st;
+    if (wtotal >= (1ull << 32)) return fail(SLS_ERR_INVALID, "adjacency exceeds 2^32 words");
+    M->adj_words = wtotal;
+    GB_TRY(cudaMalloc(&M->adj, sizeof(uint32_t) * (wtotal > 0 ? wtotal : 1)), "adjacency");
+    node_pass2_kernel<<<grid, block, 0, s>>>(n, d_tri, ptr, inc, nbtmp, deg, fixed, node_off, M->adj);
+    GB_TRY(cudaGetLastError(), "node pass 2");
+
+    GB_TRY(cudaMemsetAsync(keys + 2, 0xff, 2 * sizeof(unsigned long long), s), "bbox");
+    GB_TRY(cudaMemsetAsync(keys + 4, 0x00, 3 * sizeof(unsigned long long), s), "bbox");
+    bbox_kernel<<<grid, block, 0, s>>>(reinterpret_cast<const double2 *>(d_xy), n, fixed, keys + 2, keys + 6);
+    GB_TRY(cudaGetLastError(), "bbox");
+    unsigned long long hk[5];
+    GB_TRY(cudaMemcpyAsync(hk, keys + 2, sizeof hk, cudaMemcpyDeviceToHost, s), "bbox");
+    GB_TRY(cudaStreamSynchronize(s), "build");
+    auto unkey = [](unsigned long long k) {
+        const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+        double v;
+        std::memcpy(&v, &b, sizeof v);
+        return v;
+    };
+    const double xmin = unkey(hk[0]), ymin = unkey(hk[1]), xmax = unkey(hk[2]), ymax = unkey(hk[3]);
+    M->diag = bbox_diagonal(xmin, xmax, ymin, ymax);
+    M->n_free = (int64_t)hk[4];
+    return SLS_OK;
+}
+
+}  // namespace sls

@@ -35,15 +35,10 @@ static void to_layout(const double *xy, int64_t n, int layout, std::vector<doubl
     }
 }
 
-sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const int32_t *tri,
-                       const sls_options &o)
+// Common set-up of a handle: stream, statistics, accept mask, launch shape.
+static sls_status mesh_setup(sls_mesh *M, const sls_options &o)
 {
     M->opt = o;
-    M->n = hm.n;
-    M->m = hm.m;
-    M->n_free = hm.n_free;
-    M->diag = hm.diag;
-    M->adj_words = hm.node_off[hm.n];
     SLS_CUDA_TRY(cudaGetDevice(&M->device), "cudaGetDevice");
     if (o.stream) {
         M->stream = (cudaStream_t)o.stream;
@@ -51,13 +46,7 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
         SLS_CUDA_TRY(cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking), "cudaStreamCreate");
         M->own_stream = true;
     }
-    const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
     sls_status st;
-    for (int b = 0; b < 2; ++b)
-        if ((st = dev_alloc((void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
-    if ((st = dev_alloc((void **)&M->node_off, sizeof(uint32_t) * (M->n + 1), "node offsets")) != SLS_OK) return st;
-    if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
-    if ((st = dev_alloc((void **)&M->tri, sizeof(int32_t) * 3 * (size_t)M->m, "triangles")) != SLS_OK) return st;
     M->stats_cap = 256;
     if ((st = dev_alloc((void **)&M->stats, sizeof(PassStats) * M->stats_cap, "pass statistics")) != SLS_OK) return st;
     SLS_CUDA_TRY(cudaMallocHost((void **)&M->h_stats, sizeof(PassStats)), "cudaMallocHost");
@@ -65,6 +54,31 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
         if ((st = dev_alloc((void **)&M->accept, (size_t)M->n, "accept mask")) != SLS_OK) return st;
         SLS_CUDA_TRY(cudaMemsetAsync(M->accept, 0, (size_t)M->n, M->stream), "cudaMemset");
     }
+    M->cur = 0;
+    M->block = o.block_size;
+    M->screened = o.kernel != SLS_KERNEL_FP64;
+    if (M->screened && (M->block < 64 || M->block > 256)) M->block = 256;  // the screened kernel is built for <= 256
+    M->grid = device_sm_count() * (M->screened ? pass_screened_occupancy(o.layout, M->block)
+                                               : pass_fp64_occupancy(o.layout, M->block));
+    return SLS_OK;
+}
+
+sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const int32_t *tri,
+                       const sls_options &o)
+{
+    M->n = hm.n;
+    M->m = hm.m;
+    M->n_free = hm.n_free;
+    M->diag = hm.diag;
+    M->adj_words = hm.node_off[hm.n];
+    sls_status st = mesh_setup(M, o);
+    if (st != SLS_OK) return st;
+    const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
+    for (int b = 0; b < 2; ++b)
+        if ((st = dev_alloc((void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
+    if ((st = dev_alloc((void **)&M->node_off, sizeof(uint32_t) * (M->n + 1), "node offsets")) != SLS_OK) return st;
+    if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
+    if ((st = dev_alloc((void **)&M->tri, sizeof(int32_t) * 3 * (size_t)M->m, "triangles")) != SLS_OK) return st;
     if (o.layout == 0) {
         SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[0], xy, cbytes, cudaMemcpyHostToDevice, M->stream), "upload coordinates");
         SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload coordinates");
@@ -82,12 +96,51 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
     SLS_CUDA_TRY(cudaMemcpyAsync(M->tri, tri, sizeof(int32_t) * 3 * (size_t)M->m,
                                  cudaMemcpyHostToDevice, M->stream), "upload triangles");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload");
-    M->cur = 0;
-    M->block = o.block_size;
-    M->screened = o.kernel != SLS_KERNEL_FP64;
-    if (M->screened && (M->block < 64 || M->block > 256)) M->block = 256;  // the screened kernel is built for <= 256
-    M->grid = device_sm_count() * (M->screened ? pass_screened_occupancy(o.layout, M->block)
-                                               : pass_fp64_occupancy(o.layout, M->block));
+    return SLS_OK;
+}
+
+sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const int32_t *tri, int64_t m,
+                                 const uint8_t *boundary, const sls_options &o)
+{
+    M->n = n;
+    M->m = m;
+    sls_status st = mesh_setup(M, o);
+    if (st != SLS_OK) return st;
+    const size_t cbytes = sizeof(double) * 2 * (size_t)n;
+    for (int b = 0; b < 2; ++b)
+        if ((st = dev_alloc((void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
+    if ((st = dev_alloc((void **)&M->tri, sizeof(int32_t) * 3 * (size_t)m, "triangles")) != SLS_OK) return st;
+    // interleaved coordinates go to xy[0] (AoS) or xy[1] (staging for SoA)
+    double *aos = o.layout == 0 ? M->xy[0] : M->xy[1];
+    SLS_CUDA_TRY(cudaMemcpyAsync(aos, xy, cbytes, cudaMemcpyHostToDevice, M->stream), "upload coordinates");
+    SLS_CUDA_TRY(cudaMemcpyAsync(M->tri, tri, sizeof(int32_t) * 3 * (size_t)m, cudaMemcpyHostToDevice, M->stream),
+                 "upload triangles");
+    st = build_device_mesh(M, aos, M->tri, boundary, M->stream);
+    if (st == SLS_ERR_NOT_FOUND) {
+        // a node with more incident triangles than the device build handles
+        HostMesh hm;
+        st = build_host_mesh(xy, n, tri, m, boundary, hm);
+        if (st != SLS_OK) return st;
+        cudaFree(M->node_off);
+        cudaFree(M->adj);
+        M->node_off = nullptr;
+        M->adj = nullptr;
+        M->n_free = hm.n_free;
+        M->diag = hm.diag;
+        M->adj_words = hm.node_off[hm.n];
+        if ((st = dev_alloc((void **)&M->node_off, sizeof(uint32_t) * (n + 1), "node offsets")) != SLS_OK) return st;
+        if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
+        SLS_CUDA_TRY(cudaMemcpyAsync(M->node_off, hm.node_off.data(), sizeof(uint32_t) * (n + 1),
+                                     cudaMemcpyHostToDevice, M->stream), "upload offsets");
+        SLS_CUDA_TRY(cudaMemcpyAsync(M->adj, hm.adj.data(), sizeof(uint32_t) * M->adj_words,
+                                     cudaMemcpyHostToDevice, M->stream), "upload adjacency");
+    } else if (st != SLS_OK) {
+        return st;
+    }
+    if (o.layout == 1)
+        SLS_CUDA_TRY(launch_aos_to_soa(M->xy[1], M->xy[0], n, device_sm_count() * 4, M->stream), "split");
+    SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[1], M->xy[0], cbytes, cudaMemcpyDeviceToDevice, M->stream), "copy coordinates");
+    SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "mesh create");
     return SLS_OK;
 }
 

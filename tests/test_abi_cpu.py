@@ -36,13 +36,16 @@ def test_library_exports_every_declared_symbol(L):
         assert hasattr(L, s), s
 
 
-def _create(L, xy, tri, bnd=None):
+def _create(L, xy, tri, bnd=None, host_build=True):
+    """Host validation runs before any device call when the host build is
+    selected, so these checks need no GPU."""
     xy = np.ascontiguousarray(xy, np.float64)
     tri = np.ascontiguousarray(tri, np.int32)
     h = C.c_void_p()
     bp = None if bnd is None else np.ascontiguousarray(bnd, np.uint8).ctypes.data_as(C.c_void_p)
+    opt = sls.make_options(host_build=host_build)
     st = L.sls_mesh_create(xy.ctypes.data_as(C.c_void_p), xy.shape[0], tri.ctypes.data_as(C.c_void_p),
-                           tri.shape[0], bp, None, C.byref(h))
+                           tri.shape[0], bp, C.byref(opt), C.byref(h))
     if st == 0:
         L.sls_mesh_destroy(h)
     return st, L.sls_last_error().decode()
@@ -77,5 +80,6 @@ def test_fails_loudly_without_a_gpu(L):
     except ImportError:
         pass
     xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
-    st, msg = _create(L, xy, [[0, 1, 2]])
-    assert st == 4 and msg  # SLS_ERR_CUDA with a message: no silent CPU path
+    for host_build in (True, False):
+        st, msg = _create(L, xy, [[0, 1, 2]], host_build=host_build)
+        assert st == 4 and msg  # SLS_ERR_CUDA with a message: no silent CPU path
