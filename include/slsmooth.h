@@ -93,6 +93,9 @@ typedef struct sls_info {
     int64_t accepted_last; /* accepted free nodes in the last executed pass                   */
     double max_d2_last;    /* largest squared move in the last executed pass                  */
     int64_t fp64_fallbacks;/* accept tests the screened kernel re-did in FP64 (last call)     */
+    int64_t launches;      /* kernel launches issued by the last sls_smooth call (passes
+                              launched after the tolerance was met return at once; 0 from
+                              the batched and served forms)                                 */
 } sls_info;
 
 typedef struct sls_mesh sls_mesh;

@@ -224,6 +224,7 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
     while (it < launched && hs[it].executed) fb += (long long)hs[it++].fallbacks;
     info.iterations = it;
     info.fp64_fallbacks = fb;
+    info.launches = (int64_t)launched * (cb ? 2 : 1);
     if (it > 0) {
         const PassStats &l = hs[it - 1];
         info.accepted_last = (int64_t)l.nacc;

@@ -139,6 +139,7 @@ extern "C" sls_status sls_smooth_noalloc(const sls_mesh *M, double *xy_in, doubl
     }
     res.iterations = it;
     res.fp64_fallbacks = fb;
+    res.launches = launched;
     if (it > 0) {
         res.accepted_last = (int64_t)last.nacc;
         std::memcpy(&res.max_d2_last, &last.maxd2_bits, sizeof(double));
