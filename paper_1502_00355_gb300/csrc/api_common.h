@@ -21,6 +21,7 @@ struct sls_mesh {
     uint32_t *node_off = nullptr; // n+1
     uint32_t *adj = nullptr;      // node_off[n] words
     uint64_t adj_words = 0;
+    uint32_t *node_order = nullptr;  // n_free: processing order of the free nodes
     int32_t *tri = nullptr;       // 3m, for the histogram
     sls::PassStats *stats = nullptr;  // one record per pass of a call
     int stats_cap = 0;
@@ -47,6 +48,9 @@ sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const
 // Device adjacency build (mesh_build_gpu.cu); SLS_ERR_NOT_FOUND = use the host build.
 sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
                              cudaStream_t s);
+// The processing order of the free nodes, from the adjacency on the device
+// (mesh_build_gpu.cu): fills M->node_order.
+sls_status build_node_order(sls_mesh *M, cudaStream_t s);
 void mesh_release(sls_mesh *M);
 sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info);
 sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device);

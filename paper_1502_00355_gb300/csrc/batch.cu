@@ -98,6 +98,8 @@ sls_status run(sls_batch *B, sls_info *infos)
         J.node_off = M->node_off;
         J.adj = M->adj;
         J.n = M->n;
+        J.order = M->node_order;
+        J.norder = M->n_free;
         J.stats = B->d_stats + B->stats_off[slot];
         const double tol = B->tols[mi];
         const double thr = tolerance_threshold(tol, M->diag);
@@ -254,7 +256,8 @@ sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *i
     B->stats_off.resize(k);
     for (int slot = 0; slot < k; ++slot) {
         sls_mesh *M = B->meshes[B->order[slot]];
-        for (int64_t f = 0; f < M->n; f += 32) tasks.push_back(WarpTask{slot, (int32_t)f});
+        // at least one task, which marks the job's passes as executed
+        for (int64_t f = 0; f < std::max<int64_t>(1, M->n_free); f += 32) tasks.push_back(WarpTask{slot, (int32_t)f});
         tasks_upto[slot + 1] = (int64_t)tasks.size();
         B->stats_off[slot] = B->nstats;
         B->nstats += std::max(1, B->iters[B->order[slot]]);

@@ -7,6 +7,12 @@
 
 #include "slsmooth.h"
 
+#ifdef __CUDACC__
+#define SLS_HOST_DEVICE __host__ __device__
+#else
+#define SLS_HOST_DEVICE
+#endif
+
 namespace sls {
 
 // Thread-local error message behind sls_last_error().
@@ -41,7 +47,18 @@ struct HostMesh {
     std::vector<uint32_t> node_off;    // n + 1
     std::vector<uint32_t> adj;         // node_off[n] words
     std::vector<uint8_t> fixed;        // n
+    std::vector<uint32_t> order;       // n_free: processing order of the free nodes
 };
+
+// Processing order of the free nodes: tiles of kOrderTile consecutive node ids,
+// inside a tile the free nodes by ascending (degree, triangle count), each
+// clamped to 255, then id.  A warp then mostly holds nodes of one degree, so
+// its loops run as many trips as its nodes need.
+constexpr int kOrderTile = 1024;
+SLS_HOST_DEVICE inline uint32_t order_key(uint32_t deg, uint32_t ntri)
+{
+    return ((deg < 255u ? deg : 255u) << 8) | (ntri < 255u ? ntri : 255u);
+}
 
 // sqrt((xmax - xmin)^2 + (ymax - ymin)^2), the bounding-box diagonal D.
 double bbox_diagonal(double xmin, double xmax, double ymin, double ymax);

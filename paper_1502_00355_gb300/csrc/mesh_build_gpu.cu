@@ -355,7 +355,76 @@ sls_status scan_u32(const unsigned *in, int64_t len, uint32_t *out, unsigned lon
     return SLS_OK;
 }
 
+// One block of kOrderTile threads per tile: the number of free nodes.
+__global__ void __launch_bounds__(kOrderTile) order_count_kernel(const uint32_t *__restrict__ node_off,
+                                                                  const uint32_t *__restrict__ adj, int64_t n,
+                                                                  unsigned *cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * kOrderTile + threadIdx.x;
+    const bool fr = i < n && !(adj[node_off[i]] & 0x80000000u);
+    const int c = __syncthreads_count(fr);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = (unsigned)c;
+}
+
+// One block of kOrderTile threads per tile: the tile's free nodes sorted by
+// (order_key, id) with a bitonic sort in shared memory, written at the tile's
+// offset.
+__global__ void __launch_bounds__(kOrderTile) order_sort_kernel(const uint32_t *__restrict__ node_off,
+                                                                 const uint32_t *__restrict__ adj, int64_t n,
+                                                                 const uint32_t *__restrict__ tile_off,
+                                                                 uint32_t *order)
+{
+    __shared__ uint32_t key[kOrderTile];
+    const unsigned tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * kOrderTile + tid;
+    uint32_t k = 0xffffffffu;  // fixed nodes and the tail sort last
+    if (i < n) {
+        const uint32_t meta = adj[node_off[i]];
+        if (!(meta & 0x80000000u)) k = (order_key(meta & 0xffffu, (meta >> 16) & 0x7fffu) << 10) | tid;
+    }
+    key[tid] = k;
+    __syncthreads();
+    for (unsigned size = 2; size <= (unsigned)kOrderTile; size <<= 1) {
+        for (unsigned stride = size >> 1; stride > 0; stride >>= 1) {
+            const unsigned j = tid ^ stride;
+            if (j > tid) {
+                const uint32_t a = key[tid], b = key[j];
+                const bool up = (tid & size) == 0;
+                if ((a > b) == up) {
+                    key[tid] = b;
+                    key[j] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const uint32_t nf = tile_off[blockIdx.x + 1] - tile_off[blockIdx.x];
+    if (tid < nf) order[tile_off[blockIdx.x] + tid] = (uint32_t)(blockIdx.x * kOrderTile) + (key[tid] & 1023u);
+}
+
 }  // namespace
+
+sls_status build_node_order(sls_mesh *M, cudaStream_t s)
+{
+    const int64_t n = M->n;
+    const int64_t tiles = (n + kOrderTile - 1) / kOrderTile;
+    DevBuf b_cnt, b_off;
+    unsigned *cnt = nullptr;
+    uint32_t *off = nullptr;
+    sls_status st;
+    if ((st = dalloc(b_cnt, (size_t)tiles, &cnt, "order counts")) != SLS_OK) return st;
+    if ((st = dalloc(b_off, (size_t)tiles + 1, &off, "order offsets")) != SLS_OK) return st;
+    order_count_kernel<<<(unsigned)tiles, kOrderTile, 0, s>>>(M->node_off, M->adj, n, cnt);
+    GB_TRY(cudaGetLastError(), "order count");
+    unsigned long long total = 0ull;
+    if ((st = scan_u32(cnt, tiles, off, &total, s)) != SLS_OK) return st;
+    if ((int64_t)total != M->n_free) return fail(SLS_ERR_INVALID, "free-node count mismatch in the processing order");
+    GB_TRY(cudaMalloc(&M->node_order, sizeof(uint32_t) * (size_t)(total > 0 ? total : 1)), "processing order");
+    order_sort_kernel<<<(unsigned)tiles, kOrderTile, 0, s>>>(M->node_off, M->adj, n, off, M->node_order);
+    GB_TRY(cudaGetLastError(), "order sort");
+    GB_TRY(cudaStreamSynchronize(s), "processing order");
+    return SLS_OK;
+}
 
 // Builds the adjacency of a mesh whose coordinates (AoS) and triangles are
 // already on the device.  On success fills M->node_off, M->adj, n_free and

@@ -96,7 +96,7 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
     SLS_CUDA_TRY(cudaMemcpyAsync(M->tri, tri, sizeof(int32_t) * 3 * (size_t)M->m,
                                  cudaMemcpyHostToDevice, M->stream), "upload triangles");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload");
-    return SLS_OK;
+    return build_node_order(M, M->stream);
 }
 
 sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const int32_t *tri, int64_t m,
@@ -141,7 +141,7 @@ sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const
         SLS_CUDA_TRY(launch_aos_to_soa(M->xy[1], M->xy[0], n, device_sm_count() * 4, M->stream), "split");
     SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[1], M->xy[0], cbytes, cudaMemcpyDeviceToDevice, M->stream), "copy coordinates");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "mesh create");
-    return SLS_OK;
+    return build_node_order(M, M->stream);
 }
 
 void mesh_release(sls_mesh *M)
@@ -151,6 +151,7 @@ void mesh_release(sls_mesh *M)
     cudaFree(M->xy[1]);
     cudaFree(M->node_off);
     cudaFree(M->adj);
+    cudaFree(M->node_order);
     cudaFree(M->tri);
     cudaFree(M->stats);
     cudaFree(M->accept);
@@ -185,6 +186,8 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
     a.node_off = M->node_off;
     a.adj = M->adj;
     a.n = M->n;
+    a.order = M->node_order;
+    a.norder = M->n_free;
     a.stats = M->stats;
     a.strict = M->opt.accept_strict;
     a.tol_active = tol_active ? 1 : 0;

@@ -88,6 +88,8 @@ extern "C" sls_status sls_smooth_noalloc(const sls_mesh *M, double *xy_in, doubl
     a.node_off = M->node_off;
     a.adj = M->adj;
     a.n = M->n;
+    a.order = M->node_order;
+    a.norder = M->n_free;
     a.stats = stats;
     a.strict = M->opt.accept_strict;
     a.tol_active = tol_active ? 1 : 0;

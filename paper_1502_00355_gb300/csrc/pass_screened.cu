@@ -8,10 +8,9 @@
 //
 //  1. The neighbour sums (Eq. 2) are the FP64 additions themselves, in the
 //     stored summation order.
-//  2. The division by the degree uses Markstein's correction (Markstein, IBM J.
-//     Res. Dev. 34(1), 1990): q0 = s*y with y = RN(1/N), r = fma(-q0, N, s)
-//     (exact), q = fma(r, y, q0), which is the correctly rounded s/N.  Three
-//     FP64 operations instead of a full division.
+//  2. The division by the degree is one FP64 multiplication by RN(1/N) and an
+//     exact integer remainder that picks the correctly rounded quotient
+//     (div_small.cuh), instead of a full division.
 //  3. If the centre equals the node's position bit for bit, q_new == q_old
 //     exactly and no quality needs evaluating.
 //  4. Otherwise alpha of every incident triangle, before and after the move, is
@@ -33,6 +32,7 @@
 // registers with FP64-pipe instructions.
 #include <cfloat>
 
+#include "div_small.cuh"
 #include "kernels.h"
 #include "node_exact.cuh"
 
@@ -46,18 +46,6 @@ __constant__ double c_degree[kFastMax + 1]; // N as a double
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
-
-// Correctly rounded s / N for a small integer N (y = RN(1/N)): Markstein's
-// correction when nothing can underflow or overflow (s's biased exponent in
-// [63, 2000]), IEEE division otherwise (subnormal or huge sums, inf, NaN).
-__device__ __forceinline__ double div_small(double s, double N, double y)
-{
-    const unsigned e = (unsigned)(dbits(s) >> 52) & 0x7ffu;
-    if (e - 63u > 1937u) return __ddiv_rn(s, N);
-    const double q0 = __dmul_rn(s, y);
-    const double r = __fma_rn(-q0, N, s);
-    return __fma_rn(r, y, q0);
-}
 
 // Splits the double with bit pattern b into a float head (its sign, exponent
 // and top 24 significant bits) and a float tail (the next 23 bits), with
@@ -263,8 +251,9 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
         sy = __dadd_rn(sy, bitsd(v.y));
     }
     const double fd = c_degree[deg], y = c_recip[deg];
-    const double cxd = div_small(sx, fd, y), cyd = div_small(sy, fd, y);
-    const unsigned long long cbx = dbits(cxd), cby = dbits(cyd);
+    const unsigned long long cbx = divs::div_small_bits(dbits(sx), deg, y, fd);
+    const unsigned long long cby = divs::div_small_bits(dbits(sy), deg, y, fd);
+    const double cxd = bitsd(cbx), cyd = bitsd(cby);
     d.cx = cbx;
     d.cy = cby;
     d.flags = kHasCentre;
@@ -388,12 +377,12 @@ __global__ void __launch_bounds__(256, 3) pass_screened_kernel(PassArgs a)
     float2 *loc = s_loc + tid;
     Deferred *wq = s_q + 64 * warp;
     int qn = 0;  // warp-uniform queue length
-    const int64_t nwtiles = (a.n + 31) / 32;
+    const int64_t nwtiles = (a.norder + 31) / 32;
     const int64_t wstride = (int64_t)gridDim.x * (nthr >> 5);
     for (int64_t wt = (int64_t)blockIdx.x * (nthr >> 5) + warp; wt < nwtiles; wt += wstride) {
-        const int64_t i = wt * 32 + lane;
+        const int64_t j = wt * 32 + lane;
         Deferred d;
-        const bool defer = i < a.n && screen_node<LAYOUT>(a, i, loc, nthr, d, best, nacc);
+        const bool defer = j < a.norder && screen_node<LAYOUT>(a, __ldg(a.order + j), loc, nthr, d, best, nacc);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
@@ -458,6 +447,8 @@ __global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restri
                 a.node_off = J->node_off;
                 a.adj = J->adj;
                 a.n = J->n;
+                a.order = J->order;
+                a.norder = J->norder;
                 a.stats = st;
                 a.q = q;
                 a.strict = J->strict;
@@ -469,9 +460,9 @@ __global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restri
         if (!active) continue;
         const int64_t first = tasks[t].first;
         if (first == 0 && lane == 0) a.stats[a.q].executed = 1u;
-        const int64_t i = first + lane;
+        const int64_t j = first + lane;
         Deferred d;
-        const bool defer = i < a.n && screen_node<LAYOUT>(a, i, loc, nthr, d, best, nacc);
+        const bool defer = j < a.norder && screen_node<LAYOUT>(a, __ldg(a.order + j), loc, nthr, d, best, nacc);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
