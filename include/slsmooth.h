@@ -84,6 +84,14 @@ typedef struct sls_options {
     int32_t host_build;    /* 1: build the adjacency on the host; 0: on the device (default;
                               the host build is still used for nodes in more than 32
                               triangles)                                                     */
+    int32_t form;          /* 0: Form A, the Jacobi pass of Eq. 2 (default).  1: Form B
+                              (Eq. 3, in place) made deterministic as multicolour
+                              Gauss-Seidel: the free nodes are coloured at creation so that
+                              no two neighbours share a colour (Jones-Plassmann rounds,
+                              priority splitmix64(150200355 + node id)), and every sweep
+                              updates the colour classes in turn, in place.  copy_back is
+                              ignored.  Single meshes only: the batched, served and
+                              allocation-free forms reject it.                               */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle    */
 } sls_options;
 

@@ -6,9 +6,10 @@ the CUDA library can both consume its output without sharing any of the
 method's code.
 
 The paper measures on Delaunay triangulations of uniformly random points
-(Section 4); those meshes are not available, so structured jittered grids of
-the same kind (planar, valence about 6, interior nodes free, the outer ring
-fixed) stand in for them:
+(Section 4), made with a generator and Triangle that are not available here.
+``delaunay_random`` rebuilds that family with Qhull; structured jittered grids
+of the same kind (planar, valence about 6, interior nodes free, the outer ring
+fixed) serve for the large workloads:
 
 * an ``nx x ny`` vertex grid with spacing ``h = 1/(ny-1)``;
 * every quad split along one of its two diagonals (a seeded coin per quad, or
@@ -172,6 +173,51 @@ def jittered_grid(nx: int, ny: int, jitter: float, seed: int, *, h: float | None
                           numbering=numbering, pull_fraction=pull_fraction))
 
 
+def delaunay_random(n: int, seed: int, *, numbering: str = "morton", perm_seed: int | None = None) -> Mesh:
+    """Delaunay triangulation of ``n`` seeded uniform random points in the unit
+    square: the paper's mesh family (Section 4), made with Qhull through
+    ``scipy.spatial.Delaunay`` in place of the paper's generator and Triangle.
+
+    Triangles are stored counter-clockwise; the convex-hull vertices are the
+    fixed nodes (points Qhull leaves out of every triangle, if any, are fixed
+    too).  Interior valence ranges from 3 to about 12.  ``numbering``: "natural"
+    (generation order), "morton" (Z-order of the points on a 2^16 grid) or
+    "random"; ``perm`` maps generation order to node id.
+    """
+    from scipy.spatial import Delaunay
+
+    if n < 3:
+        raise ValueError("need at least 3 points")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pts = rng.uniform(0.0, 1.0, size=(n, 2))
+    dt = Delaunay(pts)
+    tri_nat = dt.simplices.astype(np.int64)
+    a, b, c = pts[tri_nat[:, 0]], pts[tri_nat[:, 1]], pts[tri_nat[:, 2]]
+    cross = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    cw = cross < 0
+    tri_nat[cw, 1], tri_nat[cw, 2] = tri_nat[cw, 2].copy(), tri_nat[cw, 1].copy()
+    bnd = np.ones(n, dtype=np.uint8)
+    bnd[np.unique(tri_nat)] = 0
+    bnd[np.unique(dt.convex_hull)] = 1
+    if numbering == "natural":
+        perm = np.arange(n, dtype=np.int64)
+    elif numbering == "morton":
+        q = np.minimum((pts * 65536.0).astype(np.int64), 65535)
+        perm = morton_order(q[:, 0], q[:, 1]).astype(np.int64)
+    elif numbering == "random":
+        prng = np.random.Generator(np.random.PCG64(seed + 7919 if perm_seed is None else perm_seed))
+        perm = prng.permutation(n).astype(np.int64)
+    else:
+        raise ValueError(numbering)
+    xy = np.empty((n, 2), dtype=np.float64)
+    xy[perm] = pts
+    boundary = np.empty(n, dtype=np.uint8)
+    boundary[perm] = bnd
+    tri = perm[tri_nat].astype(np.int32)
+    return Mesh(xy=xy, tri=tri, boundary=boundary, perm=perm,
+                meta=dict(kind="delaunay", n=n, seed=seed, numbering=numbering))
+
+
 def unpermute(xy: np.ndarray, mesh: Mesh) -> np.ndarray:
     """Coordinates back in natural (row-major grid) order."""
     return xy[mesh.perm]
@@ -193,6 +239,12 @@ def large_grid(nx: int = 4096, ny: int = 4096) -> Mesh:
     """4096x4096 vertices (16,777,216 nodes, 33,538,050 triangles), jitter 0.35h,
     5% of interior nodes pulled towards the nearest of 1,024 seeded centres."""
     return jittered_grid(nx, ny, 0.35, BASE_SEED + 3, numbering="morton", pull_fraction=0.05)
+
+
+def delaunay_mesh(n: int = 100_000) -> Mesh:
+    """The paper's largest workload: a Delaunay mesh of 100,000 uniform random
+    points, Morton numbering."""
+    return delaunay_random(n, BASE_SEED + 4, numbering="morton")
 
 
 def batch_specs(k: int = 2048, lo: int = 1024, hi: int = 262144, seed: int = BASE_SEED + 1000):

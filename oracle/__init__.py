@@ -14,6 +14,9 @@ Functions and the part of the paper they follow:
   * ``OracleMesh.sweep`` - one Form-A pass (Eq. 2) with the smart accept test
                            (Sections 2.1 and 3.3.4)
   * ``OracleMesh.smooth``- the iteration loop with the copy-back of Form A
+  * ``OracleMesh.colouring`` - Jones-Plassmann colouring of the free nodes
+  * ``OracleMesh.smooth(form="B")`` - Form B (Eq. 3) as multicolour
+                           Gauss-Seidel: colour classes in turn, in place
   * ``OracleMesh.histogram`` - quality histogram of all triangles
 
 Parity pins (tests/test_oracle_*.py): closed forms of alpha, the regular
@@ -39,6 +42,9 @@ _LIBS: dict[bool, C.CDLL] = {}
 _LOCK = threading.Lock()
 
 STATUS = {0: "ok", 1: "invalid", 2: "nonmanifold", 3: "nomem"}
+
+# seed of the colouring priorities, splitmix64(COLOUR_SEED + i)
+COLOUR_SEED = 150200355
 
 
 def _lib_path(openmp: bool) -> str:
@@ -82,6 +88,11 @@ def _lib(openmp: bool = False) -> C.CDLL:
             lib.orc_smooth.restype = C.c_int
             lib.orc_smooth.argtypes = [P, P, I32, D, C.c_int, P, P, P, P, P]
             lib.orc_histogram.argtypes = [P, P, I32, D, D, P, P, P]
+            lib.orc_colour.restype = C.c_int
+            lib.orc_colour.argtypes = [P, C.c_uint64, P, P, P]
+            lib.orc_sweep_coloured.argtypes = [P, P, P, I32, C.c_int, P, P, P]
+            lib.orc_smooth_coloured.restype = C.c_int
+            lib.orc_smooth_coloured.argtypes = [P, P, P, I32, I32, D, C.c_int, P, P, P, P, P]
             _LIBS[openmp] = lib
         return _LIBS[openmp]
 
@@ -164,17 +175,49 @@ class OracleMesh:
                                    _ptr(acc), _ptr(d2), _ptr(qo), _ptr(qn), _ptr(cand))
         return out, acc, d2, qo, qn, cand
 
-    def smooth(self, xy, max_iter: int, tol: float = 0.0, strict: bool = False):
-        """Iterate from xy.  Returns (xy_final, info dict, accept mask of the last pass)."""
+    def colouring(self, seed: int = COLOUR_SEED):
+        """Jones-Plassmann colouring of the free nodes.  Returns (colour[n]
+        with -1 for fixed nodes, number of colours, number of rounds)."""
+        col = np.empty(self.n, np.int32)
+        nc = C.c_int32(0)
+        rounds = C.c_int32(0)
+        rc = self._lib.orc_colour(self._h, C.c_uint64(seed), _ptr(col), C.byref(nc), C.byref(rounds))
+        if rc != 0:
+            raise OracleError(rc)
+        return col, nc.value, rounds.value
+
+    def sweep_coloured(self, xy, colour, ncolours: int, strict: bool = False):
+        """One Form-B sweep (colour classes in turn, in place) from xy.
+        Returns (xy_next, accept, maxd2, nacc)."""
+        xy = np.array(xy, dtype=np.float64, copy=True).reshape(-1, 2)
+        colour = np.ascontiguousarray(colour, dtype=np.int32)
+        acc = np.empty(self.n, np.uint8)
+        maxd2 = C.c_double(0.0)
+        nacc = C.c_int64(0)
+        self._lib.orc_sweep_coloured(self._h, _ptr(xy), _ptr(colour), int(ncolours), int(strict), _ptr(acc),
+                                     C.byref(maxd2), C.byref(nacc))
+        return xy, acc, maxd2.value, nacc.value
+
+    def smooth(self, xy, max_iter: int, tol: float = 0.0, strict: bool = False, form: str = "A"):
+        """Iterate from xy (Form A, or Form B in colour order).  Returns
+        (xy_final, info dict, accept mask of the last pass)."""
         xy = np.array(xy, dtype=np.float64, copy=True).reshape(-1, 2)
         acc = np.zeros(self.n, np.uint8)
         it = C.c_int32(0)
         conv = C.c_int32(0)
         nacc = C.c_int64(0)
         maxd2 = C.c_double(0.0)
-        rc = self._lib.orc_smooth(self._h, _ptr(xy), int(max_iter), float(tol), int(strict),
-                                  _ptr(acc), C.byref(it), C.byref(conv), C.byref(nacc),
-                                  C.byref(maxd2))
+        if form == "A":
+            rc = self._lib.orc_smooth(self._h, _ptr(xy), int(max_iter), float(tol), int(strict),
+                                      _ptr(acc), C.byref(it), C.byref(conv), C.byref(nacc),
+                                      C.byref(maxd2))
+        elif form == "B":
+            col, nc, _ = self.colouring()
+            rc = self._lib.orc_smooth_coloured(self._h, _ptr(xy), _ptr(col), int(nc), int(max_iter),
+                                               float(tol), int(strict), _ptr(acc), C.byref(it),
+                                               C.byref(conv), C.byref(nacc), C.byref(maxd2))
+        else:
+            raise ValueError(form)
         if rc != 0:
             raise OracleError(rc)
         info = dict(iterations=it.value, converged=conv.value, accepted_last=nacc.value,

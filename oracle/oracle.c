@@ -385,6 +385,146 @@ int orc_smooth(const orc_mesh *M, double *xy, int32_t max_iter, double tol, int 
     return ORC_OK;
 }
 
+/* ---- Eq. 3, Form B, made deterministic: multicolour Gauss-Seidel ---------
+ * Form B updates the nodes in place, each reading the newest coordinates of
+ * its neighbours (Eq. 3), so a parallel run depends on the update order.  The
+ * reading used here (R9): colour the free nodes so that no two neighbours
+ * share a colour, then update one colour class after the other, each node
+ * reading the coordinates as they are at that moment (neighbours of earlier
+ * classes already moved in this sweep).  Nodes of one class are never
+ * neighbours, so a class gives the same result in any order.
+ *
+ * Colouring (R10): Jones-Plassmann rounds.  Priority of node i:
+ * splitmix64(seed + i) (Steele, Lea and Flood, OOPSLA 2014), ties by index.
+ * In each round, every uncoloured free node whose (priority, index) exceeds
+ * that of each uncoloured free neighbour takes the smallest colour not held by
+ * a neighbour coloured in an earlier round. */
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static int beats(uint64_t pi, int64_t i, uint64_t pj, int64_t j)
+{
+    return pi > pj || (pi == pj && i > j);
+}
+
+/* colour[i] = class of free node i, -1 for fixed nodes.  Returns the number of
+ * classes in *ncolours and the number of rounds in *rounds.  0 or ORC_NOMEM. */
+int orc_colour(const orc_mesh *M, uint64_t seed, int32_t *colour, int32_t *ncolours, int32_t *rounds)
+{
+    int64_t n = M->n;
+    uint64_t *prio = (uint64_t *)malloc(sizeof(uint64_t) * (n > 0 ? n : 1));
+    uint8_t *win = (uint8_t *)malloc(n > 0 ? n : 1);
+    int64_t maxdeg = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (M->nbr_ptr[i + 1] - M->nbr_ptr[i] > maxdeg) maxdeg = M->nbr_ptr[i + 1] - M->nbr_ptr[i];
+    uint8_t *used = (uint8_t *)malloc((size_t)maxdeg + 1);
+    if (!prio || !win || !used) {
+        free(prio);
+        free(win);
+        free(used);
+        return ORC_NOMEM;
+    }
+    int64_t left = 0;
+    for (int64_t i = 0; i < n; i++) {
+        prio[i] = splitmix64(seed + (uint64_t)i);
+        colour[i] = -1;
+        if (!M->fixed[i]) left++;
+    }
+    int32_t nc = 0, r = 0;
+    while (left > 0) {
+        /* the winners of this round, against the state at its start */
+        for (int64_t i = 0; i < n; i++) {
+            win[i] = 0;
+            if (M->fixed[i] || colour[i] >= 0) continue;
+            int w = 1;
+            for (int64_t k = M->nbr_ptr[i]; k < M->nbr_ptr[i + 1]; k++) {
+                int64_t j = M->nbr[k];
+                if (M->fixed[j] || colour[j] >= 0) continue;
+                if (!beats(prio[i], i, prio[j], j)) w = 0;
+            }
+            win[i] = (uint8_t)w;
+        }
+        /* winners are pairwise non-adjacent: colour them from earlier rounds */
+        for (int64_t i = 0; i < n; i++) {
+            if (!win[i]) continue;
+            int64_t deg = M->nbr_ptr[i + 1] - M->nbr_ptr[i];
+            for (int64_t c = 0; c <= deg; c++) used[c] = 0;
+            for (int64_t k = M->nbr_ptr[i]; k < M->nbr_ptr[i + 1]; k++) {
+                int32_t cj = colour[M->nbr[k]];
+                if (cj >= 0 && cj <= deg && !win[M->nbr[k]]) used[cj] = 1;
+            }
+            int32_t c = 0;
+            while (used[c]) c++;
+            colour[i] = c;
+            if (c + 1 > nc) nc = c + 1;
+            left--;
+        }
+        r++;
+    }
+    free(prio);
+    free(win);
+    free(used);
+    *ncolours = nc;
+    *rounds = r;
+    return ORC_OK;
+}
+
+/* One Form-B sweep in colour order, in place.  accept may be NULL. */
+void orc_sweep_coloured(const orc_mesh *M, double *xy, const int32_t *colour, int32_t ncolours,
+                        int strict, uint8_t *accept, double *maxd2_out, int64_t *nacc_out)
+{
+    double maxd2 = 0.0;
+    int64_t nacc = 0;
+    int64_t n = M->n;
+    if (accept)
+        for (int64_t i = 0; i < n; i++) accept[i] = 0;
+    for (int32_t c = 0; c < ncolours; c++) {
+        for (int64_t i = 0; i < n; i++) {
+            if (colour[i] != c) continue;
+            double x, y, d2;
+            int acc;
+            node_update(M, xy, i, strict, &x, &y, &acc, &d2, NULL, NULL, NULL);
+            xy[2 * i] = x;
+            xy[2 * i + 1] = y;
+            if (accept) accept[i] = (uint8_t)acc;
+            nacc += acc;
+            if (d2 > maxd2) maxd2 = d2;
+        }
+    }
+    *maxd2_out = maxd2;
+    *nacc_out = nacc;
+}
+
+/* The Form-B iteration: sweeps in colour order with the stop rule R4. */
+int orc_smooth_coloured(const orc_mesh *M, double *xy, const int32_t *colour, int32_t ncolours,
+                        int32_t max_iter, double tol, int strict, uint8_t *accept_last,
+                        int32_t *iterations, int32_t *converged, int64_t *nacc_last, double *maxd2_last)
+{
+    double thr = (tol * M->diag) * (tol * M->diag); /* R4 */
+    int32_t it = 0;
+    int32_t conv = 0;
+    int64_t nacc = 0;
+    double maxd2 = 0.0;
+    while (it < max_iter) {
+        orc_sweep_coloured(M, xy, colour, ncolours, strict, accept_last, &maxd2, &nacc);
+        it += 1;
+        if (tol > 0.0 && maxd2 < thr) {
+            conv = 1;
+            break;
+        }
+    }
+    *iterations = it;
+    *converged = conv;
+    *nacc_last = nacc;
+    *maxd2_last = maxd2;
+    return ORC_OK;
+}
+
 /* Quality histogram of all triangles at coordinates xy (Section 3.3.1).
  * bin = floor((q - lo) / (hi - lo) * nbins), clamped to [0, nbins-1];
  * qmean sums the qualities in triangle order. */

@@ -33,7 +33,7 @@ int device_sm_count()
     return sms > 0 ? sms : 1;
 }
 
-static sls_options g_defaults = {0, 0, 0, SLS_KERNEL_AUTO, 0, 0, 0, 16, 0, nullptr};
+static sls_options g_defaults = {0, 0, 0, SLS_KERNEL_AUTO, 0, 0, 0, 16, 0, 0, nullptr};
 
 sls_options resolve_options(const sls_options *opt)
 {
@@ -50,6 +50,7 @@ sls_status check_options(const sls_options &o)
         return fail(SLS_ERR_INVALID, "unknown kernel");
     if (o.block_size % 32 != 0 || o.block_size > 1024)
         return fail(SLS_ERR_INVALID, "block_size must be a multiple of 32, at most 1024");
+    if (o.form != 0 && o.form != 1) return fail(SLS_ERR_INVALID, "form must be 0 (Form A) or 1 (Form B)");
     return SLS_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -22,6 +23,7 @@ struct sls_mesh {
     uint32_t *adj = nullptr;      // node_off[n] words
     uint64_t adj_words = 0;
     uint32_t *node_order = nullptr;  // n_free: processing order of the free nodes
+    std::vector<int64_t> colour_off; // segments of node_order: one per colour (Form B), else one
     int32_t *tri = nullptr;       // 3m, for the histogram
     sls::PassStats *stats = nullptr;  // one record per pass of a call
     int stats_cap = 0;

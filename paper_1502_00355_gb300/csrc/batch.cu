@@ -98,8 +98,6 @@ sls_status run(sls_batch *B, sls_info *infos)
         J.node_off = M->node_off;
         J.adj = M->adj;
         J.n = M->n;
-        J.order = M->node_order;
-        J.norder = M->n_free;
         J.stats = B->d_stats + B->stats_off[slot];
         const double tol = B->tols[mi];
         const double thr = tolerance_threshold(tol, M->diag);
@@ -222,6 +220,7 @@ sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *i
         if (meshes[j]->device != dev) return fail(SLS_ERR_INVALID, "all meshes must live on the current device");
         if (meshes[j]->opt.layout != meshes[0]->opt.layout)
             return fail(SLS_ERR_INVALID, "all meshes of a batch must use the same layout");
+        if (meshes[j]->opt.form != 0) return fail(SLS_ERR_INVALID, "the batched form runs Form A meshes only");
         if (iters[j] < 0) return fail(SLS_ERR_INVALID, "iteration counts must be >= 0");
         if (tol_rel && std::isnan(tol_rel[j])) return fail(SLS_ERR_INVALID, "tolerance is NaN");
         for (int i = 0; i < j; ++i)
@@ -256,8 +255,7 @@ sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *i
     B->stats_off.resize(k);
     for (int slot = 0; slot < k; ++slot) {
         sls_mesh *M = B->meshes[B->order[slot]];
-        // at least one task, which marks the job's passes as executed
-        for (int64_t f = 0; f < std::max<int64_t>(1, M->n_free); f += 32) tasks.push_back(WarpTask{slot, (int32_t)f});
+        for (int64_t f = 0; f < M->n; f += 32) tasks.push_back(WarpTask{slot, (int32_t)f});
         tasks_upto[slot + 1] = (int64_t)tasks.size();
         B->stats_off[slot] = B->nstats;
         B->nstats += std::max(1, B->iters[B->order[slot]]);

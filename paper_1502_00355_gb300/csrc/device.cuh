@@ -23,8 +23,8 @@ struct PassArgs {
     const uint32_t *node_off;  // n+1 word offsets into adj
     const uint32_t *adj;       // per-node words: meta, neighbours, triangle codes
     int64_t n;
-    const uint32_t *order;     // the free nodes in processing order (screened kernel)
-    int64_t norder;            // number of free nodes
+    const uint32_t *order;     // nullptr: every node in index order; else the nodes to update
+    int64_t norder;            // (one colour class of Form B) and their number
     PassStats *stats;          // stats[q] receives this pass
     int q;                     // pass index within the call
     int strict;                // 1: accept iff q_new > q_old
@@ -39,8 +39,6 @@ struct JobDesc {
     const uint32_t *node_off;  // n+1
     const uint32_t *adj;
     int64_t n;
-    const uint32_t *order;     // the job's free nodes in processing order
-    int64_t norder;
     PassStats *stats;          // one record per pass of the job
     unsigned long long thr_bits;
     int32_t strict, tol_active;
@@ -51,7 +49,7 @@ struct JobDesc {
     uint8_t *accept;           // n decisions, or nullptr
 };
 
-// Entries [first, first + 32) of one job's processing order.
+// 32 consecutive nodes [first, first + 32) of one job.
 struct WarpTask {
     int32_t job;
     int32_t first;

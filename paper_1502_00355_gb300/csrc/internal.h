@@ -47,14 +47,17 @@ struct HostMesh {
     std::vector<uint32_t> node_off;    // n + 1
     std::vector<uint32_t> adj;         // node_off[n] words
     std::vector<uint8_t> fixed;        // n
-    std::vector<uint32_t> order;       // n_free: processing order of the free nodes
 };
 
-// Processing order of the free nodes: tiles of kOrderTile consecutive node ids,
-// inside a tile the free nodes by ascending (degree, triangle count), each
-// clamped to 255, then id.  A warp then mostly holds nodes of one degree, so
-// its loops run as many trips as its nodes need.
+// Processing order of the free nodes of one Form-B colour class: tiles of
+// kOrderTile consecutive node ids, inside a tile the class's nodes by
+// ascending (degree, triangle count), each clamped to 255, then id, so that a
+// warp mostly holds nodes of one degree.
 constexpr int kOrderTile = 1024;
+
+// Seed of the Form-B colouring priorities: node i has priority
+// splitmix64(kColourSeed + i).
+constexpr unsigned long long kColourSeed = 150200355ull;
 SLS_HOST_DEVICE inline uint32_t order_key(uint32_t deg, uint32_t ntri)
 {
     return ((deg < 255u ? deg : 255u) << 8) | (ntri < 255u ? ntri : 255u);

@@ -197,17 +197,6 @@ sls_status build_host_mesh(const double *xy, int64_t n, const int32_t *tri, int6
     }
     out.diag = bbox_diagonal(xmin, xmax, ymin, ymax);
 
-    // Processing order of the free nodes (see order_key).
-    out.order.clear();
-    out.order.reserve((size_t)n_free);
-    for (int64_t t0 = 0; t0 < n; t0 += kOrderTile) {
-        const size_t first = out.order.size();
-        const int64_t t1 = std::min<int64_t>(n, t0 + kOrderTile);
-        for (int64_t i = t0; i < t1; ++i)
-            if (!fixed[i]) out.order.push_back((uint32_t)i);
-        std::stable_sort(out.order.begin() + (std::ptrdiff_t)first, out.order.end(),
-                         [&](uint32_t a, uint32_t b) { return order_key(deg[a], ntri[a]) < order_key(deg[b], ntri[b]); });
-    }
     out.n = n;
     out.m = m;
     out.n_free = n_free;

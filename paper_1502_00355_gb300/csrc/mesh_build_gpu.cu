@@ -355,15 +355,17 @@ sls_status scan_u32(const unsigned *in, int64_t len, uint32_t *out, unsigned lon
     return SLS_OK;
 }
 
-// One block of kOrderTile threads per tile: the number of free nodes.
+// One block of kOrderTile threads per tile: the number of free nodes (of
+// colour c, when colour is given).
 __global__ void __launch_bounds__(kOrderTile) order_count_kernel(const uint32_t *__restrict__ node_off,
                                                                   const uint32_t *__restrict__ adj, int64_t n,
+                                                                  const int32_t *__restrict__ colour, int32_t c,
                                                                   unsigned *cnt)
 {
     const int64_t i = (int64_t)blockIdx.x * kOrderTile + threadIdx.x;
-    const bool fr = i < n && !(adj[node_off[i]] & 0x80000000u);
-    const int c = __syncthreads_count(fr);
-    if (threadIdx.x == 0) cnt[blockIdx.x] = (unsigned)c;
+    const bool fr = i < n && !(adj[node_off[i]] & 0x80000000u) && (!colour || colour[i] == c);
+    const int k = __syncthreads_count(fr);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = (unsigned)k;
 }
 
 // One block of kOrderTile threads per tile: the tile's free nodes sorted by
@@ -371,6 +373,7 @@ __global__ void __launch_bounds__(kOrderTile) order_count_kernel(const uint32_t 
 // offset.
 __global__ void __launch_bounds__(kOrderTile) order_sort_kernel(const uint32_t *__restrict__ node_off,
                                                                  const uint32_t *__restrict__ adj, int64_t n,
+                                                                 const int32_t *__restrict__ colour, int32_t c,
                                                                  const uint32_t *__restrict__ tile_off,
                                                                  uint32_t *order)
 {
@@ -380,7 +383,8 @@ __global__ void __launch_bounds__(kOrderTile) order_sort_kernel(const uint32_t *
     uint32_t k = 0xffffffffu;  // fixed nodes and the tail sort last
     if (i < n) {
         const uint32_t meta = adj[node_off[i]];
-        if (!(meta & 0x80000000u)) k = (order_key(meta & 0xffffu, (meta >> 16) & 0x7fffu) << 10) | tid;
+        if (!(meta & 0x80000000u) && (!colour || colour[i] == c))
+            k = (order_key(meta & 0xffffu, (meta >> 16) & 0x7fffu) << 10) | tid;
     }
     key[tid] = k;
     __syncthreads();
@@ -402,9 +406,78 @@ __global__ void __launch_bounds__(kOrderTile) order_sort_kernel(const uint32_t *
     if (tid < nf) order[tile_off[blockIdx.x] + tid] = (uint32_t)(blockIdx.x * kOrderTile) + (key[tid] & 1023u);
 }
 
-}  // namespace
+// splitmix64 (Steele, Lea and Flood, OOPSLA 2014): the colouring priorities.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
 
-sls_status build_node_order(sls_mesh *M, cudaStream_t s)
+// Initial colouring state: -2 fixed, -1 free and uncoloured.
+__global__ void colour_init_kernel(const uint32_t *__restrict__ node_off, const uint32_t *__restrict__ adj,
+                                   int64_t n, int32_t *colour)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        colour[i] = (adj[node_off[i]] & 0x80000000u) ? -2 : -1;
+}
+
+// One Jones-Plassmann round.  cur is the state at the start of the round,
+// next a copy of it that receives the winners' colours: an uncoloured free
+// node wins when its (priority, index) exceeds that of every uncoloured free
+// neighbour, and takes the smallest colour no neighbour holds.  Winners are
+// never neighbours, so the round's result does not depend on thread order.
+__global__ void colour_round_kernel(const uint32_t *__restrict__ node_off, const uint32_t *__restrict__ adj,
+                                    int64_t n, unsigned long long seed, const int32_t *__restrict__ cur,
+                                    int32_t *next, unsigned long long *left, unsigned *flags)
+{
+    unsigned long long cnt = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (cur[i] != -1) continue;
+        const uint32_t *w = adj + node_off[i];
+        const uint32_t deg = w[0] & 0xffffu;
+        const unsigned long long pi = splitmix64(seed + (unsigned long long)i);
+        bool win = true;
+        unsigned long long used = 0ull;
+        for (uint32_t k = 0; k < deg; ++k) {
+            const uint32_t j = w[1 + k];
+            const int32_t cj = cur[j];
+            if (cj == -1) {
+                const unsigned long long pj = splitmix64(seed + (unsigned long long)j);
+                if (!(pi > pj || (pi == pj && (uint32_t)i > j))) win = false;
+            } else if (cj >= 0) {
+                if (cj < 64) used |= 1ull << cj;
+                else atomicOr(flags, 1u);
+            }
+        }
+        if (win) {
+            if (used == ~0ull) atomicOr(flags, 1u);  // would need a colour past 63
+            next[i] = __ffsll((long long)~used) - 1;
+        } else {
+            cnt += 1ull;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(left, cnt);
+}
+
+__global__ void colour_max_kernel(const int32_t *__restrict__ colour, int64_t n, int *cmax)
+{
+    int m = -1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        m = max(m, colour[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(cmax, m);
+}
+
+// One segment of the processing order: the free nodes of colour c (all free
+// nodes when colour is null), tile by tile, by (degree, triangles, id).
+sls_status order_segment(sls_mesh *M, const int32_t *colour, int32_t c, uint32_t *dst, int64_t expect,
+                         int64_t *count, cudaStream_t s)
 {
     const int64_t n = M->n;
     const int64_t tiles = (n + kOrderTile - 1) / kOrderTile;
@@ -414,15 +487,72 @@ sls_status build_node_order(sls_mesh *M, cudaStream_t s)
     sls_status st;
     if ((st = dalloc(b_cnt, (size_t)tiles, &cnt, "order counts")) != SLS_OK) return st;
     if ((st = dalloc(b_off, (size_t)tiles + 1, &off, "order offsets")) != SLS_OK) return st;
-    order_count_kernel<<<(unsigned)tiles, kOrderTile, 0, s>>>(M->node_off, M->adj, n, cnt);
+    order_count_kernel<<<(unsigned)tiles, kOrderTile, 0, s>>>(M->node_off, M->adj, n, colour, c, cnt);
     GB_TRY(cudaGetLastError(), "order count");
     unsigned long long total = 0ull;
     if ((st = scan_u32(cnt, tiles, off, &total, s)) != SLS_OK) return st;
-    if ((int64_t)total != M->n_free) return fail(SLS_ERR_INVALID, "free-node count mismatch in the processing order");
-    GB_TRY(cudaMalloc(&M->node_order, sizeof(uint32_t) * (size_t)(total > 0 ? total : 1)), "processing order");
-    order_sort_kernel<<<(unsigned)tiles, kOrderTile, 0, s>>>(M->node_off, M->adj, n, off, M->node_order);
-    GB_TRY(cudaGetLastError(), "order sort");
+    if (expect >= 0 && (int64_t)total > expect) return fail(SLS_ERR_INVALID, "processing order overflow");
+    if (total > 0) {
+        order_sort_kernel<<<(unsigned)tiles, kOrderTile, 0, s>>>(M->node_off, M->adj, n, colour, c, off, dst);
+        GB_TRY(cudaGetLastError(), "order sort");
+    }
     GB_TRY(cudaStreamSynchronize(s), "processing order");
+    *count = (int64_t)total;
+    return SLS_OK;
+}
+
+}  // namespace
+
+sls_status build_node_order(sls_mesh *M, cudaStream_t s)
+{
+    // Form A visits every node in index order: no list needed
+    if (M->opt.form != 1) return SLS_OK;
+    GB_TRY(cudaMalloc(&M->node_order, sizeof(uint32_t) * (size_t)(M->n_free > 0 ? M->n_free : 1)),
+           "processing order");
+    // Form B: Jones-Plassmann colouring, then one order segment per colour
+    const int64_t n = M->n;
+    DevBuf b_col[2], b_cnt;
+    int32_t *col[2] = {nullptr, nullptr};
+    unsigned long long *cnt = nullptr;
+    sls_status st;
+    for (int k = 0; k < 2; ++k)
+        if ((st = dalloc(b_col[k], (size_t)n, &col[k], "colours")) != SLS_OK) return st;
+    if ((st = dalloc(b_cnt, 2, &cnt, "colouring counters")) != SLS_OK) return st;
+    const int grid = device_sm_count() * 8, block = 256;
+    colour_init_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, n, col[0]);
+    GB_TRY(cudaGetLastError(), "colouring");
+    int cur = 0;
+    unsigned long long h[2] = {0ull, 0ull};
+    for (int round = 0;; ++round) {
+        if (round > 100000) return fail(SLS_ERR_INVALID, "colouring did not finish");
+        GB_TRY(cudaMemcpyAsync(col[cur ^ 1], col[cur], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s),
+               "colouring");
+        GB_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s), "colouring");
+        colour_round_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, n, kColourSeed, col[cur], col[cur ^ 1], cnt,
+                                                   reinterpret_cast<unsigned *>(cnt + 1));
+        GB_TRY(cudaGetLastError(), "colouring round");
+        GB_TRY(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, s), "colouring");
+        GB_TRY(cudaStreamSynchronize(s), "colouring");
+        cur ^= 1;
+        if (h[1]) return fail(SLS_ERR_INVALID, "the coloured form needs more than 64 colours");
+        if (h[0] == 0ull) break;
+    }
+    int *cmax = reinterpret_cast<int *>(cnt);
+    GB_TRY(cudaMemsetAsync(cmax, 0xff, sizeof(int), s), "colouring");
+    colour_max_kernel<<<grid, block, 0, s>>>(col[cur], n, cmax);
+    int hmax = -1;
+    GB_TRY(cudaMemcpyAsync(&hmax, cmax, sizeof hmax, cudaMemcpyDeviceToHost, s), "colouring");
+    GB_TRY(cudaStreamSynchronize(s), "colouring");
+    const int nc = hmax + 1;
+    M->colour_off.assign((size_t)nc + 1, 0);
+    int64_t at = 0;
+    for (int c = 0; c < nc; ++c) {
+        int64_t k = 0;
+        if ((st = order_segment(M, col[cur], c, M->node_order + at, M->n_free - at, &k, s)) != SLS_OK) return st;
+        at += k;
+        M->colour_off[(size_t)c + 1] = at;
+    }
+    if (at != M->n_free) return fail(SLS_ERR_INVALID, "free-node count mismatch in the colouring");
     return SLS_OK;
 }
 

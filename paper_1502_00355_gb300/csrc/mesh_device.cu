@@ -57,7 +57,7 @@ static sls_status mesh_setup(sls_mesh *M, const sls_options &o)
     M->cur = 0;
     M->block = o.block_size;
     M->screened = o.kernel != SLS_KERNEL_FP64;
-    if (M->screened && (M->block < 64 || M->block > 256)) M->block = 256;  // the screened kernel is built for <= 256
+    if (M->screened && M->block > 128) M->block = 128;  // the screened kernel is built for <= 128
     M->grid = device_sm_count() * (M->screened ? pass_screened_occupancy(o.layout, M->block)
                                                : pass_fp64_occupancy(o.layout, M->block));
     return SLS_OK;
@@ -193,22 +193,43 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
     a.tol_active = tol_active ? 1 : 0;
     a.thr_bits = thr_bits;
     a.accept = M->accept;
-    const int cb = M->opt.copy_back;
+    const bool form_b = M->opt.form == 1;
+    const int cb = form_b ? 0 : M->opt.copy_back;
     const int chunk = M->opt.passes_per_check;
+    const int nseg = (int)M->colour_off.size() - 1;
     int launched = 0;
+    int64_t kernels = 0;
     while (launched < max_iter) {
         const int end = std::min(launched + chunk, (int)max_iter);
         for (int q = launched; q < end; ++q) {
+            a.q = q;
+            if (form_b) {
+                // Form B: the colour classes in turn, in place (Eq. 3)
+                a.in = a.out = M->xy[M->cur];
+                for (int c = 0; c < nseg; ++c) {
+                    a.order = M->node_order + M->colour_off[c];
+                    a.norder = M->colour_off[c + 1] - M->colour_off[c];
+                    SLS_CUDA_TRY(M->screened ? launch_pass_screened(a, M->opt.layout, M->block, M->grid, M->stream)
+                                             : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream),
+                                 "pass kernel");
+                    ++kernels;
+                }
+                continue;
+            }
             const int src = cb ? M->cur : (M->cur ^ (q & 1));
             a.in = M->xy[src];
             a.out = M->xy[src ^ 1];
-            a.q = q;
+            a.order = nullptr;
+            a.norder = 0;
             SLS_CUDA_TRY(M->screened ? launch_pass_screened(a, M->opt.layout, M->block, M->grid, M->stream)
                                      : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream),
                          "pass kernel");
-            if (cb)
+            ++kernels;
+            if (cb) {
                 SLS_CUDA_TRY(launch_copy_back(M->xy[src ^ 1], M->xy[src], 2 * M->n, M->stats, q,
                                               device_sm_count() * 4, M->stream), "copy-back kernel");
+                ++kernels;
+            }
         }
         launched = end;
         if (tol_active && launched < max_iter) {
@@ -227,14 +248,14 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
     while (it < launched && hs[it].executed) fb += (long long)hs[it++].fallbacks;
     info.iterations = it;
     info.fp64_fallbacks = fb;
-    info.launches = (int64_t)launched * (cb ? 2 : 1);
+    info.launches = kernels;
     if (it > 0) {
         const PassStats &l = hs[it - 1];
         info.accepted_last = (int64_t)l.nacc;
         std::memcpy(&info.max_d2_last, &l.maxd2_bits, sizeof(double));
         info.converged = (tol_active && l.maxd2_bits < thr_bits) ? 1 : 0;
     }
-    if (!cb) M->cur ^= (it & 1);
+    if (!cb && !form_b) M->cur ^= (it & 1);
     return SLS_OK;
 }
 

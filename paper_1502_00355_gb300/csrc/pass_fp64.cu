@@ -26,7 +26,10 @@ __global__ void __launch_bounds__(1024) pass_fp64_kernel(PassArgs a)
 
     unsigned long long best = 0ull, nacc = 0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    // every node, or (a colour class of Form B) the listed free nodes
+    const int64_t cnt = a.order ? a.norder : a.n;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
+        const int64_t i = a.order ? (int64_t)__ldg(a.order + j) : j;
         const uint32_t meta = __ldg(a.adj + __ldg(a.node_off + i));
         if (meta & kMetaFixed) {
             if (a.accept) a.accept[i] = 0;

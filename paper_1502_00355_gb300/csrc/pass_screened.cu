@@ -362,7 +362,8 @@ __device__ __forceinline__ void warp_flush_stats(PassStats *st, unsigned long lo
 }
 
 template <int LAYOUT>
-__global__ void __launch_bounds__(256, 3) pass_screened_kernel(PassArgs a)
+// 128 threads, 7 blocks per SM: 28 warps per SM (72 registers a thread).
+__global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;
@@ -377,19 +378,25 @@ __global__ void __launch_bounds__(256, 3) pass_screened_kernel(PassArgs a)
     float2 *loc = s_loc + tid;
     Deferred *wq = s_q + 64 * warp;
     int qn = 0;  // warp-uniform queue length
-    const int64_t nwtiles = (a.norder + 31) / 32;
+    // every node in index order, or (a colour class of Form B) the listed nodes
+    const int64_t cnt = a.order ? a.norder : a.n;
+    const int64_t nwtiles = (cnt + 31) / 32;
     const int64_t wstride = (int64_t)gridDim.x * (nthr >> 5);
     for (int64_t wt = (int64_t)blockIdx.x * (nthr >> 5) + warp; wt < nwtiles; wt += wstride) {
         const int64_t j = wt * 32 + lane;
         Deferred d;
-        const bool defer = j < a.norder && screen_node<LAYOUT>(a, __ldg(a.order + j), loc, nthr, d, best, nacc);
+        const bool defer =
+            j < cnt && screen_node<LAYOUT>(a, a.order ? (int64_t)__ldg(a.order + j) : j, loc, nthr, d, best, nacc);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
         nfb += defer ? 1ull : 0ull;
-        __syncwarp();
-        drain_queue<LAYOUT>(a, wq, qn, false, best, nacc);
+        if (qn >= 32) {  // warp-uniform; entries written by other lanes must be visible
+            __syncwarp();
+            drain_queue<LAYOUT>(a, wq, qn, false, best, nacc);
+        }
     }
+    __syncwarp();
     drain_queue<LAYOUT>(a, wq, qn, true, best, nacc);
     block_reduce_stats(a.stats + a.q, best, nacc, nfb);
 }
@@ -427,6 +434,7 @@ __global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restri
         const int job = t < t1 ? tasks[t].job : -2;
         if (job != cur_job) {
             if (cur_job >= 0 && active) {
+                __syncwarp();
                 drain_queue<LAYOUT>(a, wq, qn, true, best, nacc);
                 warp_flush_stats(a.stats + a.q, best, nacc, nfb);
             }
@@ -447,8 +455,8 @@ __global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restri
                 a.node_off = J->node_off;
                 a.adj = J->adj;
                 a.n = J->n;
-                a.order = J->order;
-                a.norder = J->norder;
+                a.order = nullptr;
+                a.norder = 0;
                 a.stats = st;
                 a.q = q;
                 a.strict = J->strict;
@@ -460,15 +468,17 @@ __global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restri
         if (!active) continue;
         const int64_t first = tasks[t].first;
         if (first == 0 && lane == 0) a.stats[a.q].executed = 1u;
-        const int64_t j = first + lane;
+        const int64_t i = first + lane;
         Deferred d;
-        const bool defer = j < a.norder && screen_node<LAYOUT>(a, __ldg(a.order + j), loc, nthr, d, best, nacc);
+        const bool defer = i < a.n && screen_node<LAYOUT>(a, i, loc, nthr, d, best, nacc);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
         nfb += defer ? 1ull : 0ull;
-        __syncwarp();
-        drain_queue<LAYOUT>(a, wq, qn, false, best, nacc);
+        if (qn >= 32) {
+            __syncwarp();
+            drain_queue<LAYOUT>(a, wq, qn, false, best, nacc);
+        }
     }
 }
 

@@ -47,7 +47,7 @@ struct ServerJob {
     size_t footprint = 0;
     // device state
     double *d_xy[2] = {nullptr, nullptr};
-    uint32_t *d_off = nullptr, *d_adj = nullptr, *d_order = nullptr;
+    uint32_t *d_off = nullptr, *d_adj = nullptr;
     PassStats *d_stats = nullptr;
     cudaEvent_t uploaded = nullptr;
     int base_round = 0;
@@ -104,8 +104,7 @@ namespace {
 size_t job_footprint(const HostMesh &hm, int32_t max_iter)
 {
     return 2 * sizeof(double) * 2 * (size_t)hm.n + sizeof(uint32_t) * (size_t)(hm.n + 1) +
-           sizeof(uint32_t) * hm.adj.size() + sizeof(uint32_t) * hm.order.size() +
-           sizeof(PassStats) * (size_t)std::max(1, max_iter);
+           sizeof(uint32_t) * hm.adj.size() + sizeof(PassStats) * (size_t)std::max(1, max_iter);
 }
 
 void builder_loop(sls_server *S)
@@ -147,11 +146,10 @@ void free_job_device(sls_server *S, ServerJob &J)
     cudaFreeAsync(J.d_xy[1], S->stream);
     cudaFreeAsync(J.d_off, S->stream);
     cudaFreeAsync(J.d_adj, S->stream);
-    cudaFreeAsync(J.d_order, S->stream);
     cudaFreeAsync(J.d_stats, S->stream);
     if (J.uploaded) cudaEventDestroy(J.uploaded);
     J.d_xy[0] = J.d_xy[1] = nullptr;
-    J.d_off = J.d_adj = J.d_order = nullptr;
+    J.d_off = J.d_adj = nullptr;
     J.d_stats = nullptr;
     J.uploaded = nullptr;
 }
@@ -167,14 +165,11 @@ bool start_upload(sls_server *S, ServerJob &J)
               cudaMallocAsync((void **)&J.d_xy[1], cbytes, cs) == cudaSuccess &&
               cudaMallocAsync((void **)&J.d_off, sizeof(uint32_t) * (n + 1), cs) == cudaSuccess &&
               cudaMallocAsync((void **)&J.d_adj, sizeof(uint32_t) * std::max<size_t>(1, J.hm.adj.size()), cs) == cudaSuccess &&
-              cudaMallocAsync((void **)&J.d_order, sizeof(uint32_t) * std::max<size_t>(1, J.hm.order.size()), cs) == cudaSuccess &&
               cudaMallocAsync((void **)&J.d_stats, sizeof(PassStats) * std::max(1, J.max_iter), cs) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(J.d_xy[0], J.xy.data(), cbytes, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
          cudaMemcpyAsync(J.d_xy[1], J.xy.data(), cbytes, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
          cudaMemcpyAsync(J.d_off, J.hm.node_off.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice, cs) == cudaSuccess &&
          cudaMemcpyAsync(J.d_adj, J.hm.adj.data(), sizeof(uint32_t) * J.hm.adj.size(), cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-         (J.hm.order.empty() ||
-          cudaMemcpyAsync(J.d_order, J.hm.order.data(), sizeof(uint32_t) * J.hm.order.size(), cudaMemcpyHostToDevice, cs) == cudaSuccess) &&
          cudaMemsetAsync(J.d_stats, 0, sizeof(PassStats) * std::max(1, J.max_iter), cs) == cudaSuccess &&
          cudaEventCreateWithFlags(&J.uploaded, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventRecord(J.uploaded, cs) == cudaSuccess;
@@ -229,7 +224,7 @@ bool rebuild_table(sls_server *S)
 {
     const size_t na = S->active.size();
     size_t ntasks = 0;
-    for (auto &J : S->active) ntasks += (size_t)((std::max<int64_t>(1, (int64_t)J->hm.order.size()) + 31) / 32);
+    for (auto &J : S->active) ntasks += (size_t)((J->hm.n + 31) / 32);
     if (!grow_pair(S->h_jobs, S->d_jobs, S->jobs_cap, na) ||
         !grow_pair(S->h_tasks, S->d_tasks, S->tasks_cap, std::max<size_t>(1, ntasks)))
         return false;
@@ -241,8 +236,6 @@ bool rebuild_table(sls_server *S)
         D.xy[1] = J.d_xy[1];
         D.node_off = J.d_off;
         D.adj = J.d_adj;
-        D.order = J.d_order;
-        D.norder = (int64_t)J.hm.order.size();
         D.n = J.hm.n;
         D.stats = J.d_stats;
         const double thr = tolerance_threshold(J.tol, J.hm.diag);
@@ -254,8 +247,7 @@ bool rebuild_table(sls_server *S)
         D.cur0 = 0;
         D.pad = 0;
         D.accept = nullptr;
-        // at least one task, which marks the job's passes as executed
-        for (int64_t f = 0; f < std::max<int64_t>(1, D.norder); f += 32) S->h_tasks[t++] = WarpTask{(int32_t)j, (int32_t)f};
+        for (int64_t f = 0; f < J.hm.n; f += 32) S->h_tasks[t++] = WarpTask{(int32_t)j, (int32_t)f};
     }
     S->ntasks = (int64_t)t;
     return cudaMemcpyAsync(S->d_jobs, S->h_jobs, sizeof(JobDesc) * na, cudaMemcpyHostToDevice, S->stream) == cudaSuccess &&
@@ -414,6 +406,7 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
     sls_options o = resolve_options(opt);
     sls_status st = check_options(o);
     if (st != SLS_OK) return st;
+    if (o.form != 0) return fail(SLS_ERR_INVALID, "the server runs Form A only");
     auto S = std::make_unique<sls_server>();
     S->opt = o;
     S->max_queue = max_queue;

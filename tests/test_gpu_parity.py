@@ -136,6 +136,24 @@ def test_hexagon_and_fan_cases(sls, kernel):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("boundary", ["given", "derived"])
+def test_delaunay_random_points(sls, kernel, boundary):
+    # the paper's mesh family: valence 3 to 12 and more, hull nodes fixed,
+    # some nodes past the screened kernel's degree limit
+    mesh = meshgen.delaunay_random(20000, 17, numbering="random")
+    got, ref = _run_both(sls, mesh, 40, boundary=boundary, kernel=kernel)
+    _check(got, ref, f"delaunay-20k-{boundary}")
+
+
+def test_delaunay_paper_size_to_tolerance(sls):
+    # 100,000 points (the paper's largest mesh), smoothed to the tolerance
+    mesh = meshgen.delaunay_mesh()
+    got, ref = _run_both(sls, mesh, 300, tol=1e-9, omp=True)
+    _check(got, ref, "delaunay-100k")
+    assert got[1]["converged"] == 1
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_histogram_matches_oracle(sls, kernel):
     mesh = meshgen.jittered_grid(100, 80, 0.45, 31)
     om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary)

@@ -1,5 +1,6 @@
 """The synthetic input generator: shapes, seeds and structure the workloads rely on."""
 import numpy as np
+import pytest
 
 import meshgen
 
@@ -59,3 +60,42 @@ def test_batch_and_serve_specs():
     reqs = meshgen.serve_requests(50)
     t = [r[0] for r in reqs]
     assert t == sorted(t) and all(10 <= r[3] <= 200 for r in reqs)
+
+
+def test_delaunay_random_is_a_ccw_delaunay_triangulation():
+    pytest.importorskip("scipy")
+    m = meshgen.delaunay_random(300, 21, numbering="random")
+    p = m.xy
+    a, b, c = p[m.tri[:, 0]], p[m.tri[:, 1]], p[m.tri[:, 2]]
+    cross = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    assert (cross > 0).all()
+    # Euler: a triangulated convex polygon with h hull vertices has 2n - h - 2 triangles
+    h = int(m.boundary.sum())
+    assert m.m == 2 * m.n - h - 2
+    # every hull edge lies in one triangle, every other edge in two; the fixed
+    # nodes are exactly the ends of one-triangle edges
+    e = np.sort(np.concatenate([m.tri[:, [0, 1]], m.tri[:, [1, 2]], m.tri[:, [2, 0]]]), axis=1)
+    _, cnt = np.unique(e, axis=0, return_counts=True)
+    assert set(cnt.tolist()) == {1, 2}
+    ends = np.unique(np.unique(e, axis=0)[cnt == 1])
+    assert np.array_equal(np.flatnonzero(m.boundary), ends)
+    # empty circumcircles (brute force): the in-circle determinant of every
+    # other point against every CCW triangle is not positive
+    def rows(V):
+        d = V[None, :] - p
+        return np.stack([d[:, 0], d[:, 1], d[:, 0] ** 2 + d[:, 1] ** 2], 1)
+    for t in range(m.m):
+        incircle = np.linalg.det(np.stack([rows(a[t]), rows(b[t]), rows(c[t])], 1))
+        others = np.ones(m.n, bool)
+        others[m.tri[t]] = False
+        assert (incircle[others] < 1e-12).all(), t
+
+
+def test_delaunay_numberings_are_permutations_of_one_mesh():
+    pytest.importorskip("scipy")
+    a = meshgen.delaunay_random(2000, 5, numbering="morton")
+    r = meshgen.delaunay_random(2000, 5, numbering="random")
+    assert np.array_equal(meshgen.unpermute(a.xy, a), meshgen.unpermute(r.xy, r))
+    ta = np.sort(np.sort(a.perm.argsort()[a.tri], axis=1), axis=0)
+    tr = np.sort(np.sort(r.perm.argsort()[r.tri], axis=1), axis=0)
+    assert np.array_equal(np.unique(ta, axis=0), np.unique(tr, axis=0))
