@@ -101,11 +101,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes_per_pass(n, n_free, adj_words):
+def algorithmic_bytes_per_pass(n, n_free, adj_words, coord_bytes=16):
     """Bytes one pass must move at ideal reuse: every node's coordinates read
-    once (16 B), every free node's new coordinates written (16 B), the node
-    offsets (4 B per node + 1) and the adjacency words (4 B each)."""
-    return 16 * n + 16 * n_free + 4 * (n + 1) + 4 * adj_words
+    once (16 B in FP64, 8 B in binary32), every free node's new coordinates
+    written, the node offsets (4 B per node + 1) and the adjacency words (4 B
+    each)."""
+    return coord_bytes * n + coord_bytes * n_free + 4 * (n + 1) + 4 * adj_words
 
 
 def adjacency_words(mesh):
@@ -132,16 +133,22 @@ def reduce_over_ranks(ms: float, updates: float, device="cpu"):
     return float(t.item()), float(u.item())
 
 
-def cpu_oracle_rate(mesh, passes: int):
-    """Times `passes` Form-A passes of the OpenMP oracle on all host cores."""
+def cpu_oracle_rate(mesh, passes: int, precision: int = 64, form: str = "A"):
+    """Times `passes` passes of the oracle: Form A FP64 on all host cores
+    (OpenMP build); binary32 or Form B on one core (the oracle's sequential
+    loops)."""
     import oracle
-    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary, openmp=True)
-    xy = mesh.xy.copy()
+    omp = precision == 64 and form == "A"
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary, openmp=omp)
     t0 = time.perf_counter()
-    for _ in range(passes):
-        xy, _, _, _ = om.sweep(xy)
+    if omp:
+        xy = mesh.xy.copy()
+        for _ in range(passes):
+            xy, _, _, _ = om.sweep(xy)
+    else:
+        om.smooth(mesh.xy, passes, form=form, precision=precision)
     dt = time.perf_counter() - t0
-    return mesh.n * passes / dt, dt, os.cpu_count()
+    return mesh.n * passes / dt, dt, (os.cpu_count() if omp else 1)
 
 
 def run_reference(args, mesh, workload):
@@ -298,6 +305,10 @@ def main():
     ap.add_argument("--cpu-passes", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
+                    help="64: FP64 (the headline); 32: binary32, the paper's precision")
+    ap.add_argument("--form", default="A", choices=["A", "B"],
+                    help="A: Jacobi (the headline); B: multicolour Gauss-Seidel")
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch(args)
@@ -324,7 +335,8 @@ def main():
     sls.lib()
 
     stream = torch.cuda.Stream()
-    g = sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, kernel=args.kernel, stream=stream.cuda_stream)
+    variant = dict(kernel=args.kernel, precision=args.precision, form=args.form)
+    g = sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, stream=stream.cuda_stream, **variant)
     xy0 = torch.from_numpy(mesh.xy).to("cuda")
     torch.cuda.synchronize()
 
@@ -371,7 +383,7 @@ def main():
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with sls.Mesh(xy_h, tri_h, bnd_h, kernel=args.kernel) as h:
+        with sls.Mesh(xy_h, tri_h, bnd_h, **variant) as h:
             inf = h.smooth(MAX_PASSES, TOL)
             h.coords(out=out_host)
         e2e_times.append(time.perf_counter() - t0)
@@ -382,27 +394,31 @@ def main():
     # DRAM bytes of one pass-kernel launch: ncu dram__bytes_read.sum +
     # dram__bytes_write.sum of a 2048x2048 capture of this kernel (361.0 MB),
     # scaled by the node count to the 4096x4096 mesh; None for other sizes
-    traffic = 1443.8e6 if (mesh.n == 4096 * 4096 and args.kernel == "auto") else None
+    headline = args.kernel == "auto" and args.precision == 64 and args.form == "A"
+    traffic = 1443.8e6 if (mesh.n == 4096 * 4096 and headline) else None
     adj_words = adjacency_words(mesh)
-    bytes_pass = algorithmic_bytes_per_pass(mesh.n, g.n_free, adj_words)
+    bytes_pass = algorithmic_bytes_per_pass(mesh.n, g.n_free, adj_words, 16 if args.precision == 64 else 8)
     achieved = bytes_pass / (pass_ms * 1e-3) / 1e9
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, cores = cpu_oracle_rate(mesh, args.cpu_passes)
+        rate, dt, cores = cpu_oracle_rate(mesh, args.cpu_passes, args.precision, args.form)
         cpu = {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_passes} Form-A passes of the same mesh from its initial coordinates "
-                         f"({dt:.1f} s, OpenMP oracle build on all host cores)"}
+               "sample": f"{args.cpu_passes} Form-{args.form} passes ({'FP64' if args.precision == 64 else 'binary32'}) "
+                         f"of the same mesh from its initial coordinates ({dt:.1f} s, "
+                         f"{'OpenMP oracle build on all host cores' if cores > 1 else 'sequential oracle'})"}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if args.precision == 64 else "f32",
                "data": "synthetic",
                "config": {"workload": workload, "n": mesh.n, "m": mesh.m, "n_free": g.n_free,
                           "max_passes": MAX_PASSES, "tol_rel": TOL,
                           "passes_per_step": passes / args.steps, "kernel": args.kernel,
-                          "layout": "aos", "form": "ping-pong",
+                          "layout": "aos",
+                          "form": "A (Jacobi, ping-pong)" if args.form == "A" else "B (coloured Gauss-Seidel, in place)",
                           "l2": "inputs larger than L2 (no flush)",
                           "parallelism": "replicas" if world > 1 else "single"},
                "e2e": {"value": e2e_value, "unit": "node-updates/s",

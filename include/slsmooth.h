@@ -92,6 +92,11 @@ typedef struct sls_options {
                               updates the colour classes in turn, in place.  copy_back is
                               ignored.  Single meshes only: the batched, served and
                               allocation-free forms reject it.                               */
+    int32_t precision;     /* 64 (default; 0 means 64): FP64 coordinates and arithmetic,
+                              results bit-identical to the FP64 definition.  32: binary32
+                              coordinates (the given doubles rounded to nearest) and every
+                              operation one binary32 round-to-nearest operation in the same
+                              order, the paper's precision (Section 4).  Single meshes only. */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle    */
 } sls_options;
 

@@ -17,6 +17,8 @@ Functions and the part of the paper they follow:
   * ``OracleMesh.colouring`` - Jones-Plassmann colouring of the free nodes
   * ``OracleMesh.smooth(form="B")`` - Form B (Eq. 3) as multicolour
                            Gauss-Seidel: colour classes in turn, in place
+  * ``OracleMesh.smooth(precision=32)`` - both forms in binary32, the
+                           paper's precision (Section 4, reading R11)
   * ``OracleMesh.histogram`` - quality histogram of all triangles
 
 Parity pins (tests/test_oracle_*.py): closed forms of alpha, the regular
@@ -93,6 +95,11 @@ def _lib(openmp: bool = False) -> C.CDLL:
             lib.orc_sweep_coloured.argtypes = [P, P, P, I32, C.c_int, P, P, P]
             lib.orc_smooth_coloured.restype = C.c_int
             lib.orc_smooth_coloured.argtypes = [P, P, P, I32, I32, D, C.c_int, P, P, P, P, P]
+            lib.orc32_alpha.restype = C.c_float
+            lib.orc32_alpha.argtypes = [C.c_float] * 6
+            lib.orc32_sweep.argtypes = [P, P, P, P, I32, C.c_int, P, P, P]
+            lib.orc32_smooth.restype = C.c_int
+            lib.orc32_smooth.argtypes = [P, P, P, I32, I32, D, C.c_int, P, P, P, P, P]
             _LIBS[openmp] = lib
         return _LIBS[openmp]
 
@@ -104,6 +111,11 @@ def _ptr(a: np.ndarray | None):
 def alpha(ax, ay, bx, by, cx, cy) -> float:
     """Lee and Lo's alpha of triangle (a, b, c) in that vertex order (Section 3.3.1)."""
     return _lib().orc_alpha(ax, ay, bx, by, cx, cy)
+
+
+def alpha32(ax, ay, bx, by, cx, cy) -> np.float32:
+    """The same alpha in binary32 arithmetic (R11); arguments are rounded to float."""
+    return np.float32(_lib().orc32_alpha(*[float(np.float32(v)) for v in (ax, ay, bx, by, cx, cy)]))
 
 
 class OracleError(RuntimeError):
@@ -198,15 +210,31 @@ class OracleMesh:
                                      C.byref(maxd2), C.byref(nacc))
         return xy, acc, maxd2.value, nacc.value
 
-    def smooth(self, xy, max_iter: int, tol: float = 0.0, strict: bool = False, form: str = "A"):
-        """Iterate from xy (Form A, or Form B in colour order).  Returns
-        (xy_final, info dict, accept mask of the last pass)."""
-        xy = np.array(xy, dtype=np.float64, copy=True).reshape(-1, 2)
+    def smooth(self, xy, max_iter: int, tol: float = 0.0, strict: bool = False, form: str = "A",
+               precision: int = 64):
+        """Iterate from xy (Form A, or Form B in colour order; FP64, or binary32
+        with xy rounded to float first).  Returns (xy_final as float64 --
+        binary32 values widened exactly --, info dict, accept mask of the last
+        pass)."""
         acc = np.zeros(self.n, np.uint8)
         it = C.c_int32(0)
         conv = C.c_int32(0)
         nacc = C.c_int64(0)
         maxd2 = C.c_double(0.0)
+        if precision == 32:
+            x32 = np.array(xy, dtype=np.float64).reshape(-1, 2).astype(np.float32)
+            col, nc = (None, 0) if form == "A" else self.colouring()[:2]
+            rc = self._lib.orc32_smooth(self._h, _ptr(x32), _ptr(col), int(nc), int(max_iter), float(tol),
+                                        int(strict), _ptr(acc), C.byref(it), C.byref(conv), C.byref(nacc),
+                                        C.byref(maxd2))
+            if rc != 0:
+                raise OracleError(rc)
+            info = dict(iterations=it.value, converged=conv.value, accepted_last=nacc.value,
+                        maxd2_last=maxd2.value)
+            return x32.astype(np.float64), info, acc
+        if precision != 64:
+            raise ValueError(precision)
+        xy = np.array(xy, dtype=np.float64, copy=True).reshape(-1, 2)
         if form == "A":
             rc = self._lib.orc_smooth(self._h, _ptr(xy), int(max_iter), float(tol), int(strict),
                                       _ptr(acc), C.byref(it), C.byref(conv), C.byref(nacc),

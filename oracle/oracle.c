@@ -525,6 +525,135 @@ int orc_smooth_coloured(const orc_mesh *M, double *xy, const int32_t *colour, in
     return ORC_OK;
 }
 
+/* ---- Forms A and B in binary32, the paper's precision (Section 4) --------
+ * Reading R11: the coordinates are held as binary32 values (the creation
+ * coordinates rounded to nearest) and every operation is one binary32
+ * round-to-nearest operation in the order of the FP64 definition above, with
+ * K32 the float nearest to 2*sqrt(3).  Summation order (R1) and constraints
+ * are those of the mesh; the stop rule compares the largest squared move,
+ * widened exactly to double, with (tol * D)^2 computed in double. */
+static const float ORC_K32 = 3.46410161514f;
+
+float orc32_alpha(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    float e1x = bx - ax, e1y = by - ay;
+    float e2x = cx - ax, e2y = cy - ay;
+    float e3x = cx - bx, e3y = cy - by;
+    float cross = e1x * e2y - e1y * e2x;
+    float l1 = e1x * e1x + e1y * e1y;
+    float l2 = e2x * e2x + e2y * e2y;
+    float l3 = e3x * e3x + e3y * e3y;
+    float s = (l1 + l2) + l3;
+    if (s > 0.0f)
+        return (ORC_K32 * cross) / s;
+    return 0.0f;
+}
+
+/* One node of one pass in binary32 (the steps of node_update). */
+static void node_update32(const orc_mesh *M, const float *xy, int64_t i, int strict, float *out_x,
+                          float *out_y, int *accepted, float *d2)
+{
+    float xi = xy[2 * i], yi = xy[2 * i + 1];
+    *out_x = xi;
+    *out_y = yi;
+    *accepted = 0;
+    *d2 = 0.0f;
+    if (M->fixed[i]) return;
+    int64_t b = M->nbr_ptr[i], e = M->nbr_ptr[i + 1];
+    int64_t N = e - b;
+    float sx = xy[2 * (int64_t)M->nbr[b]];
+    float sy = xy[2 * (int64_t)M->nbr[b] + 1];
+    for (int64_t k = b + 1; k < e; k++) {
+        sx = sx + xy[2 * (int64_t)M->nbr[k]];
+        sy = sy + xy[2 * (int64_t)M->nbr[k] + 1];
+    }
+    float cx = sx / (float)N;
+    float cy = sy / (float)N;
+    float q_old = 0.0f, q_new = 0.0f;
+    int first = 1;
+    for (int64_t k = M->tri_ptr[i]; k < M->tri_ptr[i + 1]; k++) {
+        int64_t t = M->tri_of[k];
+        float px[3], py[3], mx[3], my[3];
+        for (int c = 0; c < 3; c++) {
+            int64_t v = M->tri[3 * t + c];
+            px[c] = xy[2 * v];
+            py[c] = xy[2 * v + 1];
+            mx[c] = (v == i) ? cx : px[c];
+            my[c] = (v == i) ? cy : py[c];
+        }
+        float qb = orc32_alpha(px[0], py[0], px[1], py[1], px[2], py[2]);
+        float qa = orc32_alpha(mx[0], my[0], mx[1], my[1], mx[2], my[2]);
+        if (first || qb < q_old) q_old = qb;
+        if (first || qa < q_new) q_new = qa;
+        first = 0;
+    }
+    int ok = strict ? (q_new > q_old) : (q_new >= q_old);
+    if (ok) {
+        float dx = cx - xi, dy = cy - yi;
+        *out_x = cx;
+        *out_y = cy;
+        *accepted = 1;
+        *d2 = dx * dx + dy * dy;
+    }
+}
+
+/* One binary32 sweep: Form A into xy_next (colour == NULL), or Form B in
+ * colour order in place (xy_next == xy). */
+void orc32_sweep(const orc_mesh *M, float *xy, float *xy_next, const int32_t *colour, int32_t ncolours,
+                 int strict, uint8_t *accept, float *maxd2_out, int64_t *nacc_out)
+{
+    float maxd2 = 0.0f;
+    int64_t nacc = 0;
+    int64_t n = M->n;
+    if (accept)
+        for (int64_t i = 0; i < n; i++) accept[i] = 0;
+    int32_t classes = colour ? ncolours : 1;
+    for (int32_t c = 0; c < classes; c++) {
+        for (int64_t i = 0; i < n; i++) {
+            if (colour && colour[i] != c) continue;
+            float x, y, d2;
+            int acc;
+            node_update32(M, xy, i, strict, &x, &y, &acc, &d2);
+            xy_next[2 * i] = x;
+            xy_next[2 * i + 1] = y;
+            if (accept) accept[i] = (uint8_t)acc;
+            nacc += acc;
+            if (d2 > maxd2) maxd2 = d2;
+        }
+    }
+    *maxd2_out = maxd2;
+    *nacc_out = nacc;
+}
+
+/* The binary32 iteration (Form A with copy-back, or Form B in place). */
+int orc32_smooth(const orc_mesh *M, float *xy, const int32_t *colour, int32_t ncolours, int32_t max_iter,
+                 double tol, int strict, uint8_t *accept_last, int32_t *iterations, int32_t *converged,
+                 int64_t *nacc_last, double *maxd2_last)
+{
+    int64_t n = M->n;
+    float *next = colour ? xy : (float *)malloc(sizeof(float) * 2 * (n > 0 ? n : 1));
+    if (!next) return ORC_NOMEM;
+    double thr = (tol * M->diag) * (tol * M->diag); /* R4 */
+    int32_t it = 0, conv = 0;
+    int64_t nacc = 0;
+    float maxd2 = 0.0f;
+    while (it < max_iter) {
+        orc32_sweep(M, xy, next, colour, ncolours, strict, accept_last, &maxd2, &nacc);
+        if (!colour) memcpy(xy, next, sizeof(float) * 2 * n);
+        it += 1;
+        if (tol > 0.0 && (double)maxd2 < thr) {
+            conv = 1;
+            break;
+        }
+    }
+    if (!colour) free(next);
+    *iterations = it;
+    *converged = conv;
+    *nacc_last = nacc;
+    *maxd2_last = (double)maxd2;
+    return ORC_OK;
+}
+
 /* Quality histogram of all triangles at coordinates xy (Section 3.3.1).
  * bin = floor((q - lo) / (hi - lo) * nbins), clamped to [0, nbins-1];
  * qmean sums the qualities in triangle order. */

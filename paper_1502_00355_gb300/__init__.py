@@ -34,7 +34,7 @@ class Options(C.Structure):
     _fields_ = [("accept_strict", C.c_int32), ("copy_back", C.c_int32), ("layout", C.c_int32),
                 ("kernel", C.c_int32), ("record_accept", C.c_int32), ("block_size", C.c_int32),
                 ("l2_window", C.c_int32), ("passes_per_check", C.c_int32), ("host_build", C.c_int32),
-                ("form", C.c_int32), ("stream", C.c_void_p)]
+                ("form", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -112,7 +112,7 @@ def _p(a: np.ndarray | None):
 
 def make_options(*, strict=False, copy_back=False, layout="aos", kernel="auto", record_accept=False,
                  block_size=0, l2_window=False, passes_per_check=0, host_build=False, form="A",
-                 stream=None) -> Options:
+                 precision=64, stream=None) -> Options:
     o = Options()
     lib().sls_default_options(C.byref(o))
     o.accept_strict = int(bool(strict))
@@ -125,6 +125,7 @@ def make_options(*, strict=False, copy_back=False, layout="aos", kernel="auto", 
     o.passes_per_check = int(passes_per_check)
     o.host_build = int(bool(host_build))
     o.form = {"A": 0, "B": 1}[form]
+    o.precision = int(precision)
     o.stream = None if stream is None else C.c_void_p(int(stream))
     return o
 

@@ -33,13 +33,14 @@ int device_sm_count()
     return sms > 0 ? sms : 1;
 }
 
-static sls_options g_defaults = {0, 0, 0, SLS_KERNEL_AUTO, 0, 0, 0, 16, 0, 0, nullptr};
+static sls_options g_defaults = {0, 0, 0, SLS_KERNEL_AUTO, 0, 0, 0, 16, 0, 0, 64, nullptr};
 
 sls_options resolve_options(const sls_options *opt)
 {
     sls_options o = opt ? *opt : g_defaults;
     if (o.block_size <= 0) o.block_size = 256;
     if (o.passes_per_check <= 0) o.passes_per_check = 16;
+    if (o.precision == 0) o.precision = 64;
     return o;
 }
 
@@ -51,6 +52,7 @@ sls_status check_options(const sls_options &o)
     if (o.block_size % 32 != 0 || o.block_size > 1024)
         return fail(SLS_ERR_INVALID, "block_size must be a multiple of 32, at most 1024");
     if (o.form != 0 && o.form != 1) return fail(SLS_ERR_INVALID, "form must be 0 (Form A) or 1 (Form B)");
+    if (o.precision != 32 && o.precision != 64) return fail(SLS_ERR_INVALID, "precision must be 32 or 64");
     return SLS_OK;
 }
 

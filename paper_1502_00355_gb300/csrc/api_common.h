@@ -17,7 +17,8 @@ struct sls_mesh {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    double *xy[2] = {nullptr, nullptr};  // the two coordinate arrays (2n doubles each)
+    double *xy[2] = {nullptr, nullptr};  // the two coordinate arrays (2n doubles each, 2n floats when f32)
+    bool f32 = false;             // binary32 coordinates and arithmetic
     int cur = 0;                  // which of the two holds the current coordinates
     uint32_t *node_off = nullptr; // n+1
     uint32_t *adj = nullptr;      // node_off[n] words

@@ -220,7 +220,8 @@ sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *i
         if (meshes[j]->device != dev) return fail(SLS_ERR_INVALID, "all meshes must live on the current device");
         if (meshes[j]->opt.layout != meshes[0]->opt.layout)
             return fail(SLS_ERR_INVALID, "all meshes of a batch must use the same layout");
-        if (meshes[j]->opt.form != 0) return fail(SLS_ERR_INVALID, "the batched form runs Form A meshes only");
+        if (meshes[j]->opt.form != 0 || meshes[j]->f32)
+            return fail(SLS_ERR_INVALID, "the batched form runs FP64 Form A meshes only");
         if (iters[j] < 0) return fail(SLS_ERR_INVALID, "iteration counts must be >= 0");
         if (tol_rel && std::isnan(tol_rel[j])) return fail(SLS_ERR_INVALID, "tolerance is NaN");
         for (int i = 0; i < j; ++i)

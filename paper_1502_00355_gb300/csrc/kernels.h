@@ -35,6 +35,16 @@ cudaError_t launch_histogram(const double *xy, int layout, int64_t n, const int3
                              unsigned long long *counts, unsigned long long *qmin_key,
                              double *qsum, int grid, cudaStream_t s);
 
+// One pass in binary32 (pass_f32.cu): a.in / a.out hold floats.
+cudaError_t launch_pass_f32(const PassArgs &a, int layout, int block, int grid, cudaStream_t s);
+int pass_f32_occupancy(int layout, int block);
+// Copy-back form of the binary32 pass (count floats; skipped when pass q was skipped).
+cudaError_t launch_copy_back_f32(const float *src, float *dst, int64_t count, const PassStats *stats, int q,
+                                 int grid, cudaStream_t s);
+// Interleaved doubles -> floats in a layout (round to nearest), and back (exact).
+cudaError_t launch_narrow(const double *aos, float *dst, int64_t n, int layout, int grid, cudaStream_t s);
+cudaError_t launch_widen(const float *src, double *aos, int64_t n, int layout, int grid, cudaStream_t s);
+
 // Layout conversions on the device (SoA <-> interleaved).
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int64_t n, int grid, cudaStream_t s);

@@ -55,11 +55,43 @@ static sls_status mesh_setup(sls_mesh *M, const sls_options &o)
         SLS_CUDA_TRY(cudaMemsetAsync(M->accept, 0, (size_t)M->n, M->stream), "cudaMemset");
     }
     M->cur = 0;
+    M->f32 = o.precision == 32;
     M->block = o.block_size;
-    M->screened = o.kernel != SLS_KERNEL_FP64;
+    M->screened = o.kernel != SLS_KERNEL_FP64 && !M->f32;
     if (M->screened && M->block > 128) M->block = 128;  // the screened kernel is built for <= 128
-    M->grid = device_sm_count() * (M->screened ? pass_screened_occupancy(o.layout, M->block)
-                                               : pass_fp64_occupancy(o.layout, M->block));
+    if (M->f32 && M->block > 256) M->block = 256;  // the binary32 kernel is built for <= 256
+    M->grid = device_sm_count() * (M->f32        ? pass_f32_occupancy(o.layout, M->block)
+                                   : M->screened ? pass_screened_occupancy(o.layout, M->block)
+                                                 : pass_fp64_occupancy(o.layout, M->block));
+    return SLS_OK;
+}
+
+// Binary32 meshes: the coordinates, built as doubles in the mesh's layout,
+// are rounded to floats; the two arrays then hold 2n floats each.
+static sls_status narrow_coordinates(sls_mesh *M)
+{
+    if (!M->f32) return SLS_OK;
+    const size_t fbytes = sizeof(float) * 2 * (size_t)M->n;
+    float *f[2] = {nullptr, nullptr};
+    sls_status st;
+    for (int b = 0; b < 2; ++b)
+        if ((st = dev_alloc((void **)&f[b], fbytes, "coordinates")) != SLS_OK) {
+            cudaFree(f[0]);
+            return st;
+        }
+    const int grid = device_sm_count() * 4;
+    const double *aos = M->xy[0];
+    if (M->opt.layout == 1) {  // interleave first (xy[1] holds a copy of xy[0])
+        SLS_CUDA_TRY(launch_soa_to_aos(M->xy[0], M->xy[1], M->n, grid, M->stream), "interleave");
+        aos = M->xy[1];
+    }
+    SLS_CUDA_TRY(launch_narrow(aos, f[0], M->n, M->opt.layout, grid, M->stream), "narrow");
+    SLS_CUDA_TRY(cudaMemcpyAsync(f[1], f[0], fbytes, cudaMemcpyDeviceToDevice, M->stream), "copy coordinates");
+    SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "narrow");
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(M->xy[b]);
+        M->xy[b] = reinterpret_cast<double *>(f[b]);
+    }
     return SLS_OK;
 }
 
@@ -96,6 +128,7 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
     SLS_CUDA_TRY(cudaMemcpyAsync(M->tri, tri, sizeof(int32_t) * 3 * (size_t)M->m,
                                  cudaMemcpyHostToDevice, M->stream), "upload triangles");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload");
+    if ((st = narrow_coordinates(M)) != SLS_OK) return st;
     return build_node_order(M, M->stream);
 }
 
@@ -141,6 +174,7 @@ sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const
         SLS_CUDA_TRY(launch_aos_to_soa(M->xy[1], M->xy[0], n, device_sm_count() * 4, M->stream), "split");
     SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[1], M->xy[0], cbytes, cudaMemcpyDeviceToDevice, M->stream), "copy coordinates");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "mesh create");
+    if ((st = narrow_coordinates(M)) != SLS_OK) return st;
     return build_node_order(M, M->stream);
 }
 
@@ -158,6 +192,13 @@ void mesh_release(sls_mesh *M)
     if (M->h_stats) cudaFreeHost(M->h_stats);
     if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
     M->stream = nullptr;
+}
+
+static cudaError_t launch_pass(const sls_mesh *M, const PassArgs &a)
+{
+    if (M->f32) return launch_pass_f32(a, M->opt.layout, M->block, M->grid, M->stream);
+    return M->screened ? launch_pass_screened(a, M->opt.layout, M->block, M->grid, M->stream)
+                       : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream);
 }
 
 sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info)
@@ -209,9 +250,7 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
                 for (int c = 0; c < nseg; ++c) {
                     a.order = M->node_order + M->colour_off[c];
                     a.norder = M->colour_off[c + 1] - M->colour_off[c];
-                    SLS_CUDA_TRY(M->screened ? launch_pass_screened(a, M->opt.layout, M->block, M->grid, M->stream)
-                                             : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream),
-                                 "pass kernel");
+                    SLS_CUDA_TRY(launch_pass(M, a), "pass kernel");
                     ++kernels;
                 }
                 continue;
@@ -221,13 +260,15 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
             a.out = M->xy[src ^ 1];
             a.order = nullptr;
             a.norder = 0;
-            SLS_CUDA_TRY(M->screened ? launch_pass_screened(a, M->opt.layout, M->block, M->grid, M->stream)
-                                     : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream),
-                         "pass kernel");
+            SLS_CUDA_TRY(launch_pass(M, a), "pass kernel");
             ++kernels;
             if (cb) {
-                SLS_CUDA_TRY(launch_copy_back(M->xy[src ^ 1], M->xy[src], 2 * M->n, M->stats, q,
-                                              device_sm_count() * 4, M->stream), "copy-back kernel");
+                SLS_CUDA_TRY(M->f32 ? launch_copy_back_f32(reinterpret_cast<const float *>(M->xy[src ^ 1]),
+                                                           reinterpret_cast<float *>(M->xy[src]), 2 * M->n,
+                                                           M->stats, q, device_sm_count() * 4, M->stream)
+                                    : launch_copy_back(M->xy[src ^ 1], M->xy[src], 2 * M->n, M->stats, q,
+                                                       device_sm_count() * 4, M->stream),
+                             "copy-back kernel");
                 ++kernels;
             }
         }
@@ -263,7 +304,22 @@ sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device)
 {
     const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
     const double *src = M->xy[M->cur];
-    if (M->opt.layout == 0) {
+    if (M->f32) {
+        const float *f = reinterpret_cast<const float *>(src);
+        if (dst_is_device) {
+            SLS_CUDA_TRY(launch_widen(f, xy_out, M->n, M->opt.layout, device_sm_count() * 4, M->stream), "widen");
+        } else {
+            std::vector<float> tmp(2 * (size_t)M->n);
+            SLS_CUDA_TRY(cudaMemcpyAsync(tmp.data(), f, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost,
+                                         M->stream), "download");
+            SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "download");
+            for (int64_t i = 0; i < M->n; ++i) {
+                const bool soa = M->opt.layout == 1;
+                xy_out[2 * i] = (double)tmp[soa ? i : 2 * i];
+                xy_out[2 * i + 1] = (double)tmp[soa ? M->n + i : 2 * i + 1];
+            }
+        }
+    } else if (M->opt.layout == 0) {
         SLS_CUDA_TRY(cudaMemcpyAsync(xy_out, src, cbytes,
                                      dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                      M->stream), "download coordinates");
@@ -284,6 +340,25 @@ sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device)
 
 sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
 {
+    if (M->f32) {
+        const size_t fbytes = sizeof(float) * 2 * (size_t)M->n;
+        float *f = reinterpret_cast<float *>(M->xy[M->cur]);
+        if (src_is_device) {
+            SLS_CUDA_TRY(launch_narrow(xy, f, M->n, M->opt.layout, device_sm_count() * 4, M->stream), "narrow");
+        } else {
+            std::vector<float> tmp(2 * (size_t)M->n);
+            for (int64_t i = 0; i < M->n; ++i) {
+                const bool soa = M->opt.layout == 1;
+                tmp[soa ? i : 2 * i] = (float)xy[2 * i];
+                tmp[soa ? M->n + i : 2 * i + 1] = (float)xy[2 * i + 1];
+            }
+            SLS_CUDA_TRY(cudaMemcpyAsync(f, tmp.data(), fbytes, cudaMemcpyHostToDevice, M->stream), "upload");
+            SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload");
+        }
+        SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[M->cur ^ 1], f, fbytes, cudaMemcpyDeviceToDevice, M->stream), "copy");
+        SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "set coordinates");
+        return SLS_OK;
+    }
     const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
     if (src_is_device) {
         if (M->opt.layout == 0)
@@ -312,21 +387,39 @@ sls_status mesh_histogram(const sls_mesh *M, int nbins, double lo, double hi, in
     unsigned long long *d_counts = nullptr, *d_key = nullptr;
     double *d_sum = nullptr;
     sls_status st;
-    if ((st = dev_alloc((void **)&d_counts, sizeof(unsigned long long) * (nbins + 2), "histogram")) != SLS_OK)
+    // binary32 meshes: alpha (FP64) of the coordinates widened exactly
+    double *wide = nullptr;
+    const double *hx = M->xy[M->cur];
+    int hlayout = M->opt.layout;
+    if (M->f32) {
+        if ((st = dev_alloc((void **)&wide, sizeof(double) * 2 * (size_t)M->n, "histogram")) != SLS_OK) return st;
+        cudaError_t e0 = launch_widen(reinterpret_cast<const float *>(M->xy[M->cur]), wide, M->n, M->opt.layout,
+                                      device_sm_count() * 4, M->stream);
+        if (e0 != cudaSuccess) {
+            cudaFree(wide);
+            return cuda_fail(e0, "widen");
+        }
+        hx = wide;
+        hlayout = 0;
+    }
+    if ((st = dev_alloc((void **)&d_counts, sizeof(unsigned long long) * (nbins + 2), "histogram")) != SLS_OK) {
+        cudaFree(wide);
         return st;
+    }
     d_key = d_counts + nbins;
     d_sum = reinterpret_cast<double *>(d_counts + nbins + 1);
     std::vector<unsigned long long> h(nbins + 2);
     cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * (nbins + 2), M->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_key, 0xff, sizeof(unsigned long long), M->stream);
     if (e == cudaSuccess)
-        e = launch_histogram(M->xy[M->cur], M->opt.layout, M->n, M->tri, M->m, nbins, lo, hi, d_counts,
-                             d_key, d_sum, device_sm_count() * 8, M->stream);
+        e = launch_histogram(hx, hlayout, M->n, M->tri, M->m, nbins, lo, hi, d_counts, d_key, d_sum,
+                             device_sm_count() * 8, M->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), d_counts, sizeof(unsigned long long) * (nbins + 2),
                             cudaMemcpyDeviceToHost, M->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
     cudaFree(d_counts);
+    cudaFree(wide);
     if (e != cudaSuccess) return cuda_fail(e, "histogram");
     for (int b = 0; b < nbins; ++b) counts[b] = (int64_t)h[b];
     unsigned long long key = h[nbins];

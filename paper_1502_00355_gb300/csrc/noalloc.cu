@@ -59,7 +59,7 @@ extern "C" sls_status sls_smooth_noalloc(const sls_mesh *M, double *xy_in, doubl
     if (!M || !xy_in || !xy_out) return fail(SLS_ERR_INVALID, "mesh, xy_in and xy_out must not be NULL");
     if (xy_in == xy_out) return fail(SLS_ERR_INVALID, "xy_in and xy_out must be distinct buffers");
     if (M->opt.layout != 0) return fail(SLS_ERR_INVALID, "sls_smooth_noalloc needs a mesh with the AoS layout");
-    if (M->opt.form != 0) return fail(SLS_ERR_INVALID, "sls_smooth_noalloc runs Form A only");
+    if (M->opt.form != 0 || M->f32) return fail(SLS_ERR_INVALID, "sls_smooth_noalloc runs FP64 Form A only");
     if (max_iter < 0 || max_iter > kNoAllocMaxPasses)
         return fail(SLS_ERR_INVALID, "max_iter must be in [0, SLS_NOALLOC_MAX_PASSES] for sls_smooth_noalloc");
     if (std::isnan(tol_rel)) return fail(SLS_ERR_INVALID, "tol_rel is NaN");

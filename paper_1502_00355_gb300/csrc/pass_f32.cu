@@ -1,0 +1,231 @@
+// pass_f32.cu -- Smart Laplacian passes in binary32, the paper's precision
+// (Section 4).
+//
+// The coordinates are stored as floats and every step is one binary32
+// round-to-nearest operation in the order of the FP64 definition: the
+// neighbour sum of Eq. 2 in the stored order, the division by the neighbour
+// count, alpha of Section 3.3.1 with the same expression tree, the accept test
+// of Section 3.3.4, the squared move.  Nothing here needs screening: the
+// exact binary32 evaluation is itself cheap on the FP32 pipe, so one thread
+// takes one node from start to end.
+#include "kernels.h"
+
+namespace sls {
+
+namespace {
+
+template <int LAYOUT>
+struct Coords32;
+
+template <>
+struct Coords32<0> {  // AoS: one float2 per node
+    static __device__ __forceinline__ float2 get(const float *p, int64_t, int64_t i)
+    {
+        return __ldg(reinterpret_cast<const float2 *>(p) + i);
+    }
+    static __device__ __forceinline__ void put(float *p, int64_t, int64_t i, float2 v)
+    {
+        reinterpret_cast<float2 *>(p)[i] = v;
+    }
+};
+
+template <>
+struct Coords32<1> {  // SoA: x[n] then y[n]
+    static __device__ __forceinline__ float2 get(const float *p, int64_t n, int64_t i)
+    {
+        return make_float2(__ldg(p + i), __ldg(p + n + i));
+    }
+    static __device__ __forceinline__ void put(float *p, int64_t n, int64_t i, float2 v)
+    {
+        p[i] = v.x;
+        p[n + i] = v.y;
+    }
+};
+
+// alpha of the triangle (a, b, c) in stored order, in binary32, with the
+// tree of the FP64 definition; every operation an explicit round-to-nearest
+// intrinsic (no contraction).  K is the float nearest to 2 sqrt(3).
+__device__ __forceinline__ float alpha_f32(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    const float kTwoSqrt3 = 3.46410161514f;
+    const float e1x = __fsub_rn(bx, ax), e1y = __fsub_rn(by, ay);
+    const float e2x = __fsub_rn(cx, ax), e2y = __fsub_rn(cy, ay);
+    const float e3x = __fsub_rn(cx, bx), e3y = __fsub_rn(cy, by);
+    const float cross = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
+    const float l1 = __fadd_rn(__fmul_rn(e1x, e1x), __fmul_rn(e1y, e1y));
+    const float l2 = __fadd_rn(__fmul_rn(e2x, e2x), __fmul_rn(e2y, e2y));
+    const float l3 = __fadd_rn(__fmul_rn(e3x, e3x), __fmul_rn(e3y, e3y));
+    const float s = __fadd_rn(__fadd_rn(l1, l2), l3);
+    return s > 0.0f ? __fdiv_rn(__fmul_rn(kTwoSqrt3, cross), s) : 0.0f;
+}
+
+// alpha of an incident triangle with the moving node at x: the stored vertex
+// order puts x in slot `slot` and the two neighbours A, B in the other two
+// slots in order.  The points are picked with selects, so every lane runs
+// the same instructions whatever its slot.
+__device__ __forceinline__ float alpha_slot(uint32_t slot, float2 x, float2 A, float2 B)
+{
+    const float2 a = slot == 0u ? x : A;
+    const float2 b = slot == 0u ? A : (slot == 1u ? x : B);
+    const float2 c = slot == 2u ? x : B;
+    return alpha_f32(a.x, a.y, b.x, b.y, c.x, c.y);
+}
+
+constexpr int kRingMax = 16;  // neighbours kept in shared memory; larger rings read global memory
+
+// One pass over every node (a.order null) or over the listed nodes (one
+// colour class of Form B, in place).  a.in / a.out hold floats.  Each thread
+// keeps its node's ring in its own column of a shared buffer (stride: block).
+template <int LAYOUT>
+__global__ void __launch_bounds__(256) pass_f32_kernel(PassArgs a)
+{
+    __shared__ float2 s_ring[kRingMax * 256];
+    if (pass_is_skipped(a.stats, a.q, a.tol_active, a.thr_bits)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.stats[a.q].executed = 1u;
+    const float *in = reinterpret_cast<const float *>(a.in);
+    float *out = reinterpret_cast<float *>(a.out);
+    float2 *ring = s_ring + threadIdx.x;
+    const int rs = blockDim.x;
+
+    unsigned best = 0u;  // bits of the largest squared move (non-negative floats order as integers)
+    unsigned long long nacc = 0ull;
+    const int64_t cnt = a.order ? a.norder : a.n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
+        const int64_t i = a.order ? (int64_t)__ldg(a.order + j) : j;
+        const uint32_t off = __ldg(a.node_off + i);
+        const uint32_t meta = __ldg(a.adj + off);
+        if (meta & kMetaFixed) {
+            if (a.accept) a.accept[i] = 0;
+            continue;
+        }
+        const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
+        const uint32_t *nb = a.adj + off + 1;
+        const bool kept = deg <= (uint32_t)kRingMax;
+        const float2 p = Coords32<LAYOUT>::get(in, a.n, i);
+        // Eq. 2 in the stored order
+        float2 v = Coords32<LAYOUT>::get(in, a.n, __ldg(nb));
+        if (kept) ring[0] = v;
+        float sx = v.x, sy = v.y;
+        for (uint32_t k = 1; k < deg; ++k) {
+            v = Coords32<LAYOUT>::get(in, a.n, __ldg(nb + k));
+            if (kept) ring[k * rs] = v;
+            sx = __fadd_rn(sx, v.x);
+            sy = __fadd_rn(sy, v.y);
+        }
+        const float fd = (float)deg;
+        const float2 c = make_float2(__fdiv_rn(sx, fd), __fdiv_rn(sy, fd));
+        bool ok;
+        if (__float_as_uint(c.x) == __float_as_uint(p.x) && __float_as_uint(c.y) == __float_as_uint(p.y)) {
+            ok = !a.strict;  // the centre is the node itself: q_new == q_old
+        } else {
+            float q_old = 0.0f, q_new = 0.0f;
+            for (uint32_t t = 0; t < ntri; ++t) {
+                const uint32_t code = __ldg(nb + deg + t);
+                const uint32_t fa = code_first(code), fb = code_second(code);
+                const float2 A = kept ? ring[fa * rs] : Coords32<LAYOUT>::get(in, a.n, __ldg(nb + fa));
+                const float2 B = kept ? ring[fb * rs] : Coords32<LAYOUT>::get(in, a.n, __ldg(nb + fb));
+                const uint32_t slot = code_slot(code);
+                const float qo = alpha_slot(slot, p, A, B);
+                const float qn = alpha_slot(slot, c, A, B);
+                if (t == 0 || qo < q_old) q_old = qo;
+                if (t == 0 || qn < q_new) q_new = qn;
+            }
+            ok = a.strict ? (q_new > q_old) : (q_new >= q_old);
+        }
+        float2 o = p;
+        if (ok) {
+            const float dx = __fsub_rn(c.x, p.x), dy = __fsub_rn(c.y, p.y);
+            const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+            best = max(best, __float_as_uint(d2));
+            nacc += 1ull;
+            o = c;
+        }
+        Coords32<LAYOUT>::put(out, a.n, i, o);
+        if (a.accept) a.accept[i] = ok ? 1 : 0;
+    }
+    // widened exactly to double, so the pass records compare like FP64 ones
+    const unsigned long long b64 = (unsigned long long)__double_as_longlong((double)__uint_as_float(best));
+    block_reduce_stats(a.stats + a.q, b64, nacc, 0ull);
+}
+
+__global__ void copy_back_f32_kernel(const float *__restrict__ src, float *__restrict__ dst, int64_t count,
+                                     const PassStats *stats, int q)
+{
+    if (stats[q].executed == 0u) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride)
+        dst[k] = __ldg(src + k);
+}
+
+// interleaved doubles -> floats in the mesh's layout (round to nearest)
+__global__ void narrow_kernel(const double2 *__restrict__ aos, float *dst, int64_t n, int layout)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double2 v = __ldg(aos + i);
+        const float x = __double2float_rn(v.x), y = __double2float_rn(v.y);
+        if (layout == 0) {
+            reinterpret_cast<float2 *>(dst)[i] = make_float2(x, y);
+        } else {
+            dst[i] = x;
+            dst[n + i] = y;
+        }
+    }
+}
+
+// floats in the mesh's layout -> interleaved doubles (exact)
+__global__ void widen_kernel(const float *__restrict__ src, double2 *aos, int64_t n, int layout)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float x, y;
+        if (layout == 0) {
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(src) + i);
+            x = v.x;
+            y = v.y;
+        } else {
+            x = __ldg(src + i);
+            y = __ldg(src + n + i);
+        }
+        aos[i] = make_double2((double)x, (double)y);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pass_f32(const PassArgs &a, int layout, int block, int grid, cudaStream_t s)
+{
+    if (layout == 0) pass_f32_kernel<0><<<grid, block, 0, s>>>(a);
+    else pass_f32_kernel<1><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int pass_f32_occupancy(int layout, int block)
+{
+    int nb = 0;
+    if (layout == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_f32_kernel<0>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_f32_kernel<1>, block, 0);
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_copy_back_f32(const float *src, float *dst, int64_t count, const PassStats *stats, int q,
+                                 int grid, cudaStream_t s)
+{
+    copy_back_f32_kernel<<<grid, 256, 0, s>>>(src, dst, count, stats, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(const double *aos, float *dst, int64_t n, int layout, int grid, cudaStream_t s)
+{
+    narrow_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const double2 *>(aos), dst, n, layout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const float *src, double *aos, int64_t n, int layout, int grid, cudaStream_t s)
+{
+    widen_kernel<<<grid, 256, 0, s>>>(src, reinterpret_cast<double2 *>(aos), n, layout);
+    return cudaGetLastError();
+}
+
+}  // namespace sls
