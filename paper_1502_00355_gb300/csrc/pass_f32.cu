@@ -8,6 +8,8 @@
 // of Section 3.3.4, the squared move.  Nothing here needs screening: the
 // exact binary32 evaluation is itself cheap on the FP32 pipe, so one thread
 // takes one node from start to end.
+#include <cfloat>
+
 #include "kernels.h"
 
 namespace sls {
@@ -59,23 +61,49 @@ __device__ __forceinline__ float alpha_f32(float ax, float ay, float bx, float b
     return s > 0.0f ? __fdiv_rn(__fmul_rn(kTwoSqrt3, cross), s) : 0.0f;
 }
 
-// alpha of an incident triangle with the moving node at x: the stored vertex
-// order puts x in slot `slot` and the two neighbours A, B in the other two
-// slots in order.  The points are picked with selects, so every lane runs
-// the same instructions whatever its slot.
-__device__ __forceinline__ float alpha_slot(uint32_t slot, float2 x, float2 A, float2 B)
+// alpha of an incident triangle (node i, neighbours A and B) with node i at
+// x, in the triangle's stored vertex order (i in slot `slot`, A before B).
+// The tree of alpha_f32 rewritten with u = x - A, w = x - B, v = B - A: every
+// edge of the stored order is one of +-u, +-w, +-v, and negation commutes
+// with rounding, so
+//   slot 0: cross = u x w,     s = (|u|^2 + |w|^2) + |v|^2
+//   slot 1: cross = u x v,     s = (|u|^2 + |v|^2) + |w|^2
+//   slot 2: cross = -(u x v),  s = (|v|^2 + |u|^2) + |w|^2 (the same sum)
+// give bit for bit the values of alpha_f32 on the reordered points.  v and
+// |v|^2 are shared by both positions of node i; no lane branches on slot.
+__device__ __forceinline__ float alpha_uvw(uint32_t slot, float2 x, float2 A, float2 B, float2 v, float lv)
 {
-    const float2 a = slot == 0u ? x : A;
-    const float2 b = slot == 0u ? A : (slot == 1u ? x : B);
-    const float2 c = slot == 2u ? x : B;
-    return alpha_f32(a.x, a.y, b.x, b.y, c.x, c.y);
+    const float kTwoSqrt3 = 3.46410161514f;
+    const float2 u = make_float2(__fsub_rn(x.x, A.x), __fsub_rn(x.y, A.y));
+    const float2 w = make_float2(__fsub_rn(x.x, B.x), __fsub_rn(x.y, B.y));
+    const float lu = __fadd_rn(__fmul_rn(u.x, u.x), __fmul_rn(u.y, u.y));
+    const float lw = __fadd_rn(__fmul_rn(w.x, w.x), __fmul_rn(w.y, w.y));
+    const bool s0 = slot == 0u;
+    const float2 z = s0 ? w : v;
+    float cross = __fsub_rn(__fmul_rn(u.x, z.y), __fmul_rn(u.y, z.x));
+    cross = slot == 2u ? -cross : cross;
+    const float s = __fadd_rn(__fadd_rn(lu, s0 ? lw : lv), s0 ? lv : lw);
+    return s > 0.0f ? __fdiv_rn(__fmul_rn(kTwoSqrt3, cross), s) : 0.0f;
 }
 
-constexpr int kRingMax = 16;  // neighbours kept in shared memory; larger rings read global memory
+template <int LAYOUT>
+__device__ __forceinline__ float alpha_at(const float *in, int64_t n, const uint32_t *nb, uint32_t code, float2 x)
+{
+    const float2 A = Coords32<LAYOUT>::get(in, n, __ldg(nb + code_first(code)));
+    const float2 B = Coords32<LAYOUT>::get(in, n, __ldg(nb + code_second(code)));
+    switch (code_slot(code)) {
+    case 0: return alpha_f32(x.x, x.y, A.x, A.y, B.x, B.y);
+    case 1: return alpha_f32(A.x, A.y, x.x, x.y, B.x, B.y);
+    default: return alpha_f32(A.x, A.y, B.x, B.y, x.x, x.y);
+    }
+}
+
+constexpr int kRingMax = 16;  // rings up to this size live in shared memory
 
 // One pass over every node (a.order null) or over the listed nodes (one
 // colour class of Form B, in place).  a.in / a.out hold floats.  Each thread
-// keeps its node's ring in its own column of a shared buffer (stride: block).
+// keeps its node's ring in its own column of a shared buffer (stride: block);
+// nodes with larger rings read their neighbours from global memory.
 template <int LAYOUT>
 __global__ void __launch_bounds__(256) pass_f32_kernel(PassArgs a)
 {
@@ -101,38 +129,60 @@ __global__ void __launch_bounds__(256) pass_f32_kernel(PassArgs a)
         }
         const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
         const uint32_t *nb = a.adj + off + 1;
-        const bool kept = deg <= (uint32_t)kRingMax;
         const float2 p = Coords32<LAYOUT>::get(in, a.n, i);
-        // Eq. 2 in the stored order
-        float2 v = Coords32<LAYOUT>::get(in, a.n, __ldg(nb));
-        if (kept) ring[0] = v;
-        float sx = v.x, sy = v.y;
-        for (uint32_t k = 1; k < deg; ++k) {
-            v = Coords32<LAYOUT>::get(in, a.n, __ldg(nb + k));
-            if (kept) ring[k * rs] = v;
-            sx = __fadd_rn(sx, v.x);
-            sy = __fadd_rn(sy, v.y);
-        }
-        const float fd = (float)deg;
-        const float2 c = make_float2(__fdiv_rn(sx, fd), __fdiv_rn(sy, fd));
-        bool ok;
-        if (__float_as_uint(c.x) == __float_as_uint(p.x) && __float_as_uint(c.y) == __float_as_uint(p.y)) {
-            ok = !a.strict;  // the centre is the node itself: q_new == q_old
-        } else {
-            float q_old = 0.0f, q_new = 0.0f;
-            for (uint32_t t = 0; t < ntri; ++t) {
-                const uint32_t code = __ldg(nb + deg + t);
-                const uint32_t fa = code_first(code), fb = code_second(code);
-                const float2 A = kept ? ring[fa * rs] : Coords32<LAYOUT>::get(in, a.n, __ldg(nb + fa));
-                const float2 B = kept ? ring[fb * rs] : Coords32<LAYOUT>::get(in, a.n, __ldg(nb + fb));
-                const uint32_t slot = code_slot(code);
-                const float qo = alpha_slot(slot, p, A, B);
-                const float qn = alpha_slot(slot, c, A, B);
-                if (t == 0 || qo < q_old) q_old = qo;
-                if (t == 0 || qn < q_new) q_new = qn;
+        float2 c;
+        float q_old = FLT_MAX, q_new = FLT_MAX;
+        bool tie;
+        if (deg <= (uint32_t)kRingMax) {
+            // Eq. 2 in the stored order; the ring goes to shared memory
+            float2 v = Coords32<LAYOUT>::get(in, a.n, __ldg(nb));
+            ring[0] = v;
+            float sx = v.x, sy = v.y;
+            for (uint32_t k = 1; k < deg; ++k) {
+                v = Coords32<LAYOUT>::get(in, a.n, __ldg(nb + k));
+                ring[k * rs] = v;
+                sx = __fadd_rn(sx, v.x);
+                sy = __fadd_rn(sy, v.y);
             }
-            ok = a.strict ? (q_new > q_old) : (q_new >= q_old);
+            const float fd = (float)deg;
+            c = make_float2(__fdiv_rn(sx, fd), __fdiv_rn(sy, fd));
+            tie = __float_as_uint(c.x) == __float_as_uint(p.x) && __float_as_uint(c.y) == __float_as_uint(p.y);
+            if (!tie) {
+                for (uint32_t t = 0; t < ntri; ++t) {
+                    const uint32_t code = __ldg(nb + deg + t);
+                    const float2 A = ring[code_first(code) * rs];
+                    const float2 B = ring[code_second(code) * rs];
+                    const float2 vv = make_float2(__fsub_rn(B.x, A.x), __fsub_rn(B.y, A.y));
+                    const float lv = __fadd_rn(__fmul_rn(vv.x, vv.x), __fmul_rn(vv.y, vv.y));
+                    const float qo = alpha_uvw(code_slot(code), p, A, B, vv, lv);
+                    const float qn = alpha_uvw(code_slot(code), c, A, B, vv, lv);
+                    q_old = (t == 0u || qo < q_old) ? qo : q_old;  // first wins, as in the definition
+                    q_new = (t == 0u || qn < q_new) ? qn : q_new;
+                }
+            }
+        } else {
+            float2 v = Coords32<LAYOUT>::get(in, a.n, __ldg(nb));
+            float sx = v.x, sy = v.y;
+            for (uint32_t k = 1; k < deg; ++k) {
+                v = Coords32<LAYOUT>::get(in, a.n, __ldg(nb + k));
+                sx = __fadd_rn(sx, v.x);
+                sy = __fadd_rn(sy, v.y);
+            }
+            const float fd = (float)deg;
+            c = make_float2(__fdiv_rn(sx, fd), __fdiv_rn(sy, fd));
+            tie = __float_as_uint(c.x) == __float_as_uint(p.x) && __float_as_uint(c.y) == __float_as_uint(p.y);
+            if (!tie) {
+                for (uint32_t t = 0; t < ntri; ++t) {
+                    const uint32_t code = __ldg(nb + deg + t);
+                    const float qo = alpha_at<LAYOUT>(in, a.n, nb, code, p);
+                    const float qn = alpha_at<LAYOUT>(in, a.n, nb, code, c);
+                    q_old = (t == 0u || qo < q_old) ? qo : q_old;
+                    q_new = (t == 0u || qn < q_new) ? qn : q_new;
+                }
+            }
         }
+        // a tie (the centre is the node itself) means q_new == q_old
+        const bool ok = tie ? !a.strict : (a.strict ? (q_new > q_old) : (q_new >= q_old));
         float2 o = p;
         if (ok) {
             const float dx = __fsub_rn(c.x, p.x), dy = __fsub_rn(c.y, p.y);
