@@ -56,18 +56,15 @@ __device__ __forceinline__ bool head_tail(unsigned long long b, float &hd, float
 {
     const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
     const unsigned e = (hw >> 20) & 0x7ffu;
-    if ((hw & 0x7fffffffu) == 0u && lw == 0u) {
-        hd = 0.0f;
-        tl = 0.0f;
-        return true;
-    }
-    if (e < 943u || e > 1149u) return false;
+    const bool zero = (hw & 0x7fffffffu) == 0u && lw == 0u;
     const unsigned sign = hw & 0x80000000u;
-    hd = __uint_as_float(sign | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    const float h = __uint_as_float(sign | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
     // tail bits 28..6 of the low word, value t * 2^(E - 46): exact in FP32
     const float t = __uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)) - 8388608.0f;
-    tl = __uint_as_float(__float_as_uint(t * __uint_as_float((e - 942u) << 23)) | sign);
-    return true;
+    const float l = __uint_as_float(__float_as_uint(t * __uint_as_float((e - 942u) << 23)) | sign);
+    hd = zero ? 0.0f : h;
+    tl = zero ? 0.0f : l;
+    return zero || (e - 943u <= 206u);  // [2^-80, 2^127) in magnitude, normal
 }
 
 // FP32 value of a double, truncated to 24 significant bits (relative error
@@ -77,8 +74,8 @@ __device__ __forceinline__ float trunc_float(double v)
     const unsigned long long b = dbits(v);
     const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
     const unsigned e = (hw >> 20) & 0x7ffu;
-    if (e < 897u || e > 1150u) return 0.0f;
-    return __uint_as_float((hw & 0x80000000u) | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    const float f = __uint_as_float((hw & 0x80000000u) | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    return e - 897u <= 253u ? f : 0.0f;
 }
 
 // Screening constants (unit roundoff e = 2^-24).  A local coordinate of a
@@ -152,10 +149,9 @@ __device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float
     const float g = R2 * inv;
     const float aa = fabsf(a);
     b = fmaf(kC1, aa, fmaf(kC3, aa, kC2) * g);
-    if (!(s > 0.0f) || !(g <= kGMax)) {  // degenerate or unscreenable: no information
-        a = 0.0f;
-        b = FLT_MAX;
-    }
+    const bool usable = (s > 0.0f) & (g <= kGMax);  // else degenerate or unscreenable: no information
+    a = usable ? a : 0.0f;
+    b = usable ? b : FLT_MAX;
 }
 
 // Second screen, for a node whose two minima are attained by the same single
@@ -231,7 +227,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
     const uint32_t *nb = a.adj + off + 1;
     const ulonglong2 pb = CoordBits<LAYOUT>::get(a.in, a.n, i);
     float phx, plx, phy, ply;
-    bool ok = head_tail(pb.x, phx, plx) && head_tail(pb.y, phy, ply);
+    bool ok = head_tail(pb.x, phx, plx) & head_tail(pb.y, phy, ply);
 
     // Eq. 2: FP64 sums in the stored order; local coordinates on the side
     ulonglong2 v = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb));
@@ -239,7 +235,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
     float rn = 0.0f, rmin = FLT_MAX;  // largest / smallest neighbour offset (max norm)
     for (uint32_t k = 0;;) {
         float hx, lx, hy, ly;
-        ok = ok && head_tail(v.x, hx, lx) && head_tail(v.y, hy, ly);
+        ok = ok & head_tail(v.x, hx, lx) & head_tail(v.y, hy, ly);
         const float2 L = make_float2((hx - phx) + (lx - plx), (hy - phy) + (ly - ply));
         loc[k * nthr] = L;
         const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
@@ -275,7 +271,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
     // Every triangle's R is at least rmin and at most max(rn, rC): inside this
     // range FP32 products neither under- nor overflow and the head/tail error
     // stays below e R, so the per-triangle bounds hold.
-    if (!(rmin >= 1e-14f && fmaxf(rn, rC) <= 1e15f && rmin * kLocalRange >= M)) return true;
+    if (!((rmin >= 1e-14f) & (fmaxf(rn, rC) <= 1e15f) & (rmin * kLocalRange >= M))) return true;
     MinTrack o, nw;
     o.init();
     nw.init();
