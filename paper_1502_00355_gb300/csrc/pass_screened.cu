@@ -16,10 +16,11 @@
 //  4. Otherwise alpha of every incident triangle, before and after the move, is
 //     evaluated in FP32 in a frame centred on the node, with a rigorous bound
 //     on its distance to the exact alpha of the FP64 inputs, wide enough to
-//     also cover the FP64 evaluation's own rounding.  The neighbours' local
-//     coordinates come from float head/tail splits of the doubles; the
-//     centre's offset from one exact FP64 subtraction.  When the intervals of
-//     q_new and q_old are disjoint the FP64 decision is known.
+//     also cover the FP64 evaluation's own rounding (one bound per side, valid
+//     for all of the node's triangles).  The neighbours' local coordinates
+//     come from float head/tail splits of the doubles; the centre's offset
+//     from one exact FP64 subtraction.  When the intervals of q_new and q_old
+//     are disjoint the FP64 decision is known.
 //  5. If one triangle alone attains both minima, a second screen takes the
 //     sign of alpha(centre) - alpha(node) from a formula in the move itself
 //     (no cancellation) and decides all but rounding-level ties.
@@ -102,58 +103,6 @@ constexpr float kGMax = 1000.0f;
 constexpr float kTwoSqrt3f = 3.46410161514f;
 constexpr float kLocalRange = 1048576.0f;  // 2^20: R * 2^20 >= M keeps the head/tail error below e R
 
-// Interval [minL, minU] that holds the FP64 minimum over the triangles.  If
-// every triangle other than the one with the lowest upper end U has its lower
-// end L above that U, that triangle alone attains the minimum (single()).
-struct MinTrack {
-    float minU, minL, minLother, lofBest;
-    uint32_t best;
-    __device__ __forceinline__ void init()
-    {
-        minU = minL = minLother = lofBest = FLT_MAX;
-        best = 0u;
-    }
-    __device__ __forceinline__ void add(float a, float b, uint32_t t)
-    {
-        const float U = a + b, L = a - b;
-        if (U < minU) {
-            minLother = fminf(minLother, lofBest);
-            minU = U;
-            lofBest = L;
-            best = t;
-        } else {
-            minLother = fminf(minLother, L);
-        }
-        minL = fminf(minL, L);
-    }
-    __device__ __forceinline__ bool single() const { return minLother > minU; }
-    // candidate set for the exact path: the single triangle, or all ntri of them
-    __device__ __forceinline__ uint32_t candidates(uint32_t ntri) const
-    {
-        return single() ? (1u << best) : ((1u << ntri) - 1u);
-    }
-};
-
-// FP32 alpha and its bound for the triangle (X, A, B) in that orientation;
-// R2 bounds the squared local coordinates of its three vertices; sk is the
-// orientation sign times 2 sqrt(3).  The caller has checked that every local
-// coordinate lies in the range where the bound holds (see screen_node).
-__device__ __forceinline__ void screen_alpha(float Xx, float Xy, float Ax, float Ay, float Bx, float By,
-                                             float ba2, float R2, float sk, float &a, float &b)
-{
-    const float e1x = Ax - Xx, e1y = Ay - Xy, e2x = Bx - Xx, e2y = By - Xy;
-    const float cr = fmaf(e1x, e2y, -(e1y * e2x));
-    const float s = fmaf(e1x, e1x, fmaf(e1y, e1y, fmaf(e2x, e2x, fmaf(e2y, e2y, ba2))));
-    const float inv = __fdividef(1.0f, s);
-    a = sk * cr * inv;
-    const float g = R2 * inv;
-    const float aa = fabsf(a);
-    b = fmaf(kC1, aa, fmaf(kC3, aa, kC2) * g);
-    const bool usable = (s > 0.0f) & (g <= kGMax);  // else degenerate or unscreenable: no information
-    a = usable ? a : 0.0f;
-    b = usable ? b : FLT_MAX;
-}
-
 // Second screen, for a node whose two minima are attained by the same single
 // triangle (X, A, B) (X = 0 before the move, X = C after it; sgn gives the
 // stored orientation).  Then q_new - q_old (FP64) differs from the exact
@@ -206,9 +155,22 @@ __device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float C
 // Section 3.3.4).  Decided nodes are written and counted here; returns true
 // when the node must be finished by the exact path (d filled in).  loc is
 // this thread's slice of the shared local-coordinate buffer (stride nthr).
+//
+// Warp-synchronous: every lane of the warp calls it (have = false for lanes
+// without a node).  The neighbour loop runs to the warp's largest degree in
+// groups of four, every load of a group issued before its arithmetic; a lane
+// past its own degree keeps its sums, so each lane's FP64 additions are its
+// node's, in the stored order.
+//
+// The accept test is screened with one error bound per side (before and
+// after the move) for all of the node's triangles.  The per-triangle bound
+//   e * (13.2 |a| + (264.6 + 194 |a|) g),  g = R^2 / s,
+// grows with |a| and g, so the side's largest |a|, its largest local
+// coordinate R (every vertex of every triangle of that side lies within it)
+// and its smallest edge sum s bound every triangle at once.
 template <int LAYOUT>
-__device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2 *loc, int nthr, Deferred &d,
-                                            unsigned long long &best, unsigned long long &nacc)
+__device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_t i, float2 *loc, int nthr,
+                                            Deferred &d, unsigned long long &best, unsigned long long &nacc)
 {
     d.node = (int32_t)i;
     d.flags = 0u;
@@ -216,40 +178,70 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
     d.pad = 0u;
     d.cx = 0ull;
     d.cy = 0ull;
-    const uint32_t off = __ldg(a.node_off + i);
-    const uint32_t meta = __ldg(a.adj + off);
-    if (meta & kMetaFixed) {
-        if (a.accept) a.accept[i] = 0;
-        return false;
+    uint32_t off = 0u, meta = kMetaFixed;
+    if (have) {
+        off = __ldg(a.node_off + i);
+        meta = __ldg(a.adj + off);
     }
-    const uint32_t deg = meta_degree(meta), ntri = meta_ntri(meta);
-    if (deg > (uint32_t)kFastMax || ntri > (uint32_t)kFastMax) return true;  // exact path does it all
+    const bool fixed = (meta & kMetaFixed) != 0u;
+    if (have && fixed && a.accept) a.accept[i] = 0;
+    const uint32_t deg = fixed ? 0u : meta_degree(meta), ntri = fixed ? 0u : meta_ntri(meta);
+    const bool big = !fixed && (deg > (uint32_t)kFastMax || ntri > (uint32_t)kFastMax);
+    bool act = have && !fixed && !big;
     const uint32_t *nb = a.adj + off + 1;
-    const ulonglong2 pb = CoordBits<LAYOUT>::get(a.in, a.n, i);
+    const uint32_t dmax = __reduce_max_sync(0xffffffffu, act ? deg : 0u);
+
+    ulonglong2 pb = make_ulonglong2(0ull, 0ull), v0 = make_ulonglong2(0ull, 0ull);
+    if (act) {
+        pb = CoordBits<LAYOUT>::get(a.in, a.n, i);
+        v0 = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb));
+    }
     float phx, plx, phy, ply;
     bool ok = head_tail(pb.x, phx, plx) & head_tail(pb.y, phy, ply);
-
-    // Eq. 2: FP64 sums in the stored order; local coordinates on the side
-    ulonglong2 v = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb));
-    double sx = bitsd(v.x), sy = bitsd(v.y);
-    float rn = 0.0f, rmin = FLT_MAX;  // largest / smallest neighbour offset (max norm)
-    for (uint32_t k = 0;;) {
+    unsigned long long sxb = v0.x, syb = v0.y;
+    float rn = 0.0f, rmin = FLT_MAX;
+    {
         float hx, lx, hy, ly;
-        ok = ok & head_tail(v.x, hx, lx) & head_tail(v.y, hy, ly);
+        ok = ok & head_tail(v0.x, hx, lx) & head_tail(v0.y, hy, ly);
         const float2 L = make_float2((hx - phx) + (lx - plx), (hy - phy) + (ly - ply));
-        loc[k * nthr] = L;
+        if (act) loc[0] = L;
         const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
-        rn = fmaxf(rn, rl);
-        rmin = fminf(rmin, rl);
-        if (++k >= deg) break;
-        v = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb + k));
-        sx = __dadd_rn(sx, bitsd(v.x));
-        sy = __dadd_rn(sy, bitsd(v.y));
+        rn = rl;
+        rmin = rl;
     }
+    for (uint32_t k0 = 1; k0 < dmax; k0 += 4) {
+        uint32_t id[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) id[u] = (act && k0 + u < deg) ? __ldg(nb + k0 + u) : 0u;
+        ulonglong2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = (act && k0 + u < deg) ? CoordBits<LAYOUT>::get(a.in, a.n, id[u]) : make_ulonglong2(0ull, 0ull);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t k = k0 + (uint32_t)u;
+            if (k < dmax) {  // warp-uniform
+                const bool on = act && k < deg;
+                const unsigned long long tx = dbits(__dadd_rn(bitsd(sxb), bitsd(v[u].x)));
+                const unsigned long long ty = dbits(__dadd_rn(bitsd(syb), bitsd(v[u].y)));
+                sxb = on ? tx : sxb;
+                syb = on ? ty : syb;
+                float hx, lx, hy, ly;
+                const bool okk = head_tail(v[u].x, hx, lx) & head_tail(v[u].y, hy, ly);
+                const float2 L = make_float2((hx - phx) + (lx - plx), (hy - phy) + (ly - ply));
+                if (on) loc[k * nthr] = L;
+                const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
+                rn = on ? fmaxf(rn, rl) : rn;
+                rmin = on ? fminf(rmin, rl) : rmin;
+                ok = on ? (ok & okk) : ok;
+            }
+        }
+    }
+    if (big) return true;  // exact path does it all
+    if (!act) return false;
     const double fd = c_degree[deg], y = c_recip[deg];
-    const unsigned long long cbx = divs::div_small_bits(dbits(sx), deg, y, fd);
-    const unsigned long long cby = divs::div_small_bits(dbits(sy), deg, y, fd);
-    const double cxd = bitsd(cbx), cyd = bitsd(cby);
+    const unsigned long long cbx = divs::div_small_bits(sxb, deg, y, fd);
+    const unsigned long long cby = divs::div_small_bits(syb, deg, y, fd);
     d.cx = cbx;
     d.cy = cby;
     d.flags = kHasCentre;
@@ -262,44 +254,84 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, int64_t i, float2
         return false;
     }
     if (!ok) return true;
-    // c - p exactly as FP64 rounds it (also the move used for d2)
-    const double dx = __dsub_rn(cxd, bitsd(pb.x)), dy = __dsub_rn(cyd, bitsd(pb.y));
+    const double dx = __dsub_rn(bitsd(cbx), bitsd(pb.x)), dy = __dsub_rn(bitsd(cby), bitsd(pb.y));
     const float Cx = trunc_float(dx), Cy = trunc_float(dy);
     const float rC = fmaxf(fabsf(Cx), fabsf(Cy));
     const float M = fmaxf(fabsf(phx), fabsf(phy)) * 1.0001f + fmaxf(rn, rC);
     const float M2 = M * M;
-    // Every triangle's R is at least rmin and at most max(rn, rC): inside this
-    // range FP32 products neither under- nor overflow and the head/tail error
-    // stays below e R, so the per-triangle bounds hold.
     if (!((rmin >= 1e-14f) & (fmaxf(rn, rC) <= 1e15f) & (rmin * kLocalRange >= M))) return true;
-    MinTrack o, nw;
-    o.init();
-    nw.init();
-    for (uint32_t t = 0; t < ntri; ++t) {
-        const uint32_t c = __ldg(nb + deg + t);
-        const float2 A = loc[code_first(c) * nthr];
-        const float2 B = loc[code_second(c) * nthr];
-        const float sk = code_slot(c) == 1u ? -kTwoSqrt3f : kTwoSqrt3f;
-        const float bax = B.x - A.x, bay = B.y - A.y;
-        const float ba2 = fmaf(bax, bax, bay * bay);
-        const float rAB = fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y)));
-        const float rN = fmaxf(rAB, rC);
-        float av, bv;
-        screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, rAB * rAB, sk, av, bv);
-        o.add(av, bv, t);
-        screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, rN * rN, sk, av, bv);
-        nw.add(av, bv, t);
+    const float rN = fmaxf(rn, rC);
+    float amin_o = FLT_MAX, a2_o = FLT_MAX, amax_o = 0.0f, smin_o = FLT_MAX;
+    float amin_n = FLT_MAX, a2_n = FLT_MAX, amax_n = 0.0f, smin_n = FLT_MAX;
+    uint32_t arg_o = 0u, arg_n = 0u;
+    for (uint32_t t0 = 0; t0 < ntri; t0 += 4) {
+        uint32_t c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = t0 + u < ntri ? __ldg(nb + deg + t0 + u) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t t = t0 + (uint32_t)u;
+            if (t < ntri) {
+                const float2 A = loc[code_first(c[u]) * nthr];
+                const float2 B = loc[code_second(c[u]) * nthr];
+                const float sk = code_slot(c[u]) == 1u ? -kTwoSqrt3f : kTwoSqrt3f;
+                const float bax = B.x - A.x, bay = B.y - A.y;
+                const float ba2 = fmaf(bax, bax, bay * bay);
+                {
+                    const float cr = fmaf(A.x, B.y, -(A.y * B.x));
+                    const float sv = fmaf(A.x, A.x, fmaf(A.y, A.y, fmaf(B.x, B.x, fmaf(B.y, B.y, ba2))));
+                    const float av = sk * cr * __fdividef(1.0f, sv);
+                    if (av < amin_o) {
+                        a2_o = amin_o;
+                        amin_o = av;
+                        arg_o = t;
+                    } else {
+                        a2_o = fminf(a2_o, av);
+                    }
+                    amax_o = fmaxf(amax_o, fabsf(av));
+                    smin_o = fminf(smin_o, sv);
+                }
+                {
+                    const float e1x = A.x - Cx, e1y = A.y - Cy, e2x = B.x - Cx, e2y = B.y - Cy;
+                    const float cr = fmaf(e1x, e2y, -(e1y * e2x));
+                    const float sv = fmaf(e1x, e1x, fmaf(e1y, e1y, fmaf(e2x, e2x, fmaf(e2y, e2y, ba2))));
+                    const float av = sk * cr * __fdividef(1.0f, sv);
+                    if (av < amin_n) {
+                        a2_n = amin_n;
+                        amin_n = av;
+                        arg_n = t;
+                    } else {
+                        a2_n = fminf(a2_n, av);
+                    }
+                    amax_n = fmaxf(amax_n, fabsf(av));
+                    smin_n = fminf(smin_n, sv);
+                }
+            }
+        }
     }
-    // q_new and q_old (FP64) lie in [minL, minU] of their side
-    int verdict = nw.minL > o.minU ? 1 : (nw.minU < o.minL ? -1 : 0);
-    if (verdict == 0 && o.single() && nw.single() && o.best == nw.best) {
-        const uint32_t c = __ldg(nb + deg + o.best);
+    // per side: q (FP64) lies in [amin - b, amin + b]; the minimum is attained
+    // by triangle arg alone when every other alpha lies above amin + b + b
+    const float go = rn * rn * __fdividef(1.0f, smin_o), gn = rN * rN * __fdividef(1.0f, smin_n);
+    int verdict = 0;
+    bool single_o = false, single_n = false;
+    if ((smin_o > 0.0f) & (smin_n > 0.0f) & (go <= kGMax) & (gn <= kGMax) & (amax_o <= 2.0f) & (amax_n <= 2.0f)) {
+        const float bo = fmaf(kC1, amax_o, fmaf(kC3, amax_o, kC2) * go);
+        const float bn = fmaf(kC1, amax_n, fmaf(kC3, amax_n, kC2) * gn);
+        const float minU_o = amin_o + bo, minL_o = amin_o - bo;
+        const float minU_n = amin_n + bn, minL_n = amin_n - bn;
+        verdict = minL_n > minU_o ? 1 : (minU_n < minL_o ? -1 : 0);
+        single_o = a2_o - bo > minU_o;
+        single_n = a2_n - bn > minU_n;
+    }
+    if (verdict == 0 && single_o && single_n && arg_o == arg_n) {
+        const uint32_t c = __ldg(nb + deg + arg_o);
         verdict = diff_screen(loc[code_first(c) * nthr], loc[code_second(c) * nthr], Cx, Cy,
                               code_slot(c) == 1u ? -1.0f : 1.0f, M2);
     }
     if (verdict == 0) {
+        const uint32_t all = (1u << ntri) - 1u;
         d.flags |= kMasked;
-        d.masks = o.candidates(ntri) | (nw.candidates(ntri) << 16);
+        d.masks = (single_o ? (1u << arg_o) : all) | ((single_n ? (1u << arg_n) : all) << 16);
         return true;
     }
     const bool acc = verdict > 0;
@@ -381,8 +413,9 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
     for (int64_t wt = (int64_t)blockIdx.x * (nthr >> 5) + warp; wt < nwtiles; wt += wstride) {
         const int64_t j = wt * 32 + lane;
         Deferred d;
-        const bool defer =
-            j < cnt && screen_node<LAYOUT>(a, a.order ? (int64_t)__ldg(a.order + j) : j, loc, nthr, d, best, nacc);
+        const bool have = j < cnt;
+        const bool defer = screen_node<LAYOUT>(a, have, have ? (a.order ? (int64_t)__ldg(a.order + j) : j) : 0,
+                                               loc, nthr, d, best, nacc);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
@@ -466,7 +499,7 @@ __global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restri
         if (first == 0 && lane == 0) a.stats[a.q].executed = 1u;
         const int64_t i = first + lane;
         Deferred d;
-        const bool defer = i < a.n && screen_node<LAYOUT>(a, i, loc, nthr, d, best, nacc);
+        const bool defer = screen_node<LAYOUT>(a, i < a.n, i < a.n ? i : 0, loc, nthr, d, best, nacc);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
