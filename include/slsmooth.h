@@ -97,6 +97,16 @@ typedef struct sls_options {
                               coordinates (the given doubles rounded to nearest) and every
                               operation one binary32 round-to-nearest operation in the same
                               order, the paper's precision (Section 4).  Single meshes only. */
+    int32_t skip_unchanged;/* 1: from the second pass of an sls_smooth call on, a tile of 32
+                              consecutive nodes is not recomputed when none of its nodes and
+                              none of their neighbours changed coordinates in the previous
+                              pass: its inputs are then those of the previous pass, so its
+                              coordinates and decisions are too (Form A is a function of the
+                              previous pass only, Eq. 2).  Results are identical to 0; the
+                              gain grows as the mesh settles.  Needs form = 0, precision = 64
+                              and the screened kernel (SLS_KERNEL_AUTO or _FILTERED); costs
+                              136 bytes of device memory per 32 nodes.  The batched and
+                              allocation-free forms compute every tile; the server rejects it. */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle    */
 } sls_options;
 
@@ -109,6 +119,8 @@ typedef struct sls_info {
     int64_t launches;      /* kernel launches issued by the last sls_smooth call (passes
                               launched after the tolerance was met return at once; 0 from
                               the batched and served forms)                                 */
+    int64_t tiles_skipped; /* 32-node tiles not recomputed by the last sls_smooth call
+                              (skip_unchanged; summed over its passes)                       */
 } sls_info;
 
 typedef struct sls_mesh sls_mesh;

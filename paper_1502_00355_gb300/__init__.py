@@ -34,17 +34,20 @@ class Options(C.Structure):
     _fields_ = [("accept_strict", C.c_int32), ("copy_back", C.c_int32), ("layout", C.c_int32),
                 ("kernel", C.c_int32), ("record_accept", C.c_int32), ("block_size", C.c_int32),
                 ("l2_window", C.c_int32), ("passes_per_check", C.c_int32), ("host_build", C.c_int32),
-                ("form", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p)]
+                ("form", C.c_int32), ("precision", C.c_int32), ("skip_unchanged", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class Info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("accepted_last", C.c_int64),
-                ("max_d2_last", C.c_double), ("fp64_fallbacks", C.c_int64), ("launches", C.c_int64)]
+                ("max_d2_last", C.c_double), ("fp64_fallbacks", C.c_int64), ("launches", C.c_int64),
+                ("tiles_skipped", C.c_int64)]
 
     def as_dict(self) -> dict:
         return dict(iterations=self.iterations, converged=self.converged,
                     accepted_last=self.accepted_last, maxd2_last=self.max_d2_last,
-                    fp64_fallbacks=self.fp64_fallbacks, launches=self.launches)
+                    fp64_fallbacks=self.fp64_fallbacks, launches=self.launches,
+                    tiles_skipped=self.tiles_skipped)
 
 
 class SlsError(RuntimeError):
@@ -112,7 +115,7 @@ def _p(a: np.ndarray | None):
 
 def make_options(*, strict=False, copy_back=False, layout="aos", kernel="auto", record_accept=False,
                  block_size=0, l2_window=False, passes_per_check=0, host_build=False, form="A",
-                 precision=64, stream=None) -> Options:
+                 precision=64, skip_unchanged=False, stream=None) -> Options:
     o = Options()
     lib().sls_default_options(C.byref(o))
     o.accept_strict = int(bool(strict))
@@ -126,6 +129,7 @@ def make_options(*, strict=False, copy_back=False, layout="aos", kernel="auto", 
     o.host_build = int(bool(host_build))
     o.form = {"A": 0, "B": 1}[form]
     o.precision = int(precision)
+    o.skip_unchanged = int(bool(skip_unchanged))
     o.stream = None if stream is None else C.c_void_p(int(stream))
     return o
 

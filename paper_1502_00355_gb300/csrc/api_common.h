@@ -30,6 +30,9 @@ struct sls_mesh {
     int stats_cap = 0;
     sls::PassStats *h_stats = nullptr;  // pinned, one record
     uint8_t *accept = nullptr;    // n, when record_accept
+    uint2 *halo = nullptr;        // skip_unchanged: kHaloEntries (tile, mask) pairs per 32-node tile
+    uint32_t *chg[2] = {nullptr, nullptr};  // per tile: nodes changed by the last two passes
+    uint32_t *accm = nullptr;     // per tile: nodes accepted when the tile was last computed
     int block = 256, grid = 0;
     bool screened = true;         // screened kernel (else the plain FP64 kernel)
     sls_info last{};
@@ -54,6 +57,9 @@ sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_t
 // The processing order of the free nodes, from the adjacency on the device
 // (mesh_build_gpu.cu): fills M->node_order.
 sls_status build_node_order(sls_mesh *M, cudaStream_t s);
+// The tile lists and masks of unchanged-tile skipping (mesh_build_gpu.cu),
+// when opt.skip_unchanged is set.
+sls_status build_tile_halo(sls_mesh *M, cudaStream_t s);
 void mesh_release(sls_mesh *M);
 sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info);
 sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device);

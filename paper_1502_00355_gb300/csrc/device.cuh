@@ -13,7 +13,7 @@ struct PassStats {
     unsigned long long nacc;        // accepted free nodes
     unsigned long long fallbacks;   // accept tests redone in FP64 by the screened kernel
     unsigned int executed;          // 1 once the pass ran (0: skipped after convergence)
-    unsigned int pad;
+    unsigned int tiles_skipped;     // 32-node tiles left as they were (unchanged inputs)
 };
 
 // Arguments of one Jacobi pass over one mesh.
@@ -31,7 +31,23 @@ struct PassArgs {
     int tol_active;            // 1: skip the pass when pass q-1 met the tolerance or was skipped
     unsigned long long thr_bits;  // bits of (tol * D)^2
     uint8_t *accept;           // n decisions, or nullptr
+    // Skipping of unchanged tiles (tiles of 32 consecutive nodes; all null
+    // and skip = 0 when the mesh does not use it).  A tile whose nodes and
+    // whose nodes' neighbours all kept their coordinates in the previous pass
+    // has the same inputs as then, so its update is the identity: its nodes
+    // keep their coordinates (already in `out`, two passes old and equal) and
+    // their decisions.
+    const uint2 *halo;         // kHaloEntries (tile, node mask) pairs per tile: itself and every
+                               // tile holding a neighbour of one of its nodes; (kHaloNever, 0)
+                               // first marks a tile that is never skipped
+    const uint32_t *chg_prev;  // per tile: nodes whose coordinates changed in the previous pass
+    uint32_t *chg_cur;         // the same, written by this pass
+    uint32_t *accm;            // per tile: nodes accepted the last time the tile was computed
+    int skip;                  // 1: unchanged tiles may be skipped in this pass
 };
+
+constexpr int kHaloEntries = 16;
+constexpr uint32_t kHaloNever = 0xffffffffu;
 
 // One mesh (job) of the batched and served forms.
 struct JobDesc {

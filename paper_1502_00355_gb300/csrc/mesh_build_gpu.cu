@@ -474,6 +474,68 @@ __global__ void colour_max_kernel(const int32_t *__restrict__ colour, int64_t n,
     if ((threadIdx.x & 31) == 0) atomicMax(cmax, m);
 }
 
+// Unchanged-tile skipping: for tile t (nodes 32t .. 32t+31), the tiles that
+// hold its nodes and the neighbours of its free nodes, each with the mask of
+// those nodes; (kHaloNever, 0) when more than kHaloEntries tiles are involved
+// (such a tile is always computed).  One thread per tile.
+__global__ void tile_halo_kernel(const uint32_t *__restrict__ node_off, const uint32_t *__restrict__ adj,
+                                 int64_t n, int64_t ntiles, uint2 *halo)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    uint32_t ids[kHaloEntries], masks[kHaloEntries];
+    int cnt = 1;
+    ids[0] = (uint32_t)t;
+    masks[0] = 0xffffffffu;
+    bool over = false;
+    for (int l = 0; l < 32 && !over; ++l) {
+        const int64_t i = t * 32 + l;
+        if (i >= n) break;
+        const uint32_t off = node_off[i], meta = adj[off];
+        if (meta & kMetaFixed) continue;
+        const uint32_t deg = meta_degree(meta);
+        for (uint32_t k = 0; k < deg; ++k) {
+            const uint32_t j = adj[off + 1 + k];
+            const uint32_t tj = j >> 5;
+            int e = 0;
+            while (e < cnt && ids[e] != tj) ++e;
+            if (e == cnt) {
+                if (cnt == kHaloEntries) {
+                    over = true;
+                    break;
+                }
+                ids[cnt] = tj;
+                masks[cnt] = 0u;
+                ++cnt;
+            }
+            masks[e] |= 1u << (j & 31);
+        }
+    }
+    uint2 *h = halo + t * kHaloEntries;
+    for (int e = 0; e < kHaloEntries; ++e)
+        h[e] = over ? make_uint2(e == 0 ? kHaloNever : 0u, 0u)
+                    : (e < cnt ? make_uint2(ids[e], masks[e]) : make_uint2(0u, 0u));
+}
+
+}  // namespace
+
+sls_status build_tile_halo(sls_mesh *M, cudaStream_t s)
+{
+    if (!M->opt.skip_unchanged) return SLS_OK;
+    const int64_t nt = (M->n + 31) / 32;
+    GB_TRY(cudaMalloc(&M->halo, sizeof(uint2) * (size_t)kHaloEntries * (size_t)nt), "tile halo");
+    for (int k = 0; k < 2; ++k) GB_TRY(cudaMalloc(&M->chg[k], sizeof(uint32_t) * (size_t)nt), "tile masks");
+    GB_TRY(cudaMalloc(&M->accm, sizeof(uint32_t) * (size_t)nt), "tile masks");
+    for (int k = 0; k < 2; ++k) GB_TRY(cudaMemsetAsync(M->chg[k], 0xff, sizeof(uint32_t) * (size_t)nt, s), "tile masks");
+    GB_TRY(cudaMemsetAsync(M->accm, 0, sizeof(uint32_t) * (size_t)nt, s), "tile masks");
+    tile_halo_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(M->node_off, M->adj, M->n, nt, M->halo);
+    GB_TRY(cudaGetLastError(), "tile halo");
+    GB_TRY(cudaStreamSynchronize(s), "tile halo");
+    return SLS_OK;
+}
+
+namespace {
+
 // One segment of the processing order: the free nodes of colour c (all free
 // nodes when colour is null), tile by tile, by (degree, triangles, id).
 sls_status order_segment(sls_mesh *M, const int32_t *colour, int32_t c, uint32_t *dst, int64_t expect,

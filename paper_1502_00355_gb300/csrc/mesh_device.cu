@@ -129,7 +129,8 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
                                  cudaMemcpyHostToDevice, M->stream), "upload triangles");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload");
     if ((st = narrow_coordinates(M)) != SLS_OK) return st;
-    return build_node_order(M, M->stream);
+    if ((st = build_node_order(M, M->stream)) != SLS_OK) return st;
+    return build_tile_halo(M, M->stream);
 }
 
 sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const int32_t *tri, int64_t m,
@@ -175,7 +176,8 @@ sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const
     SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[1], M->xy[0], cbytes, cudaMemcpyDeviceToDevice, M->stream), "copy coordinates");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "mesh create");
     if ((st = narrow_coordinates(M)) != SLS_OK) return st;
-    return build_node_order(M, M->stream);
+    if ((st = build_node_order(M, M->stream)) != SLS_OK) return st;
+    return build_tile_halo(M, M->stream);
 }
 
 void mesh_release(sls_mesh *M)
@@ -189,6 +191,10 @@ void mesh_release(sls_mesh *M)
     cudaFree(M->tri);
     cudaFree(M->stats);
     cudaFree(M->accept);
+    cudaFree(M->halo);
+    cudaFree(M->chg[0]);
+    cudaFree(M->chg[1]);
+    cudaFree(M->accm);
     if (M->h_stats) cudaFreeHost(M->h_stats);
     if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
     M->stream = nullptr;
@@ -260,6 +266,13 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
             a.out = M->xy[src ^ 1];
             a.order = nullptr;
             a.norder = 0;
+            if (M->halo) {  // unchanged-tile skipping from the second pass of a call on
+                a.halo = M->halo;
+                a.chg_prev = M->chg[(q + 1) & 1];
+                a.chg_cur = M->chg[q & 1];
+                a.accm = M->accm;
+                a.skip = q > 0 ? 1 : 0;
+            }
             SLS_CUDA_TRY(launch_pass(M, a), "pass kernel");
             ++kernels;
             if (cb) {
@@ -285,10 +298,14 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
                                  cudaMemcpyDeviceToHost, M->stream), "read pass statistics");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "passes");
     int it = 0;
-    long long fb = 0;
-    while (it < launched && hs[it].executed) fb += (long long)hs[it++].fallbacks;
+    long long fb = 0, sk = 0;
+    for (; it < launched && hs[it].executed; ++it) {
+        fb += (long long)hs[it].fallbacks;
+        sk += (long long)hs[it].tiles_skipped;
+    }
     info.iterations = it;
     info.fp64_fallbacks = fb;
+    info.tiles_skipped = sk;
     info.launches = kernels;
     if (it > 0) {
         const PassStats &l = hs[it - 1];

@@ -39,12 +39,12 @@ __device__ __forceinline__ double alpha_with(const PassArgs &a, const uint32_t *
 // the minima over all incident triangles or, with kMasked, over the triangles
 // in the masks: the screen proved every other triangle's FP64 alpha larger
 // than some masked one, so the minimum is the same.  Writes the node and its
-// decision; returns the squared move bits (0 if not accepted) and whether it
-// was accepted.
+// decision; returns the squared move bits (0 if not accepted), whether it was
+// accepted and whether its coordinates changed.
 template <int LAYOUT>
 __device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint32_t flags, uint32_t masks,
                                              unsigned long long cxb, unsigned long long cyb,
-                                             unsigned long long &d2_bits, bool &accepted)
+                                             unsigned long long &d2_bits, bool &accepted, bool &moved)
 {
     double cx = __longlong_as_double((long long)cxb), cy = __longlong_as_double((long long)cyb);
     const uint32_t off = __ldg(a.node_off + i);
@@ -104,6 +104,8 @@ __device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint3
     const bool ok = a.strict ? (q_new > q_old) : (q_new >= q_old);
     double2 o = p;
     d2_bits = 0ull;
+    moved = ok && (__double_as_longlong(cx) != __double_as_longlong(p.x) ||
+                   __double_as_longlong(cy) != __double_as_longlong(p.y));
     if (ok) {
         const double dx = __dsub_rn(cx, p.x), dy = __dsub_rn(cy, p.y);
         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));

@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(1024) pass_fp64_kernel(PassArgs a)
             continue;
         }
         unsigned long long bits;
-        bool ok;
-        exact_update<LAYOUT>(a, i, 0u, 0u, 0ull, 0ull, bits, ok);
+        bool ok, moved;
+        exact_update<LAYOUT>(a, i, 0u, 0u, 0ull, 0ull, bits, ok, moved);
         best = bits > best ? bits : best;
         nacc += ok ? 1ull : 0ull;
     }

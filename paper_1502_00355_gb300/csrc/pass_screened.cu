@@ -170,8 +170,10 @@ __device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float C
 // and its smallest edge sum s bound every triangle at once.
 template <int LAYOUT>
 __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_t i, float2 *loc, int nthr,
-                                            Deferred &d, unsigned long long &best, unsigned long long &nacc)
+                                            Deferred &d, unsigned long long &best, unsigned long long &nacc,
+                                            uint32_t &res)
 {
+    res = 0u;  // decided nodes: bit 0 accepted, bit 1 coordinates changed
     d.node = (int32_t)i;
     d.flags = 0u;
     d.masks = 0u;
@@ -251,6 +253,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         CoordBits<LAYOUT>::put(a.out, a.n, i, pb);
         if (a.accept) a.accept[i] = acc ? 1 : 0;
         nacc += acc ? 1ull : 0ull;
+        res = acc ? 1u : 0u;
         return false;
     }
     if (!ok) return true;
@@ -341,6 +344,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         best = b2 > best ? b2 : best;
         nacc += 1ull;
         outp = make_ulonglong2(cbx, cby);
+        res = 3u;  // the centre differs from the node (equal centres return above)
     }
     CoordBits<LAYOUT>::put(a.out, a.n, i, outp);
     if (a.accept) a.accept[i] = acc ? 1 : 0;
@@ -359,10 +363,15 @@ __device__ __forceinline__ void drain_queue(const PassArgs &a, Deferred *wq, int
         if (lane < qn) {
             const Deferred e = wq[lane];
             unsigned long long b2;
-            bool acc;
-            exact_update<LAYOUT>(a, e.node, e.flags, e.masks, e.cx, e.cy, b2, acc);
+            bool acc, moved;
+            exact_update<LAYOUT>(a, e.node, e.flags, e.masks, e.cx, e.cy, b2, acc, moved);
             best = b2 > best ? b2 : best;
             nacc += acc ? 1ull : 0ull;
+            if (a.halo) {  // the node's bits in its tile's masks (written with the tile's other nodes)
+                const uint32_t bit = 1u << (e.node & 31);
+                if (moved) atomicOr(a.chg_cur + (e.node >> 5), bit);
+                if (acc) atomicOr(a.accm + (e.node >> 5), bit);
+            }
         }
         const int rest = qn > 32 ? qn - 32 : 0;
         __syncwarp();
@@ -403,6 +412,7 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
     if (blockIdx.x == 0 && tid == 0) a.stats[a.q].executed = 1u;
 
     unsigned long long best = 0ull, nacc = 0ull, nfb = 0ull;
+    unsigned nskip = 0u;  // tiles this warp left as they were (lane 0)
     float2 *loc = s_loc + tid;
     Deferred *wq = s_q + 64 * warp;
     int qn = 0;  // warp-uniform queue length
@@ -411,12 +421,37 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
     const int64_t nwtiles = (cnt + 31) / 32;
     const int64_t wstride = (int64_t)gridDim.x * (nthr >> 5);
     for (int64_t wt = (int64_t)blockIdx.x * (nthr >> 5) + warp; wt < nwtiles; wt += wstride) {
+        if (a.skip) {
+            // the tile's inputs: its own nodes and every neighbour, by tile
+            const uint2 h = lane < kHaloEntries ? __ldg(a.halo + wt * kHaloEntries + lane) : make_uint2(0u, 0u);
+            const bool never = __shfl_sync(0xffffffffu, h.x, 0) == kHaloNever;
+            const uint32_t c = h.y != 0u ? __ldg(a.chg_prev + h.x) & h.y : 0u;
+            if (!__any_sync(0xffffffffu, c != 0u) && !never) {
+                // all unchanged: the same inputs as in the previous pass, so the
+                // same results, which `out` and the masks already hold
+                if (lane == 0) {
+                    a.chg_cur[wt] = 0u;
+                    nacc += (unsigned long long)__popc(a.accm[wt]);
+                    ++nskip;
+                }
+                continue;
+            }
+        }
         const int64_t j = wt * 32 + lane;
         Deferred d;
         const bool have = j < cnt;
+        uint32_t res;
         const bool defer = screen_node<LAYOUT>(a, have, have ? (a.order ? (int64_t)__ldg(a.order + j) : j) : 0,
-                                               loc, nthr, d, best, nacc);
+                                               loc, nthr, d, best, nacc, res);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
+        if (a.halo) {  // before any drain: deferred nodes add their bits there
+            const unsigned cb = __ballot_sync(0xffffffffu, (res & 2u) != 0u);
+            const unsigned ab = __ballot_sync(0xffffffffu, (res & 1u) != 0u);
+            if (lane == 0) {
+                a.chg_cur[wt] = cb;
+                a.accm[wt] = ab;
+            }
+        }
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
         nfb += defer ? 1ull : 0ull;
@@ -427,6 +462,7 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
     }
     __syncwarp();
     drain_queue<LAYOUT>(a, wq, qn, true, best, nacc);
+    if (nskip) atomicAdd(&a.stats[a.q].tiles_skipped, nskip);
     block_reduce_stats(a.stats + a.q, best, nacc, nfb);
 }
 
@@ -499,7 +535,8 @@ __global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restri
         if (first == 0 && lane == 0) a.stats[a.q].executed = 1u;
         const int64_t i = first + lane;
         Deferred d;
-        const bool defer = screen_node<LAYOUT>(a, i < a.n, i < a.n ? i : 0, loc, nthr, d, best, nacc);
+        uint32_t res;
+        const bool defer = screen_node<LAYOUT>(a, i < a.n, i < a.n ? i : 0, loc, nthr, d, best, nacc, res);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);

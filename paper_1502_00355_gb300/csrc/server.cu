@@ -407,6 +407,7 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
     sls_status st = check_options(o);
     if (st != SLS_OK) return st;
     if (o.form != 0 || o.precision != 64) return fail(SLS_ERR_INVALID, "the server runs FP64 Form A only");
+    if (o.skip_unchanged) return fail(SLS_ERR_INVALID, "the server computes every tile (skip_unchanged is for single meshes)");
     auto S = std::make_unique<sls_server>();
     S->opt = o;
     S->max_queue = max_queue;
