@@ -291,7 +291,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="large", choices=["large", "batch", "serve"])
     ap.add_argument("--batch-meshes", type=int, default=2048)
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-max-n", type=int, default=262144)
     ap.add_argument("--gpus", type=int, default=1)

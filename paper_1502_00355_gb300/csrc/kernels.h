@@ -22,6 +22,9 @@ int pass_screened_occupancy(int layout, int block);
 cudaError_t launch_batch_pass(const JobDesc *jobs, const WarpTask *tasks, int64_t ntasks, int round,
                               int layout, int block, int grid, cudaStream_t s);
 int batch_pass_occupancy(int layout, int block);
+// Record of round `round` of each of the na jobs (pass round - base_round,
+// clamped to the job's last pass) into out[0 .. na).
+cudaError_t launch_gather_round(const JobDesc *jobs, int na, int round, PassStats *out, cudaStream_t s);
 
 // Copy-back form: out -> in after pass q (skipped when pass q was skipped).
 cudaError_t launch_copy_back(const double *src, double *dst, int64_t n_doubles,

@@ -603,6 +603,28 @@ cudaError_t launch_batch_pass(const JobDesc *jobs, const WarpTask *tasks, int64_
     return cudaGetLastError();
 }
 
+namespace {
+
+__global__ void gather_round_kernel(const JobDesc *__restrict__ jobs, int na, int round, PassStats *out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= na) return;
+    const JobDesc &J = jobs[j];
+    int q = round - J.base_round;
+    const int last = J.max_iter > 1 ? J.max_iter - 1 : 0;
+    q = q < last ? q : last;
+    out[j] = J.stats[q];
+}
+
+}  // namespace
+
+cudaError_t launch_gather_round(const JobDesc *jobs, int na, int round, PassStats *out, cudaStream_t s)
+{
+    if (na <= 0) return cudaSuccess;
+    gather_round_kernel<<<(na + 127) / 128, 128, 0, s>>>(jobs, na, round, out);
+    return cudaGetLastError();
+}
+
 int batch_pass_occupancy(int layout, int block)
 {
     if (ensure_constants() != cudaSuccess) return 1;

@@ -86,6 +86,7 @@ struct sls_server {
     WarpTask *d_tasks = nullptr, *h_tasks = nullptr;
     size_t jobs_cap = 0, tasks_cap = 0;
     PassStats *h_round = nullptr;  // pinned: this round's record of each active job
+    PassStats *d_round = nullptr;  // the same records gathered on the device
     size_t round_cap = 0;
     int64_t ntasks = 0;
     int block = 256, grid = 0;
@@ -311,19 +312,17 @@ void scheduler_loop(sls_server *S)
             }
             dirty = false;
         }
-        if (!grow_host(S->h_round, S->round_cap, na)) {
+        if (!grow_pair(S->h_round, S->d_round, S->round_cap, na)) {
             S->sched_error = "out of pinned host memory";
             break;
         }
         const auto t0 = Clock::now();
         cudaError_t e = launch_batch_pass(S->d_jobs, S->d_tasks, S->ntasks, S->round, S->opt.layout, S->block,
                                           S->grid, S->stream);
-        for (size_t j = 0; j < na && e == cudaSuccess; ++j) {
-            ServerJob &J = *S->active[j];
-            const int q = S->round - J.base_round;
-            e = cudaMemcpyAsync(S->h_round + j, J.d_stats + std::min(q, std::max(0, J.max_iter - 1)),
-                                sizeof(PassStats), cudaMemcpyDeviceToHost, S->stream);
-        }
+        // every job's record of this round, gathered by one kernel, read back by one copy
+        if (e == cudaSuccess) e = launch_gather_round(S->d_jobs, (int)na, S->round, S->d_round, S->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->h_round, S->d_round, sizeof(PassStats) * na, cudaMemcpyDeviceToHost, S->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
         S->busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
         if (e != cudaSuccess) {
@@ -332,7 +331,7 @@ void scheduler_loop(sls_server *S)
             break;
         }
         S->round += 1;
-        std::vector<std::shared_ptr<ServerJob>> keep;
+        std::vector<std::shared_ptr<ServerJob>> keep, finished;
         for (size_t j = 0; j < na; ++j) {
             auto Jp = S->active[j];
             ServerJob &J = *Jp;
@@ -358,7 +357,11 @@ void scheduler_loop(sls_server *S)
             J.result.resize(2 * (size_t)J.hm.n);
             cudaMemcpyAsync(J.result.data(), J.d_xy[J.iterations & 1], sizeof(double) * J.result.size(),
                             cudaMemcpyDeviceToHost, S->stream);
-            cudaStreamSynchronize(S->stream);
+            finished.push_back(Jp);
+        }
+        if (!finished.empty()) cudaStreamSynchronize(S->stream);  // one wait for all of this round's results
+        for (auto &Jp : finished) {
+            ServerJob &J = *Jp;
             std::lock_guard<std::mutex> lk(S->mu);
             free_job_device(S, J);
             S->used -= J.footprint;
@@ -522,6 +525,7 @@ sls_status sls_server_destroy(sls_server *S)
     cudaFreeHost(S->h_tasks);
     cudaFree(S->d_tasks);
     cudaFreeHost(S->h_round);
+    cudaFree(S->d_round);
     cudaStreamDestroy(S->stream);
     cudaStreamDestroy(S->copy_stream);
     delete S;
