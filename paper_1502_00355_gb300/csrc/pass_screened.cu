@@ -103,6 +103,17 @@ constexpr float kGMax = 1000.0f;
 constexpr float kTwoSqrt3f = 3.46410161514f;
 constexpr float kLocalRange = 1048576.0f;  // 2^20: R * 2^20 >= M keeps the head/tail error below e R
 
+// FP32 alpha of the triangle (X, A, B) for the screen (sk: orientation sign
+// times 2 sqrt(3); ba2 = |B - A|^2); sv receives the edge sum.  The second
+// candidate loop calls it again and gets the same bits.
+__device__ __forceinline__ float screen_alpha(float2 X, float2 A, float2 B, float ba2, float sk, float &sv)
+{
+    const float e1x = A.x - X.x, e1y = A.y - X.y, e2x = B.x - X.x, e2y = B.y - X.y;
+    const float cr = fmaf(e1x, e2y, -(e1y * e2x));
+    sv = fmaf(e1x, e1x, fmaf(e1y, e1y, fmaf(e2x, e2x, fmaf(e2y, e2y, ba2))));
+    return sk * cr * __fdividef(1.0f, sv);
+}
+
 // Second screen, for a node whose two minima are attained by the same single
 // triangle (X, A, B) (X = 0 before the move, X = C after it; sgn gives the
 // stored orientation).  Then q_new - q_old (FP64) differs from the exact
@@ -281,9 +292,8 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                 const float bax = B.x - A.x, bay = B.y - A.y;
                 const float ba2 = fmaf(bax, bax, bay * bay);
                 {
-                    const float cr = fmaf(A.x, B.y, -(A.y * B.x));
-                    const float sv = fmaf(A.x, A.x, fmaf(A.y, A.y, fmaf(B.x, B.x, fmaf(B.y, B.y, ba2))));
-                    const float av = sk * cr * __fdividef(1.0f, sv);
+                    float sv;
+                    const float av = screen_alpha(make_float2(0.0f, 0.0f), A, B, ba2, sk, sv);
                     if (av < amin_o) {
                         a2_o = amin_o;
                         amin_o = av;
@@ -295,10 +305,8 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                     smin_o = fminf(smin_o, sv);
                 }
                 {
-                    const float e1x = A.x - Cx, e1y = A.y - Cy, e2x = B.x - Cx, e2y = B.y - Cy;
-                    const float cr = fmaf(e1x, e2y, -(e1y * e2x));
-                    const float sv = fmaf(e1x, e1x, fmaf(e1y, e1y, fmaf(e2x, e2x, fmaf(e2y, e2y, ba2))));
-                    const float av = sk * cr * __fdividef(1.0f, sv);
+                    float sv;
+                    const float av = screen_alpha(make_float2(Cx, Cy), A, B, ba2, sk, sv);
                     if (av < amin_n) {
                         a2_n = amin_n;
                         amin_n = av;
@@ -317,11 +325,13 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     const float go = rn * rn * __fdividef(1.0f, smin_o), gn = rN * rN * __fdividef(1.0f, smin_n);
     int verdict = 0;
     bool single_o = false, single_n = false;
-    if ((smin_o > 0.0f) & (smin_n > 0.0f) & (go <= kGMax) & (gn <= kGMax) & (amax_o <= 2.0f) & (amax_n <= 2.0f)) {
-        const float bo = fmaf(kC1, amax_o, fmaf(kC3, amax_o, kC2) * go);
-        const float bn = fmaf(kC1, amax_n, fmaf(kC3, amax_n, kC2) * gn);
-        const float minU_o = amin_o + bo, minL_o = amin_o - bo;
-        const float minU_n = amin_n + bn, minL_n = amin_n - bn;
+    const bool bok =
+        (smin_o > 0.0f) & (smin_n > 0.0f) & (go <= kGMax) & (gn <= kGMax) & (amax_o <= 2.0f) & (amax_n <= 2.0f);
+    const float bo = fmaf(kC1, amax_o, fmaf(kC3, amax_o, kC2) * go);
+    const float bn = fmaf(kC1, amax_n, fmaf(kC3, amax_n, kC2) * gn);
+    const float minU_o = amin_o + bo, minU_n = amin_n + bn;
+    if (bok) {
+        const float minL_o = amin_o - bo, minL_n = amin_n - bn;
         verdict = minL_n > minU_o ? 1 : (minU_n < minL_o ? -1 : 0);
         single_o = a2_o - bo > minU_o;
         single_n = a2_n - bn > minU_n;
@@ -332,9 +342,29 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                               code_slot(c) == 1u ? -1.0f : 1.0f, M2);
     }
     if (verdict == 0) {
+        // candidates for the exact path: every triangle whose interval
+        // reaches below the side's lowest upper end (all of them when the
+        // bounds do not hold)
         const uint32_t all = (1u << ntri) - 1u;
+        uint32_t mo = bok ? (single_o ? (1u << arg_o) : 0u) : all;
+        uint32_t mn = bok ? (single_n ? (1u << arg_n) : 0u) : all;
+        if (bok && !(single_o && single_n)) {
+            for (uint32_t t = 0; t < ntri; ++t) {
+                const uint32_t c = __ldg(nb + deg + t);
+                const float2 A = loc[code_first(c) * nthr];
+                const float2 B = loc[code_second(c) * nthr];
+                const float sk = code_slot(c) == 1u ? -kTwoSqrt3f : kTwoSqrt3f;
+                const float bax = B.x - A.x, bay = B.y - A.y;
+                const float ba2 = fmaf(bax, bax, bay * bay);
+                float sv;
+                if (!single_o && screen_alpha(make_float2(0.0f, 0.0f), A, B, ba2, sk, sv) - bo <= minU_o)
+                    mo |= 1u << t;
+                if (!single_n && screen_alpha(make_float2(Cx, Cy), A, B, ba2, sk, sv) - bn <= minU_n)
+                    mn |= 1u << t;
+            }
+        }
         d.flags |= kMasked;
-        d.masks = (single_o ? (1u << arg_o) : all) | ((single_n ? (1u << arg_n) : all) << 16);
+        d.masks = mo | (mn << 16);
         return true;
     }
     const bool acc = verdict > 0;
