@@ -229,16 +229,16 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         ulonglong2 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            v[u] = (act && k0 + u < deg) ? CoordBits<LAYOUT>::get(a.in, a.n, id[u]) : make_ulonglong2(0ull, 0ull);
+            v[u] = (act && k0 + u < deg) ? CoordBits<LAYOUT>::get(a.in, a.n, id[u])
+                                         : make_ulonglong2(0x8000000000000000ull, 0x8000000000000000ull);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t k = k0 + (uint32_t)u;
             if (k < dmax) {  // warp-uniform
                 const bool on = act && k < deg;
-                const unsigned long long tx = dbits(__dadd_rn(bitsd(sxb), bitsd(v[u].x)));
-                const unsigned long long ty = dbits(__dadd_rn(bitsd(syb), bitsd(v[u].y)));
-                sxb = on ? tx : sxb;
-                syb = on ? ty : syb;
+                // x + (-0) == x for every x: lanes past their degree add -0
+                sxb = dbits(__dadd_rn(bitsd(sxb), bitsd(v[u].x)));
+                syb = dbits(__dadd_rn(bitsd(syb), bitsd(v[u].y)));
                 float hx, lx, hy, ly;
                 const bool okk = head_tail(v[u].x, hx, lx) & head_tail(v[u].y, hy, ly);
                 const float2 L = make_float2((hx - phx) + (lx - plx), (hy - phy) + (ly - ply));
