@@ -311,6 +311,8 @@ def main():
                     help="A: Jacobi (the headline); B: multicolour Gauss-Seidel")
     ap.add_argument("--skip-unchanged", action="store_true",
                     help="leave unchanged tiles as they are (identical results; not the headline)")
+    ap.add_argument("--l2-window", action="store_true",
+                    help="persisting L2 window over the gathered coordinates (identical results)")
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch(args)
@@ -338,7 +340,7 @@ def main():
 
     stream = torch.cuda.Stream()
     variant = dict(kernel=args.kernel, precision=args.precision, form=args.form,
-                   skip_unchanged=args.skip_unchanged)
+                   skip_unchanged=args.skip_unchanged, l2_window=args.l2_window)
     g = sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, stream=stream.cuda_stream, **variant)
     xy0 = torch.from_numpy(mesh.xy).to("cuda")
     torch.cuda.synchronize()
@@ -397,7 +399,8 @@ def main():
     # DRAM bytes of one pass-kernel launch: ncu dram__bytes_read.sum +
     # dram__bytes_write.sum of a 2048x2048 capture of this kernel (361.4 MB),
     # scaled by the node count to the 4096x4096 mesh; None for other sizes
-    headline = args.kernel == "auto" and args.precision == 64 and args.form == "A" and not args.skip_unchanged
+    headline = (args.kernel == "auto" and args.precision == 64 and args.form == "A" and not args.skip_unchanged
+                and not args.l2_window)
     traffic = 1445.6e6 if (mesh.n == 4096 * 4096 and headline) else None
     adj_words = adjacency_words(mesh)
     bytes_pass = algorithmic_bytes_per_pass(mesh.n, g.n_free, adj_words, 16 if args.precision == 64 else 8)
@@ -424,7 +427,7 @@ def main():
                           "form": "A (Jacobi, ping-pong)" if args.form == "A" else "B (coloured Gauss-Seidel, in place)",
                           "l2": "inputs larger than L2 (no flush)",
                           "parallelism": "replicas" if world > 1 else "single",
-                          "skip_unchanged": bool(args.skip_unchanged),
+                          "skip_unchanged": bool(args.skip_unchanged), "l2_window": bool(args.l2_window),
                           "tiles_skipped_frac": sum(i["tiles_skipped"] for i in infos)
                           / (((mesh.n + 31) // 32) * max(1, passes))},
                "e2e": {"value": e2e_value, "unit": "node-updates/s",

@@ -79,7 +79,11 @@ typedef struct sls_options {
     int32_t kernel;        /* SLS_KERNEL_*                                                   */
     int32_t record_accept; /* 1: keep the per-node accept decisions of the last pass         */
     int32_t block_size;    /* threads per block; 0 = library default                         */
-    int32_t l2_window;     /* 1: L2 persisting access window over the coordinates            */
+    int32_t l2_window;     /* 1: each pass marks the coordinates it gathers from as
+                              persisting in L2 (a stream access-policy window; the share
+                              that fits the context's persisting carve-out, which this
+                              sets with cudaDeviceSetLimit), cleared when sls_smooth
+                              returns.  Same results; see the measured effect before use.  */
     int32_t passes_per_check; /* passes launched between host checks of the stop rule; 0 = 16 */
     int32_t host_build;    /* 1: build the adjacency on the host; 0: on the device (default;
                               the host build is still used for nodes in more than 32

@@ -33,6 +33,8 @@ struct sls_mesh {
     uint2 *halo = nullptr;        // skip_unchanged: kHaloEntries (tile, mask) pairs per 32-node tile
     uint32_t *chg[2] = {nullptr, nullptr};  // per tile: nodes changed by the last two passes
     uint32_t *accm = nullptr;     // per tile: nodes accepted when the tile was last computed
+    size_t l2_persist = 0;        // l2_window: persisting L2 bytes set aside for this context
+    size_t l2_win_max = 0;        //            largest access-policy window the device accepts
     int block = 256, grid = 0;
     bool screened = true;         // screened kernel (else the plain FP64 kernel)
     sls_info last{};

@@ -60,6 +60,20 @@ static sls_status mesh_setup(sls_mesh *M, const sls_options &o)
     M->screened = o.kernel != SLS_KERNEL_FP64 && !M->f32;
     if (M->screened && M->block > 128) M->block = 128;  // the screened kernel is built for <= 128
     if (M->f32 && M->block > 256) M->block = 256;  // the binary32 kernel is built for <= 256
+    if (o.l2_window) {
+        // Persisting L2 for the coordinates each pass gathers from: the
+        // context's persisting carve-out covers at most one coordinate array.
+        int maxp = 0, maxw = 0;
+        cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, M->device);
+        cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, M->device);
+        const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
+        M->l2_persist = std::min((size_t)(maxp > 0 ? maxp : 0), cbytes);
+        M->l2_win_max = (size_t)(maxw > 0 ? maxw : 0);
+        if (M->l2_persist > 0 && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, M->l2_persist) != cudaSuccess) {
+            cudaGetLastError();
+            M->l2_persist = 0;
+        }
+    }
     M->grid = device_sm_count() * (M->f32        ? pass_f32_occupancy(o.layout, M->block)
                                    : M->screened ? pass_screened_occupancy(o.layout, M->block)
                                                  : pass_fp64_occupancy(o.layout, M->block));
@@ -200,8 +214,25 @@ void mesh_release(sls_mesh *M)
     M->stream = nullptr;
 }
 
+// Access-policy window of the handle's stream: `bytes` from `base` persist in
+// L2 (the share that fits the carve-out), the rest streams; bytes = 0 clears
+// it.  Best effort: a refusal leaves the ordinary caching.
+static void set_l2_window(const sls_mesh *M, const void *base, size_t bytes)
+{
+    if (M->l2_persist == 0 || M->l2_win_max == 0) return;
+    cudaStreamAttrValue v{};
+    bytes = std::min(bytes, M->l2_win_max);
+    v.accessPolicyWindow.base_ptr = bytes ? const_cast<void *>(base) : nullptr;
+    v.accessPolicyWindow.num_bytes = bytes;
+    v.accessPolicyWindow.hitRatio = bytes ? (float)std::min(1.0, (double)M->l2_persist / (double)bytes) : 0.0f;
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    if (cudaStreamSetAttribute(M->stream, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess) cudaGetLastError();
+}
+
 static cudaError_t launch_pass(const sls_mesh *M, const PassArgs &a)
 {
+    if (M->opt.l2_window) set_l2_window(M, a.in, (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)M->n);
     if (M->f32) return launch_pass_f32(a, M->opt.layout, M->block, M->grid, M->stream);
     return M->screened ? launch_pass_screened(a, M->opt.layout, M->block, M->grid, M->stream)
                        : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream);
@@ -292,6 +323,11 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
             SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "pass");
             if (M->h_stats->executed == 0u || M->h_stats->maxd2_bits < thr_bits) break;
         }
+    }
+    if (M->opt.l2_window && M->l2_persist) {  // leave no persisting lines behind
+        set_l2_window(M, nullptr, 0);
+        SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "pass");
+        if (cudaCtxResetPersistingL2Cache() != cudaSuccess) cudaGetLastError();
     }
     std::vector<PassStats> hs(launched);
     SLS_CUDA_TRY(cudaMemcpyAsync(hs.data(), M->stats, sizeof(PassStats) * launched,

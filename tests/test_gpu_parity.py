@@ -268,3 +268,12 @@ def test_screened_matches_fp64_on_many_meshes(sls):
         assert np.array_equal(outs[1][1], outs[0][1])
         for key in ("iterations", "accepted_last", "maxd2_last"):
             assert outs[1][2][key] == outs[0][2][key]
+
+
+def test_l2_window_same_results(sls):
+    # the persisting-L2 option changes caching only
+    for mesh, iters in ((meshgen.small_grid(), 30), (meshgen.jittered_grid(300, 200, 0.35, 4), 60)):
+        got, ref = _run_both(sls, mesh, iters, tol=1e-10, l2_window=True)
+        _check(got, ref, f"l2 window n={mesh.n}")
+        got, ref = _run_both(sls, mesh, iters, l2_window=True, layout="soa", copy_back=True)
+        _check(got, ref, f"l2 window soa/copy-back n={mesh.n}")
