@@ -428,8 +428,8 @@ def main():
                           "l2": "inputs larger than L2 (no flush)",
                           "parallelism": "replicas" if world > 1 else "single",
                           "skip_unchanged": bool(args.skip_unchanged), "l2_window": bool(args.l2_window),
-                          "tiles_skipped_frac": sum(i["tiles_skipped"] for i in infos)
-                          / (((mesh.n + 31) // 32) * max(1, passes))},
+                          "nodes_skipped_frac": sum(i["nodes_skipped"] for i in infos)
+                          / (mesh.n * max(1, passes))},
                "e2e": {"value": e2e_value, "unit": "node-updates/s",
                        "h2d_bytes_per_step": int(mesh.xy.nbytes + mesh.tri.nbytes + mesh.boundary.nbytes),
                        "d2h_bytes_per_step": int(mesh.xy.nbytes)},

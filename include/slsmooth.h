@@ -123,8 +123,9 @@ typedef struct sls_info {
     int64_t launches;      /* kernel launches issued by the last sls_smooth call (passes
                               launched after the tolerance was met return at once; 0 from
                               the batched and served forms)                                 */
-    int64_t tiles_skipped; /* 32-node tiles not recomputed by the last sls_smooth call
-                              (skip_unchanged; summed over its passes)                       */
+    int64_t nodes_skipped; /* node updates not recomputed by the last sls_smooth call
+                              (skip_unchanged: the nodes of the skipped tiles, summed over
+                              its passes)                                                   */
 } sls_info;
 
 typedef struct sls_mesh sls_mesh;

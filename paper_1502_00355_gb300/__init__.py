@@ -41,13 +41,13 @@ class Options(C.Structure):
 class Info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("accepted_last", C.c_int64),
                 ("max_d2_last", C.c_double), ("fp64_fallbacks", C.c_int64), ("launches", C.c_int64),
-                ("tiles_skipped", C.c_int64)]
+                ("nodes_skipped", C.c_int64)]
 
     def as_dict(self) -> dict:
         return dict(iterations=self.iterations, converged=self.converged,
                     accepted_last=self.accepted_last, maxd2_last=self.max_d2_last,
                     fp64_fallbacks=self.fp64_fallbacks, launches=self.launches,
-                    tiles_skipped=self.tiles_skipped)
+                    nodes_skipped=self.nodes_skipped)
 
 
 class SlsError(RuntimeError):

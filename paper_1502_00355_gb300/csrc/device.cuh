@@ -13,7 +13,7 @@ struct PassStats {
     unsigned long long nacc;        // accepted free nodes
     unsigned long long fallbacks;   // accept tests redone in FP64 by the screened kernel
     unsigned int executed;          // 1 once the pass ran (0: skipped after convergence)
-    unsigned int tiles_skipped;     // 32-node tiles left as they were (unchanged inputs)
+    unsigned int nodes_skipped;     // node updates not recomputed (unchanged inputs)
 };
 
 // Arguments of one Jacobi pass over one mesh.

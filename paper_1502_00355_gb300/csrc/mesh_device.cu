@@ -337,11 +337,11 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
     long long fb = 0, sk = 0;
     for (; it < launched && hs[it].executed; ++it) {
         fb += (long long)hs[it].fallbacks;
-        sk += (long long)hs[it].tiles_skipped;
+        sk += (long long)hs[it].nodes_skipped;
     }
     info.iterations = it;
     info.fp64_fallbacks = fb;
-    info.tiles_skipped = sk;
+    info.nodes_skipped = sk;
     info.launches = kernels;
     if (it > 0) {
         const PassStats &l = hs[it - 1];

@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
     if (blockIdx.x == 0 && tid == 0) a.stats[a.q].executed = 1u;
 
     unsigned long long best = 0ull, nacc = 0ull, nfb = 0ull;
-    unsigned nskip = 0u;  // tiles this warp left as they were (lane 0)
+    unsigned nskip = 0u;  // node updates this warp left as they were (lane 0)
     float2 *loc = s_loc + tid;
     Deferred *wq = s_q + 64 * warp;
     int qn = 0;  // warp-uniform queue length
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
                 if (lane == 0) {
                     a.chg_cur[wt] = 0u;
                     nacc += (unsigned long long)__popc(a.accm[wt]);
-                    ++nskip;
+                    nskip += (unsigned)(a.n - wt * 32 < 32 ? a.n - wt * 32 : 32);
                 }
                 continue;
             }
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
     }
     __syncwarp();
     drain_queue<LAYOUT>(a, wq, qn, true, best, nacc);
-    if (nskip) atomicAdd(&a.stats[a.q].tiles_skipped, nskip);
+    if (nskip) atomicAdd(&a.stats[a.q].nodes_skipped, nskip);
     block_reduce_stats(a.stats + a.q, best, nacc, nfb);
 }
 
