@@ -133,6 +133,40 @@ def reduce_over_ranks(ms: float, updates: float, device="cpu"):
     return float(t.item()), float(u.item())
 
 
+def rank_env():
+    """(world size, rank, local rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def shard(items, rank: int, world: int):
+    """The items of one rank: every world-th one from position `rank` on.
+    The batched and served workloads are independent meshes, so ranks share
+    no data; with a list of world x k items each rank gets k of them."""
+    return list(items)[rank::world]
+
+
+def reduce_flag(ok: bool, device="cpu") -> bool:
+    """Logical AND of a flag over all ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([1 if ok else 0], dtype=torch.int32, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return bool(t.item())
+
+
+def init_ranks():
+    """One process per GPU: select the local GPU and join the NCCL group."""
+    import torch
+    import torch.distributed as dist
+    world, rank, local = rank_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    return world, rank
+
+
 def cpu_oracle_rate(mesh, passes: int, precision: int = 64, form: str = "A"):
     """Times `passes` passes of the oracle: Form A FP64 on all host cores
     (OpenMP build); binary32 or Form B on one core (the oracle's sequential
@@ -181,9 +215,12 @@ def run_batch(args):
     """Batched form: many meshes of uneven size in one graph launch, against
     smoothing the same meshes one request at a time (same kernels)."""
     import torch
+    import torch.distributed as dist
     import paper_1502_00355_gb300 as sls
+    world, rank = init_ranks()
     sls.lib()
-    specs = meshgen.batch_specs(args.batch_meshes)
+    # weak scaling: every rank smooths its own batch of batch_meshes meshes
+    specs = shard(meshgen.batch_specs(args.batch_meshes * world), rank, world)
     meshes = [meshgen.batch_mesh(sp) for sp in specs]
     iters = [sp[2] for sp in specs]
     total_nodes = sum(m.n for m in meshes)
@@ -193,6 +230,8 @@ def run_batch(args):
         batch.reset()
         batch.smooth()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     times = []
     for _ in range(args.steps):
         batch.reset()
@@ -200,7 +239,10 @@ def run_batch(args):
         infos = batch.smooth()                       # one cudaGraphLaunch, returns when done
         times.append(time.perf_counter() - t0)
     updates = sum(m.n * inf["iterations"] for m, inf in zip(meshes, infos))
-    batched = updates * len(times) / sum(times)
+    if world > 1:
+        dist.barrier()
+    ms_max, all_updates = reduce_over_ranks(1e3 * sum(times) / len(times), float(updates), device="cuda")
+    batched = all_updates / (ms_max * 1e-3)
     got = [batch.coords(j) for j in range(len(meshes))]
     # one request at a time: the same meshes, each smoothed by its own calls
     batch.reset()
@@ -208,13 +250,18 @@ def run_batch(args):
     for h, it in zip(handles, iters):
         h.smooth(it)
     per_req_s = time.perf_counter() - t0
-    per_request = updates / per_req_s
-    same = all(np.array_equal(h.coords(), g) for h, g in zip(handles, got))
-    out = {"metric": "node-updates/s (batched)", "value": batched, "unit": "node-updates/s", "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+    per_ms_max, _ = reduce_over_ranks(1e3 * per_req_s, float(updates), device="cuda")
+    per_request = all_updates / (per_ms_max * 1e-3)
+    same = reduce_flag(all(np.array_equal(h.coords(), g) for h, g in zip(handles, got)), device="cuda")
+    if rank != 0:
+        return
+    out = {"metric": "node-updates/s (batched)", "value": batched, "unit": "node-updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"batch{len(meshes)}_logu1K-256K_aspect1-4_iters10-100", "meshes": len(meshes),
-                      "total_nodes": total_nodes, "block": None},
+           "config": {"workload": f"batch{len(meshes)}_logu1K-256K_aspect1-4_iters10-100",
+                      "meshes_per_gpu": len(meshes), "meshes": len(meshes) * world,
+                      "nodes_rank0": total_nodes, "block": None,
+                      "parallelism": f"{world} ranks, independent meshes (no collective)" if world > 1 else "single"},
            "per_request": {"value": per_request, "unit": "node-updates/s", "seconds": per_req_s},
            "speedup_vs_per_request": batched / per_request, "identical_results": bool(same)}
     print(json.dumps(out), flush=True)
@@ -225,9 +272,13 @@ def run_serve(args):
     continuous-batching server, against one request at a time (FIFO)."""
     import threading
     import torch
+    import torch.distributed as dist
     import paper_1502_00355_gb300 as sls
+    world, rank = init_ranks()
     sls.lib()
-    reqs = meshgen.serve_requests(args.serve_requests, rate=args.serve_rate, hi=args.serve_max_n)
+    # weak scaling: every rank serves its own stream at the configured rate
+    reqs = shard(meshgen.serve_requests(args.serve_requests * world, rate=args.serve_rate * world,
+                                        hi=args.serve_max_n), rank, world)
     meshes = [meshgen.jittered_grid(nx, ny, 0.3, seed, numbering="morton") for _, nx, ny, _, seed in reqs]
     caps = [r[3] for r in reqs]
     arrivals = [r[0] for r in reqs]
@@ -239,6 +290,8 @@ def run_serve(args):
     srv = sls.Server()
     results = [None] * len(reqs)
     ids = [None] * len(reqs)
+    if world > 1:
+        dist.barrier()
     t_start = time.perf_counter()
 
     def submitter():
@@ -259,6 +312,8 @@ def run_serve(args):
     updates = sum(m.n * r[1]["iterations"] for m, r in zip(meshes, results))
     # FIFO baseline: one job on the GPU at a time, same kernels, same arrivals
     lat = []
+    if world > 1:
+        dist.barrier()
     t_start = time.perf_counter()
     busy = 0.0
     same = True
@@ -274,16 +329,29 @@ def run_serve(args):
         lat.append(1e3 * (time.perf_counter() - t_start - arrivals[k]))
         same = same and np.array_equal(xy, results[k][0]) and inf["iterations"] == results[k][1]["iterations"]
     fifo_wall = time.perf_counter() - t_start
-    out = {"metric": "node-updates/s (served)", "value": updates / wall, "unit": "node-updates/s", "n_gpus": 1,
-           "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+    # over ranks: slowest wall times, summed work, worst percentiles
+    wall_ms, all_updates = reduce_over_ranks(1e3 * wall, float(updates), device="cuda")
+    fifo_ms, _ = reduce_over_ranks(1e3 * fifo_wall, 0.0, device="cuda")
+    p50, _ = reduce_over_ranks(st["p50_ms"], 0.0, device="cuda")
+    p99, _ = reduce_over_ranks(st["p99_ms"], 0.0, device="cuda")
+    f50, _ = reduce_over_ranks(float(np.percentile(lat, 50)), 0.0, device="cuda")
+    f99, _ = reduce_over_ranks(float(np.percentile(lat, 99)), 0.0, device="cuda")
+    same = reduce_flag(same, device="cuda")
+    if rank != 0:
+        return
+    served = all_updates / (wall_ms * 1e-3)
+    fifo = all_updates / (fifo_ms * 1e-3)
+    out = {"metric": "node-updates/s (served)", "value": served, "unit": "node-updates/s", "n_gpus": world,
+           "steps": 1, "warmup": 1, "ms_per_step": wall_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"serve{len(reqs)}_poisson{args.serve_rate:g}_logu1K-{args.serve_max_n}_cap10-200_tol1e-9",
-                      "requests": len(reqs)},
-           "served": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "node_updates_per_s_busy": st["node_updates_per_s"],
-                      "wall_s": wall},
-           "fifo": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                    "node_updates_per_s": updates / fifo_wall, "wall_s": fifo_wall, "busy_s": busy},
-           "speedup_vs_fifo": (updates / wall) / (updates / fifo_wall), "identical_results": bool(same)}
+                      "requests_per_gpu": len(reqs), "requests": len(reqs) * world,
+                      "parallelism": f"{world} ranks, one server each (no collective)" if world > 1 else "single"},
+           "served": {"p50_ms": p50, "p99_ms": p99, "node_updates_per_s_busy_rank0": st["node_updates_per_s"],
+                      "wall_s": wall_ms * 1e-3},
+           "fifo": {"p50_ms": f50, "p99_ms": f99, "node_updates_per_s": fifo, "wall_s": fifo_ms * 1e-3,
+                    "busy_s_rank0": busy},
+           "speedup_vs_fifo": served / fifo, "identical_results": bool(same)}
     print(json.dumps(out), flush=True)
 
 
@@ -291,7 +359,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="large", choices=["large", "batch", "serve"])
     ap.add_argument("--batch-meshes", type=int, default=2048)
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-max-n", type=int, default=262144)
     ap.add_argument("--gpus", type=int, default=1)

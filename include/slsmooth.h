@@ -109,7 +109,7 @@ typedef struct sls_options {
                               previous pass only, Eq. 2).  Results are identical to 0; the
                               gain grows as the mesh settles.  Needs form = 0, precision = 64
                               and the screened kernel (SLS_KERNEL_AUTO or _FILTERED); costs
-                              136 bytes of device memory per 32 nodes.  The batched and
+                              140 bytes of device memory per 32 nodes.  The batched and
                               allocation-free forms compute every tile; the server rejects it. */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle    */
 } sls_options;
