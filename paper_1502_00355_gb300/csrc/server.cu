@@ -4,8 +4,9 @@
 // sls_submit copies a job's inputs and hands them to builder threads, which
 // validate the mesh and build its adjacency on the host.  A scheduler thread
 // admits built jobs in arrival order while their device footprint fits the
-// memory budget, uploads them on a copy stream (overlapping the running
-// round), and runs rounds: one launch of the batched pass kernel over every
+// memory budget and hands them to an uploader thread, which copies them to
+// the device on a copy stream (overlapping the running round, and keeping
+// the host-to-device copies off the scheduler's thread); it runs rounds: one launch of the batched pass kernel over every
 // active job, each at its own pass index.  After each round it reads every
 // active job's statistics record, retires the jobs that reached their
 // iteration cap or tolerance, copies their coordinates back and frees their
@@ -50,6 +51,7 @@ struct ServerJob {
     uint32_t *d_off = nullptr, *d_adj = nullptr;
     PassStats *d_stats = nullptr;
     cudaEvent_t uploaded = nullptr;
+    int upload_state = 0;  // 0 pending, 1 copies enqueued (event recorded), 2 failed
     int base_round = 0;
     int iterations = 0;
     // result
@@ -72,14 +74,14 @@ struct sls_server {
     cudaMemPool_t pool = nullptr;
 
     std::mutex mu;
-    std::condition_variable cv_build, cv_sched, cv_done;
-    std::deque<std::shared_ptr<ServerJob>> to_build, queued;
+    std::condition_variable cv_build, cv_sched, cv_done, cv_upload;
+    std::deque<std::shared_ptr<ServerJob>> to_build, queued, to_upload;
     std::vector<std::shared_ptr<ServerJob>> uploading, active;
     std::unordered_map<uint64_t, std::shared_ptr<ServerJob>> jobs;
     uint64_t next_id = 1;
     bool stop = false;
     std::vector<std::thread> builders;
-    std::thread sched;
+    std::thread sched, uploader;
 
     // job table and warp tasks of the active set
     JobDesc *d_jobs = nullptr, *h_jobs = nullptr;
@@ -121,7 +123,7 @@ void builder_loop(sls_server *S)
         }
         const int64_t n = (int64_t)J->xy.size() / 2, m = (int64_t)J->tri.size() / 3;
         sls_status st = build_host_mesh(J->xy.data(), n, J->tri.data(), m,
-                                        J->has_boundary ? J->boundary.data() : nullptr, J->hm, 4);
+                                        J->has_boundary ? J->boundary.data() : nullptr, J->hm, 1);
         std::lock_guard<std::mutex> lk(S->mu);
         J->tri.clear();
         J->tri.shrink_to_fit();
@@ -176,6 +178,27 @@ bool start_upload(sls_server *S, ServerJob &J)
          cudaEventRecord(J.uploaded, cs) == cudaSuccess;
     if (!ok) cudaGetLastError();
     return ok;
+}
+
+// Uploads admitted jobs in admission order, off the scheduler's thread (the
+// host buffers are pageable, so each copy occupies the calling thread).
+void uploader_loop(sls_server *S)
+{
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::shared_ptr<ServerJob> J;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_upload.wait(lk, [S] { return S->stop || !S->to_upload.empty(); });
+            if (S->stop) return;
+            J = S->to_upload.front();
+            S->to_upload.pop_front();
+        }
+        const bool ok = start_upload(S, *J);
+        std::lock_guard<std::mutex> lk(S->mu);
+        J->upload_state = ok ? 1 : 2;
+        S->cv_sched.notify_all();
+    }
 }
 
 bool grow_host(PassStats *&h, size_t &cap, size_t need)
@@ -260,12 +283,13 @@ void scheduler_loop(sls_server *S)
     cudaSetDevice(S->device);
     bool dirty = true;
     for (;;) {
-        std::vector<std::shared_ptr<ServerJob>> admit;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_sched.wait(lk, [S] {
-                return S->stop || !S->active.empty() || !S->uploading.empty() ||
-                       (!S->queued.empty() && S->used + S->queued.front()->footprint <= S->budget);
+                if (S->stop || !S->active.empty()) return true;
+                for (auto &J : S->uploading)
+                    if (J->upload_state != 0) return true;
+                return !S->queued.empty() && S->used + S->queued.front()->footprint <= S->budget;
             });
             if (S->stop) break;
             while (!S->queued.empty() && S->used + S->queued.front()->footprint <= S->budget) {
@@ -273,23 +297,34 @@ void scheduler_loop(sls_server *S)
                 S->queued.pop_front();
                 S->used += J->footprint;
                 J->state = kUploading;
-                admit.push_back(J);
+                J->upload_state = 0;
+                S->uploading.push_back(J);
+                S->to_upload.push_back(J);
             }
-        }
-        for (auto &J : admit) {
-            if (!start_upload(S, *J)) {
-                std::lock_guard<std::mutex> lk(S->mu);
-                free_job_device(S, *J);
-                S->used -= J->footprint;
-                fail_job(S, *J, SLS_ERR_OOM, "device allocation or upload failed");
-                continue;
-            }
-            S->uploading.push_back(J);
+            if (!S->to_upload.empty()) S->cv_upload.notify_one();
         }
         // jobs whose upload has finished join in this round (the copies
         // overlap the previous round); with nothing running, wait for them
         for (size_t k = 0; k < S->uploading.size();) {
             auto J = S->uploading[k];
+            int ust;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                ust = J->upload_state;
+                if (ust == 2) {
+                    free_job_device(S, *J);
+                    S->used -= J->footprint;
+                    fail_job(S, *J, SLS_ERR_OOM, "device allocation or upload failed");
+                }
+            }
+            if (ust == 2) {
+                S->uploading.erase(S->uploading.begin() + k);
+                continue;
+            }
+            if (ust == 0) {  // copies not enqueued yet
+                ++k;
+                continue;
+            }
             if (S->active.empty()) cudaEventSynchronize(J->uploaded);
             if (cudaEventQuery(J->uploaded) == cudaSuccess) {
                 J->xy.clear();
@@ -379,7 +414,13 @@ void scheduler_loop(sls_server *S)
             dirty = true;
         }
     }
-    // cancel what is left
+    // cancel what is left, once the uploader has stopped touching jobs
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_upload.notify_all();
+    if (S->uploader.joinable()) S->uploader.join();
     std::lock_guard<std::mutex> lk(S->mu);
     for (auto *list : {&S->active, &S->uploading}) {
         for (auto &J : *list) {
@@ -428,7 +469,10 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
     S->block = (o.block_size >= 64 && o.block_size <= 512) ? o.block_size : 256;
     S->grid = device_sm_count() * batch_pass_occupancy(o.layout, S->block);
     sls_server *raw = S.release();
-    for (int b = 0; b < 4; ++b) raw->builders.emplace_back(builder_loop, raw);
+    // one single-threaded adjacency build per host core (jobs are small and many)
+    const int nb = std::max(2, (int)std::thread::hardware_concurrency());
+    for (int b = 0; b < nb; ++b) raw->builders.emplace_back(builder_loop, raw);
+    raw->uploader = std::thread(uploader_loop, raw);
     raw->sched = std::thread(scheduler_loop, raw);
     *out = raw;
     return SLS_OK;
@@ -517,6 +561,7 @@ sls_status sls_server_destroy(sls_server *S)
     }
     S->cv_build.notify_all();
     S->cv_sched.notify_all();
+    S->cv_upload.notify_all();
     for (auto &t : S->builders) t.join();
     if (S->sched.joinable()) S->sched.join();
     cudaStreamSynchronize(S->copy_stream);
