@@ -49,19 +49,15 @@ struct HostMesh {
     std::vector<uint8_t> fixed;        // n
 };
 
-// Processing order of the free nodes of one Form-B colour class: tiles of
-// kOrderTile consecutive node ids, inside a tile the class's nodes by
-// ascending (degree, triangle count), each clamped to 255, then id, so that a
-// warp mostly holds nodes of one degree.
+// Processing order of the free nodes of one Form-B colour class: the class's
+// nodes in ascending id, built tile by tile (kOrderTile consecutive ids per
+// block).  Id order keeps a warp's reads and in-place writes close together;
+// sorting by degree inside a tile was slower (scattered accesses).
 constexpr int kOrderTile = 1024;
 
 // Seed of the Form-B colouring priorities: node i has priority
 // splitmix64(kColourSeed + i).
 constexpr unsigned long long kColourSeed = 150200355ull;
-SLS_HOST_DEVICE inline uint32_t order_key(uint32_t deg, uint32_t ntri)
-{
-    return ((deg < 255u ? deg : 255u) << 8) | (ntri < 255u ? ntri : 255u);
-}
 
 // sqrt((xmax - xmin)^2 + (ymax - ymin)^2), the bounding-box diagonal D.
 double bbox_diagonal(double xmin, double xmax, double ymin, double ymax);

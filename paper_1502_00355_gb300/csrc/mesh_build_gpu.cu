@@ -368,9 +368,9 @@ __global__ void __launch_bounds__(kOrderTile) order_count_kernel(const uint32_t 
     if (threadIdx.x == 0) cnt[blockIdx.x] = (unsigned)k;
 }
 
-// One block of kOrderTile threads per tile: the tile's free nodes sorted by
-// (order_key, id) with a bitonic sort in shared memory, written at the tile's
-// offset.
+// One block of kOrderTile threads per tile: the tile's free nodes of the
+// class in id order (a bitonic sort of the members' ids in shared memory,
+// non-members sorting last), written at the tile's offset.
 __global__ void __launch_bounds__(kOrderTile) order_sort_kernel(const uint32_t *__restrict__ node_off,
                                                                  const uint32_t *__restrict__ adj, int64_t n,
                                                                  const int32_t *__restrict__ colour, int32_t c,
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kOrderTile) order_sort_kernel(const uint32_t *
     if (i < n) {
         const uint32_t meta = adj[node_off[i]];
         if (!(meta & 0x80000000u) && (!colour || colour[i] == c))
-            k = (order_key(meta & 0xffffu, (meta >> 16) & 0x7fffu) << 10) | tid;
+            k = tid;
     }
     key[tid] = k;
     __syncthreads();
@@ -537,7 +537,7 @@ sls_status build_tile_halo(sls_mesh *M, cudaStream_t s)
 namespace {
 
 // One segment of the processing order: the free nodes of colour c (all free
-// nodes when colour is null), tile by tile, by (degree, triangles, id).
+// nodes when colour is null), in id order.
 sls_status order_segment(sls_mesh *M, const int32_t *colour, int32_t c, uint32_t *dst, int64_t expect,
                          int64_t *count, cudaStream_t s)
 {
