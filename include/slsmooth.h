@@ -196,8 +196,9 @@ sls_status sls_mesh_destroy(sls_mesh *mesh);
  * stop rules.  The handles must outlive the batch; sls_batch_smooth advances
  * their coordinates in place.  The coordinates at packing time are saved for
  * sls_batch_reset.  With opt == NULL or opt->block_size == 0 the block size
- * is autotuned by timing one full batch smooth per candidate (128, 256, 512
- * threads), restoring the saved coordinates after each trial. */
+ * is autotuned by timing one full batch smooth per candidate (64, 96, 128
+ * threads), restoring the saved coordinates after each trial; an explicit
+ * block_size must be 32, 64, 96 or 128 (SLS_ERR_INVALID otherwise). */
 sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *iters,
                             const double *tol_rel, const sls_options *opt, sls_batch **out);
 

@@ -37,7 +37,7 @@ struct sls_batch {
     int64_t nstats = 0;
     std::vector<double *> d_start;     // per mesh: the packed starting coordinates
     int rounds = 0;
-    int block = 256, grid = 0;
+    int block = 128, grid = 0;
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -167,9 +167,9 @@ sls_status reset(sls_batch *B)
 // each candidate, restoring the starting coordinates after every trial.
 sls_status autotune(sls_batch *B)
 {
-    const int candidates[3] = {128, 256, 512};
+    const int candidates[3] = {64, 96, 128};  // the kernel is built for 6 blocks of <= 128
     float best_ms = -1.0f;
-    int best_block = 256;
+    int best_block = 128;
     cudaEvent_t e0, e1;
     BATCH_TRY(cudaEventCreate(&e0), "event");
     BATCH_TRY(cudaEventCreate(&e1), "event");
@@ -290,9 +290,10 @@ sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *i
             return fail_free(fail(SLS_ERR_CUDA, "save starting coordinates"));
     }
     if (cudaStreamSynchronize(B->stream) != cudaSuccess) return fail_free(fail(SLS_ERR_CUDA, "batch set-up"));
-    if (o.block_size > 0 && o.block_size != 256) {
-        if (o.block_size < 64 || o.block_size > 512) return fail_free(fail(SLS_ERR_INVALID, "batch block_size must be in [64, 512]"));
-        B->block = o.block_size;
+    if (opt != nullptr && opt->block_size > 0) {
+        if (opt->block_size < 32 || opt->block_size > 128)
+            return fail_free(fail(SLS_ERR_INVALID, "batch block_size must be 32, 64, 96 or 128"));
+        B->block = opt->block_size;
     }
     B->grid = device_sm_count() * batch_pass_occupancy(B->layout, B->block);
     if (opt == nullptr || opt->block_size == 0) {

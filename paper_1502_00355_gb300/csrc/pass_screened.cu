@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
 // deferred queue is drained and the statistics flushed whenever the warp
 // moves to another job, so every record gets exactly its own job's counts.
 template <int LAYOUT>
-__global__ void __launch_bounds__(512) batch_pass_kernel(const JobDesc *__restrict__ jobs,
+__global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__restrict__ jobs,
                                                           const WarpTask *__restrict__ tasks, int64_t ntasks,
                                                           int round)
 {

@@ -466,7 +466,7 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
         uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
         cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    S->block = (o.block_size >= 64 && o.block_size <= 512) ? o.block_size : 256;
+    S->block = (opt != nullptr && opt->block_size >= 32 && opt->block_size <= 128) ? opt->block_size : 128;
     S->grid = device_sm_count() * batch_pass_occupancy(o.layout, S->block);
     sls_server *raw = S.release();
     // one single-threaded adjacency build per host core (jobs are small and many)

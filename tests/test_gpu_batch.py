@@ -33,7 +33,7 @@ def _specs(k, seed, lo=60, hi=4000):
     return out
 
 
-@pytest.mark.parametrize("block", [0, 128, 512])
+@pytest.mark.parametrize("block", [0, 64, 128])
 def test_batch_matches_oracle_per_mesh(sls, block):
     specs = _specs(24, 3 + block)
     meshes = [meshgen.jittered_grid(nx, ny, 0.3, s, numbering="morton") for nx, ny, _, s in specs]
@@ -97,3 +97,6 @@ def test_batch_rejects_bad_input(sls):
     b = sls.Batch([h], [0])
     assert b.smooth()[0]["iterations"] == 0
     assert np.array_equal(h.coords(), m.xy)
+    with pytest.raises(sls.SlsError) as e:  # the kernel is built for blocks of at most 128
+        sls.Batch([h], [3], block_size=256)
+    assert e.value.code == 1
