@@ -25,8 +25,8 @@ static sls_status dev_alloc(void **p, size_t bytes, const char *what)
     return SLS_OK;
 }
 
-// Host interleaved -> the handle's layout.
-static void to_layout(const double *xy, int64_t n, int layout, std::vector<double> &tmp)
+// Host interleaved -> SoA (x[n] then y[n]).
+static void to_soa(const double *xy, int64_t n, std::vector<double> &tmp)
 {
     tmp.resize(2 * n);
     for (int64_t i = 0; i < n; ++i) {
@@ -130,7 +130,7 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
         SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload coordinates");
     } else {
         std::vector<double> tmp;
-        to_layout(xy, M->n, 1, tmp);
+        to_soa(xy, M->n, tmp);
         SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[0], tmp.data(), cbytes, cudaMemcpyHostToDevice, M->stream), "upload coordinates");
         SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload coordinates");
     }
@@ -422,7 +422,7 @@ sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
         std::vector<double> tmp;
         const double *src = xy;
         if (M->opt.layout == 1) {
-            to_layout(xy, M->n, 1, tmp);
+            to_soa(xy, M->n, tmp);
             src = tmp.data();
         }
         SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[M->cur], src, cbytes, cudaMemcpyHostToDevice, M->stream), "upload");

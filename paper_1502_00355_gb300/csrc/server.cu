@@ -201,21 +201,6 @@ void uploader_loop(sls_server *S)
     }
 }
 
-bool grow_host(PassStats *&h, size_t &cap, size_t need)
-{
-    if (need <= cap) return true;
-    const size_t c = std::max<size_t>(need, 2 * cap);
-    cudaFreeHost(h);
-    h = nullptr;
-    cap = 0;
-    if (cudaMallocHost((void **)&h, sizeof(PassStats) * c) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    cap = c;
-    return true;
-}
-
 template <class T>
 bool grow_pair(T *&h, T *&d, size_t &cap, size_t need)
 {
