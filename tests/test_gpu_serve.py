@@ -99,3 +99,26 @@ def test_server_rejects_and_times_out(sls):
         srv.wait(123456789, timeout=0.1)
     assert e.value.code == 8
     srv.close()
+
+
+def test_server_destroyed_with_jobs_in_flight(sls):
+    # closing a server while jobs are building, queued, uploading and running
+    # cancels them and returns promptly (the uploader and builders stop first)
+    jobs = _jobs(40, 9)
+    srv = sls.Server(hbm_budget=48 * 1024 * 1024)
+    for m, cap, tol in jobs:
+        srv.submit(m.xy, m.tri, m.boundary, max_iter=200, tol=0.0)
+    done = threading.Event()
+
+    def closer():
+        srv.close()
+        done.set()
+
+    t = threading.Thread(target=closer)
+    t.start()
+    t.join(timeout=120.0)
+    assert done.is_set(), "sls_server_destroy did not return"
+    # the device is still usable afterwards
+    m = meshgen.jittered_grid(30, 30, 0.3, 3)
+    with sls.Mesh(m.xy, m.tri, m.boundary) as g:
+        assert g.smooth(3)["iterations"] == 3
