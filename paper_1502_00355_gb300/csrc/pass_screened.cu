@@ -170,8 +170,8 @@ __device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float C
 // Warp-synchronous: every lane of the warp calls it (have = false for lanes
 // without a node).  The neighbour loop runs to the warp's largest degree in
 // groups of four, every load of a group issued before its arithmetic; a lane
-// past its own degree keeps its sums, so each lane's FP64 additions are its
-// node's, in the stored order.
+// past its own degree adds -0 (x + (-0) == x for every double), so each
+// lane's sums are its node's, in the stored order.
 //
 // The accept test is screened with one error bound per side (before and
 // after the move) for all of the node's triangles.  The per-triangle bound
