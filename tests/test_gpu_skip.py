@@ -134,3 +134,19 @@ def test_rejected_where_unsupported(sls):
     with pytest.raises(sls.SlsError) as e:
         sls.Server(skip_unchanged=True)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("transform", ["shift_negative", "mixed_binades"])
+def test_domain_edges_and_random_numbering(sls, transform):
+    # signs and binades that send nodes through the screen's fallbacks, a
+    # random numbering that overflows the tile lists: still identical
+    mesh = meshgen.jittered_grid(70, 55, 0.35, 41, numbering="random")
+    xy = mesh.xy.copy()
+    xy = xy - 0.5 if transform == "shift_negative" else xy * 3.0 - 1.0
+    mesh.xy = xy
+    for strict in (False, True):
+        _check(sls, mesh, 200, tol=1e-10, strict=strict)
+    m2 = meshgen.jittered_grid(70, 55, 0.35, 41, numbering="morton")
+    m2.xy = m2.xy - 0.5 if transform == "shift_negative" else m2.xy * 3.0 - 1.0
+    info = _check(sls, m2, 200, tol=1e-10)
+    assert info["nodes_skipped"] > 0
