@@ -31,7 +31,9 @@
 // Coordinates are moved as 64-bit patterns, never held in FP64 registers
 // unless they take part in FP64 arithmetic: the compiler copies FP64
 // registers with FP64-pipe instructions.
+#include <atomic>
 #include <cfloat>
+#include <mutex>
 
 #include "div_small.cuh"
 #include "kernels.h"
@@ -578,11 +580,21 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
     }
 }
 
-bool g_consts_ready = false;
+// Constant memory and function attributes belong to a device: they are set
+// up once per device, with that device current.
+constexpr int kMaxDevices = 64;
+std::atomic<bool> g_consts_ready[kMaxDevices] = {};
+std::mutex g_consts_mu;
 
 cudaError_t ensure_constants()
 {
-    if (g_consts_ready) return cudaSuccess;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (g_consts_ready[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_consts_mu);
+    if (g_consts_ready[dev].load(std::memory_order_relaxed)) return cudaSuccess;
     double r[kFastMax + 1];
     double dg[kFastMax + 1];
     r[0] = 0.0;
@@ -591,7 +603,7 @@ cudaError_t ensure_constants()
         r[k] = 1.0 / (double)k;
         dg[k] = (double)k;
     }
-    cudaError_t e = cudaMemcpyToSymbol(c_recip, r, sizeof r);
+    e = cudaMemcpyToSymbol(c_recip, r, sizeof r);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_degree, dg, sizeof dg);
     if (e != cudaSuccess) return e;
     const void *fns[4] = {(const void *)pass_screened_kernel<0>, (const void *)pass_screened_kernel<1>,
@@ -600,7 +612,7 @@ cudaError_t ensure_constants()
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
     }
-    g_consts_ready = true;
+    g_consts_ready[dev].store(true, std::memory_order_release);
     return cudaSuccess;
 }
 
