@@ -201,7 +201,7 @@ def run_reference(args, mesh, workload):
     value = mesh.n * passes * len(times) / sum(times)
     sample = f"{passes} passes of the {workload} mesh per step (OpenMP oracle build)"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "node-updates/s",
-           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": workload, "n": mesh.n, "m": mesh.m},
