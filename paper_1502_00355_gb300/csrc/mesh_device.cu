@@ -282,11 +282,13 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
         for (int q = launched; q < end; ++q) {
             a.q = q;
             if (form_b) {
-                // Form B: the colour classes in turn, in place (Eq. 3)
+                // Form B: the colour classes in turn, in place (Eq. 3).  A
+                // mesh without free nodes has no class; one launch over an
+                // empty list still records the sweep, as Form A does.
                 a.in = a.out = M->xy[M->cur];
-                for (int c = 0; c < nseg; ++c) {
-                    a.order = M->node_order + M->colour_off[c];
-                    a.norder = M->colour_off[c + 1] - M->colour_off[c];
+                for (int c = 0; c < std::max(nseg, 1); ++c) {
+                    a.order = M->node_order + (nseg > 0 ? M->colour_off[c] : 0);
+                    a.norder = nseg > 0 ? M->colour_off[c + 1] - M->colour_off[c] : 0;
                     SLS_CUDA_TRY(launch_pass(M, a), "pass kernel");
                     ++kernels;
                 }

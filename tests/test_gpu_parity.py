@@ -277,3 +277,52 @@ def test_l2_window_same_results(sls):
         _check(got, ref, f"l2 window n={mesh.n}")
         got, ref = _run_both(sls, mesh, iters, l2_window=True, layout="soa", copy_back=True)
         _check(got, ref, f"l2 window soa/copy-back n={mesh.n}")
+
+
+def _degenerate_mesh():
+    """A jittered grid with free nodes moved exactly onto a neighbour
+    (zero-length edges; triangles whose three vertices coincide have edge sum
+    0 and alpha 0), onto the midpoint of the opposite edge (zero or
+    rounding-level area), plus the inverted triangles this leaves."""
+    mesh = meshgen.jittered_grid(40, 33, 0.3, 77, numbering="morton")
+    xy = mesh.xy.copy()
+    free = mesh.boundary == 0
+    rng = np.random.default_rng(5)
+    for k, t in enumerate(rng.choice(mesh.m, 60, replace=False)):
+        a, b, c = mesh.tri[t]
+        if not free[a]:
+            continue
+        if k % 3 == 0:
+            xy[a] = xy[b]
+        elif k % 3 == 1:
+            xy[a] = 0.5 * (xy[b] + xy[c])
+        else:
+            xy[a] = xy[b]
+            if free[c]:
+                xy[c] = xy[b]
+    mesh.xy = xy
+    return mesh
+
+
+@pytest.mark.parametrize("variant", [{"kernel": "fp64"}, {"kernel": "filtered"}, {"form": "B"},
+                                     {"precision": 32}, {"precision": 32, "form": "B"}])
+def test_degenerate_triangles_and_no_free_node(sls, variant):
+    form, precision = variant.get("form", "A"), variant.get("precision", 64)
+    deg = _degenerate_mesh()
+    P = deg.xy[deg.tri]
+    e = [P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 2] - P[:, 1]]
+    assert (sum((v * v).sum(1) for v in e) == 0.0).any()  # some triangle collapsed to a point
+    # a single triangle: every node is on the boundary, nothing may move, and
+    # every pass still counts (the tolerance stops after the first)
+    one = meshgen.Mesh(xy=np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), tri=np.array([[0, 1, 2]], np.int32),
+                       boundary=np.ones(3, np.uint8))
+    for mesh, bnd, what in [(deg, deg.boundary, "degenerate"), (one, None, "single triangle")]:
+        for strict in (False, True):
+            for tol in (0.0, 1e-3):
+                om = oracle.OracleMesh(mesh.xy, mesh.tri, bnd)
+                ref = om.smooth(mesh.xy, 8, tol=tol, strict=strict, form=form, precision=precision)
+                with sls.Mesh(mesh.xy, mesh.tri, bnd, strict=strict, record_accept=True, **variant) as g:
+                    info = g.smooth(8, tol)
+                    got = (g.coords(), info, g.accept_mask())
+                _check(got, ref, f"{what} {variant} strict={strict} tol={tol}")
+    assert ref[1]["iterations"] == 1 and ref[1]["converged"] == 1
