@@ -4,8 +4,10 @@
 // vertices (the other two vertices of each incident triangle) and its
 // incident triangles; the paper runs this on a single GPU thread because of
 // the write dependencies.  Here it is a two-phase host build: a counting sort
-// of the 3m (vertex, triangle) incidences, then an independent per-node pass
-// (run on all host cores) that de-duplicates the neighbours, counts how many
+// of the 3m incidences, each carrying the triangle's other two vertices and
+// the node's slot (so the per-node passes read their own records in order
+// instead of gathering triangles), then an independent per-node pass (run on
+// all host cores) that de-duplicates the neighbours, counts how many
 // triangles share each edge, and orders the neighbours for summation.
 //
 // Section 3.3.3 marks a vertex as internal when each of its neighbours has
@@ -83,11 +85,20 @@ sls_status build_host_mesh(const double *xy, int64_t n, const int32_t *tri, int6
     std::vector<int64_t> inc_ptr(n + 1, 0);
     for (int64_t k = 0; k < 3 * m; ++k) inc_ptr[tri[k] + 1]++;
     for (int64_t i = 0; i < n; ++i) inc_ptr[i + 1] += inc_ptr[i];
-    std::vector<int32_t> inc_tri(3 * m);
+    // each incidence keeps the other two vertices (stored order) and the slot
+    struct Inc {
+        int32_t a, b;
+        uint32_t slot;
+    };
+    std::vector<Inc> inc(3 * m);
     {
         std::vector<int64_t> cursor(inc_ptr.begin(), inc_ptr.end() - 1);
-        for (int64_t t = 0; t < m; ++t)
-            for (int c = 0; c < 3; ++c) inc_tri[cursor[tri[3 * t + c]]++] = (int32_t)t;
+        for (int64_t t = 0; t < m; ++t) {
+            const int32_t v0 = tri[3 * t], v1 = tri[3 * t + 1], v2 = tri[3 * t + 2];
+            inc[cursor[v0]++] = Inc{v1, v2, 0u};
+            inc[cursor[v1]++] = Inc{v0, v2, 1u};
+            inc[cursor[v2]++] = Inc{v0, v1, 2u};
+        }
     }
 
     // Phase 1: per node, the distinct neighbours in summation order, stored in
@@ -102,9 +113,8 @@ sls_status build_host_mesh(const double *xy, int64_t n, const int32_t *tri, int6
         for (int64_t i = r.lo; i < r.hi; ++i) {
             rec.clear();
             for (int64_t k = inc_ptr[i]; k < inc_ptr[i + 1]; ++k) {
-                const int32_t *v = tri + 3 * (int64_t)inc_tri[k];
-                for (int c = 0; c < 3; ++c)
-                    if (v[c] != i) rec.push_back(v[c]);
+                rec.push_back(inc[k].a);
+                rec.push_back(inc[k].b);
             }
             std::sort(rec.begin(), rec.end());
             int32_t *dst = nb.data() + 2 * inc_ptr[i];
@@ -169,18 +179,11 @@ sls_status build_host_mesh(const double *xy, int64_t n, const int32_t *tri, int6
             uint32_t *codes = w + 1 + d;
             uint32_t c = 0;
             for (int64_t k = inc_ptr[i]; k < inc_ptr[i + 1]; ++k) {
-                const int32_t *v = tri + 3 * (int64_t)inc_tri[k];
-                uint32_t slot = 0, pos[2], np = 0;
-                for (int s = 0; s < 3; ++s) {
-                    if (v[s] == i) {
-                        slot = (uint32_t)s;
-                        continue;
-                    }
-                    uint32_t p = 0;
-                    while (list[p] != v[s]) ++p;
-                    pos[np++] = p;
-                }
-                codes[c++] = tri_code(slot, pos[0], pos[1]);
+                const Inc &r = inc[k];
+                uint32_t pa = 0, pb = 0;
+                while (list[pa] != r.a) ++pa;
+                while (list[pb] != r.b) ++pb;
+                codes[c++] = tri_code(r.slot, pa, pb);
             }
         }
     };

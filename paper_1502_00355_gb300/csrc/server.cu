@@ -8,10 +8,11 @@
 // the device on a copy stream (overlapping the running round, and keeping
 // the host-to-device copies off the scheduler's thread); it runs rounds: one launch of the batched pass kernel over every
 // active job, each at its own pass index.  After each round it reads every
-// active job's statistics record, retires the jobs that reached their
-// iteration cap or tolerance, copies their coordinates back and frees their
-// memory; queued jobs take the freed budget at the next round.  Latency is
-// measured from sls_submit to the moment the result is on the host.
+// active job's statistics record and hands the jobs that reached their
+// iteration cap or tolerance to a retire thread, which copies their
+// coordinates back and frees their memory while the next round runs; queued
+// jobs take the freed budget as it returns.  Latency is measured from
+// sls_submit to the moment the result is on the host.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -70,18 +71,18 @@ struct sls_server {
     size_t budget = 0, used = 0;
     int32_t max_queue = 0;
     int device = 0;
-    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    cudaStream_t stream = nullptr, copy_stream = nullptr, retire_stream = nullptr;
     cudaMemPool_t pool = nullptr;
 
     std::mutex mu;
-    std::condition_variable cv_build, cv_sched, cv_done, cv_upload;
-    std::deque<std::shared_ptr<ServerJob>> to_build, queued, to_upload;
+    std::condition_variable cv_build, cv_sched, cv_done, cv_upload, cv_retire;
+    std::deque<std::shared_ptr<ServerJob>> to_build, queued, to_upload, to_retire;
     std::vector<std::shared_ptr<ServerJob>> uploading, active;
     std::unordered_map<uint64_t, std::shared_ptr<ServerJob>> jobs;
     uint64_t next_id = 1;
-    bool stop = false;
+    bool stop = false, retire_stop = false;
     std::vector<std::thread> builders;
-    std::thread sched, uploader;
+    std::thread sched, uploader, retirer;
 
     // job table and warp tasks of the active set
     JobDesc *d_jobs = nullptr, *h_jobs = nullptr;
@@ -143,13 +144,13 @@ void builder_loop(sls_server *S)
     }
 }
 
-void free_job_device(sls_server *S, ServerJob &J)
+void free_job_device(ServerJob &J, cudaStream_t s)
 {
-    cudaFreeAsync(J.d_xy[0], S->stream);
-    cudaFreeAsync(J.d_xy[1], S->stream);
-    cudaFreeAsync(J.d_off, S->stream);
-    cudaFreeAsync(J.d_adj, S->stream);
-    cudaFreeAsync(J.d_stats, S->stream);
+    cudaFreeAsync(J.d_xy[0], s);
+    cudaFreeAsync(J.d_xy[1], s);
+    cudaFreeAsync(J.d_off, s);
+    cudaFreeAsync(J.d_adj, s);
+    cudaFreeAsync(J.d_stats, s);
     if (J.uploaded) cudaEventDestroy(J.uploaded);
     J.d_xy[0] = J.d_xy[1] = nullptr;
     J.d_off = J.d_adj = nullptr;
@@ -263,6 +264,51 @@ bool rebuild_table(sls_server *S)
            cudaMemcpyAsync(S->d_tasks, S->h_tasks, sizeof(WarpTask) * t, cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
 }
 
+// Copies the results of finished jobs to the host and frees their device
+// memory, off the scheduler's thread: the next round starts at once.
+void retire_loop(sls_server *S)
+{
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<std::shared_ptr<ServerJob>> batch;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_retire.wait(lk, [S] { return S->retire_stop || !S->to_retire.empty(); });
+            if (S->to_retire.empty()) return;  // stopping, and nothing left to retire
+            batch.assign(S->to_retire.begin(), S->to_retire.end());
+            S->to_retire.clear();
+        }
+        bool ok = true;
+        for (auto &Jp : batch) {
+            ServerJob &J = *Jp;
+            J.result.resize(2 * (size_t)J.hm.n);
+            ok = ok && cudaMemcpyAsync(J.result.data(), J.d_xy[J.iterations & 1], sizeof(double) * J.result.size(),
+                                       cudaMemcpyDeviceToHost, S->retire_stream) == cudaSuccess;
+        }
+        ok = ok && cudaStreamSynchronize(S->retire_stream) == cudaSuccess;  // one wait for the batch
+        if (!ok) cudaGetLastError();
+        std::lock_guard<std::mutex> lk(S->mu);
+        const auto now = Clock::now();
+        for (auto &Jp : batch) {
+            ServerJob &J = *Jp;
+            free_job_device(J, S->retire_stream);
+            S->used -= J.footprint;
+            if (ok) {
+                J.t_done = now;
+                J.state = kDone;
+                S->latency_ms.push_back(std::chrono::duration<double, std::milli>(J.t_done - J.t_submit).count());
+                S->node_updates += (double)J.hm.n * (double)J.iterations;
+                S->completed += 1;
+            } else {
+                fail_job(S, J, SLS_ERR_CUDA, "copying the result to the host failed");
+            }
+            J.hm = HostMesh();
+        }
+        S->cv_done.notify_all();
+        S->cv_sched.notify_all();
+    }
+}
+
 void scheduler_loop(sls_server *S)
 {
     cudaSetDevice(S->device);
@@ -289,7 +335,9 @@ void scheduler_loop(sls_server *S)
             if (!S->to_upload.empty()) S->cv_upload.notify_one();
         }
         // jobs whose upload has finished join in this round (the copies
-        // overlap the previous round); with nothing running, wait for them
+        // overlap the previous round); with nothing running, wait for them.
+        // One uploader thread and one copy stream finish uploads in admission
+        // order, so the scan stops at the first one still pending or running.
         for (size_t k = 0; k < S->uploading.size();) {
             auto J = S->uploading[k];
             int ust;
@@ -297,7 +345,7 @@ void scheduler_loop(sls_server *S)
                 std::lock_guard<std::mutex> lk(S->mu);
                 ust = J->upload_state;
                 if (ust == 2) {
-                    free_job_device(S, *J);
+                    free_job_device(*J, S->stream);
                     S->used -= J->footprint;
                     fail_job(S, *J, SLS_ERR_OOM, "device allocation or upload failed");
                 }
@@ -306,22 +354,16 @@ void scheduler_loop(sls_server *S)
                 S->uploading.erase(S->uploading.begin() + k);
                 continue;
             }
-            if (ust == 0) {  // copies not enqueued yet
-                ++k;
-                continue;
-            }
+            if (ust == 0) break;  // copies not enqueued yet, nor those of later jobs
             if (S->active.empty()) cudaEventSynchronize(J->uploaded);
-            if (cudaEventQuery(J->uploaded) == cudaSuccess) {
-                J->xy.clear();
-                J->xy.shrink_to_fit();
-                J->base_round = S->round;
-                J->state = kActive;
-                S->active.push_back(J);
-                S->uploading.erase(S->uploading.begin() + k);
-                dirty = true;
-            } else {
-                ++k;
-            }
+            if (cudaEventQuery(J->uploaded) != cudaSuccess) break;
+            J->xy.clear();
+            J->xy.shrink_to_fit();
+            J->base_round = S->round;
+            J->state = kActive;
+            S->active.push_back(J);
+            S->uploading.erase(S->uploading.begin() + k);
+            dirty = true;
         }
         if (S->active.empty()) continue;
         const size_t na = S->active.size();
@@ -374,25 +416,14 @@ void scheduler_loop(sls_server *S)
                 keep.push_back(Jp);
                 continue;
             }
-            J.result.resize(2 * (size_t)J.hm.n);
-            cudaMemcpyAsync(J.result.data(), J.d_xy[J.iterations & 1], sizeof(double) * J.result.size(),
-                            cudaMemcpyDeviceToHost, S->stream);
             finished.push_back(Jp);
         }
-        if (!finished.empty()) cudaStreamSynchronize(S->stream);  // one wait for all of this round's results
-        for (auto &Jp : finished) {
-            ServerJob &J = *Jp;
+        if (!finished.empty()) {
+            // the round's wait above leaves their final coordinates in place;
+            // no later round touches them (they leave the task list)
             std::lock_guard<std::mutex> lk(S->mu);
-            free_job_device(S, J);
-            S->used -= J.footprint;
-            J.t_done = Clock::now();
-            J.state = kDone;
-            S->latency_ms.push_back(std::chrono::duration<double, std::milli>(J.t_done - J.t_submit).count());
-            S->node_updates += (double)J.hm.n * (double)J.iterations;
-            S->completed += 1;
-            J.hm = HostMesh();
-            S->cv_done.notify_all();
-            S->cv_sched.notify_all();
+            for (auto &Jp : finished) S->to_retire.push_back(Jp);
+            S->cv_retire.notify_one();
         }
         if (keep.size() != na) {
             S->active.swap(keep);
@@ -409,7 +440,7 @@ void scheduler_loop(sls_server *S)
     std::lock_guard<std::mutex> lk(S->mu);
     for (auto *list : {&S->active, &S->uploading}) {
         for (auto &J : *list) {
-            free_job_device(S, *J);
+            free_job_device(*J, S->stream);
             fail_job(S, *J, SLS_ERR_NOT_FOUND, "server destroyed before the job finished");
         }
         list->clear();
@@ -445,7 +476,8 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(SLS_ERR_CUDA, "cudaMemGetInfo failed");
     S->budget = hbm_budget ? hbm_budget : (size_t)(0.8 * (double)free_b);
     if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->retire_stream, cudaStreamNonBlocking) != cudaSuccess)
         return fail(SLS_ERR_CUDA, "cudaStreamCreate failed");
     if (cudaDeviceGetDefaultMemPool(&S->pool, S->device) == cudaSuccess) {
         uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
@@ -458,6 +490,7 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
     const int nb = std::max(2, (int)std::thread::hardware_concurrency());
     for (int b = 0; b < nb; ++b) raw->builders.emplace_back(builder_loop, raw);
     raw->uploader = std::thread(uploader_loop, raw);
+    raw->retirer = std::thread(retire_loop, raw);
     raw->sched = std::thread(scheduler_loop, raw);
     *out = raw;
     return SLS_OK;
@@ -472,13 +505,10 @@ sls_status sls_submit(sls_server *S, const double *xy, int64_t n, const int32_t 
     if (max_iter < 0 || std::isnan(tol_rel)) return fail(SLS_ERR_INVALID, "bad stop rule");
     // quick lower bound of the footprint: coordinates and offsets alone
     const size_t least = 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1);
+    if (least > S->budget) return fail(SLS_ERR_REJECTED, "job larger than the server's memory budget");
     auto J = std::make_shared<ServerJob>();
     J->t_submit = Clock::now();
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (least > S->budget) return fail(SLS_ERR_REJECTED, "job larger than the server's memory budget");
-    if (S->max_queue > 0 && (int64_t)(S->to_build.size() + S->queued.size()) >= S->max_queue)
-        return fail(SLS_ERR_BUSY, "server queue is full");
-    J->id = S->next_id++;
+    // copy the inputs before taking the server's lock, which every thread needs
     J->xy.assign(xy, xy + 2 * n);
     J->tri.assign(tri, tri + 3 * m);
     if (boundary) {
@@ -487,6 +517,10 @@ sls_status sls_submit(sls_server *S, const double *xy, int64_t n, const int32_t 
     }
     J->max_iter = max_iter;
     J->tol = tol_rel;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->max_queue > 0 && (int64_t)(S->to_build.size() + S->queued.size()) >= S->max_queue)
+        return fail(SLS_ERR_BUSY, "server queue is full");
+    J->id = S->next_id++;
     S->jobs[J->id] = J;
     S->to_build.push_back(J);
     S->cv_build.notify_one();
@@ -549,7 +583,15 @@ sls_status sls_server_destroy(sls_server *S)
     S->cv_upload.notify_all();
     for (auto &t : S->builders) t.join();
     if (S->sched.joinable()) S->sched.join();
+    {
+        // the scheduler has stopped handing over jobs: finish what it handed over
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->retire_stop = true;
+    }
+    S->cv_retire.notify_all();
+    if (S->retirer.joinable()) S->retirer.join();
     cudaStreamSynchronize(S->copy_stream);
+    cudaStreamSynchronize(S->retire_stream);
     cudaFreeHost(S->h_jobs);
     cudaFree(S->d_jobs);
     cudaFreeHost(S->h_tasks);
@@ -558,6 +600,7 @@ sls_status sls_server_destroy(sls_server *S)
     cudaFree(S->d_round);
     cudaStreamDestroy(S->stream);
     cudaStreamDestroy(S->copy_stream);
+    cudaStreamDestroy(S->retire_stream);
     delete S;
     return SLS_OK;
 }
