@@ -34,7 +34,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-enum JobState { kBuilding, kQueued, kUploading, kActive, kDone, kFailed };
+enum JobState { kBuilding, kQueued, kUploading, kActive, kRetiring, kDone, kFailed };
 
 struct ServerJob {
     uint64_t id = 0;
@@ -422,7 +422,10 @@ void scheduler_loop(sls_server *S)
             // the round's wait above leaves their final coordinates in place;
             // no later round touches them (they leave the task list)
             std::lock_guard<std::mutex> lk(S->mu);
-            for (auto &Jp : finished) S->to_retire.push_back(Jp);
+            for (auto &Jp : finished) {
+                Jp->state = kRetiring;
+                S->to_retire.push_back(Jp);
+            }
             S->cv_retire.notify_one();
         }
         if (keep.size() != na) {
@@ -449,7 +452,7 @@ void scheduler_loop(sls_server *S)
     S->queued.clear();
     if (!S->sched_error.empty())
         for (auto &kv : S->jobs)
-            if (kv.second->state != kDone && kv.second->state != kFailed)
+            if (kv.second->state != kDone && kv.second->state != kFailed && kv.second->state != kRetiring)
                 fail_job(S, *kv.second, SLS_ERR_CUDA, "scheduler stopped on a CUDA error");
     cudaStreamSynchronize(S->stream);
 }
