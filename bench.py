@@ -46,7 +46,10 @@ def _peaks():
 
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+    """Samples nvidia-smi SM clocks and throttle reasons.  Started before the
+    warm-up (its start-up takes driver time that must not fall in the timed
+    region); mark_start()/mark_end() bracket the timed region, and summary()
+    uses the samples taken inside it (all samples if none arrived there)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -55,8 +58,15 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
         self.reader = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
 
     def __enter__(self):
         try:
@@ -72,7 +82,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -86,7 +96,12 @@ class ClockSampler:
     def summary(self) -> dict:
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        lines = self.lines
+        if self.t0 is not None and self.t1 is not None:
+            # a sample arrives up to one 200 ms period after it was taken
+            inside = [(t, l) for t, l in lines if self.t0 <= t <= self.t1 + 0.2]
+            lines = inside or lines
+        for _, line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -443,20 +458,22 @@ def main():
         g.set_coords(xy0)
         return g.smooth(MAX_PASSES, TOL)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark_start()
         ev0.record(stream)
         for _ in range(args.steps):
             infos.append(step())
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     ms = ev0.elapsed_time(ev1)
     passes = sum(i["iterations"] for i in infos)
     # kernel-only view: per-pass time of the pass kernel, events around the passes alone
