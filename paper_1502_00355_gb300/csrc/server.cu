@@ -6,13 +6,14 @@
 // admits built jobs in arrival order while their device footprint fits the
 // memory budget and hands them to an uploader thread, which copies them to
 // the device on a copy stream (overlapping the running round, and keeping
-// the host-to-device copies off the scheduler's thread); it runs rounds: one launch of the batched pass kernel over every
-// active job, each at its own pass index.  After each round it reads every
-// active job's statistics record and hands the jobs that reached their
-// iteration cap or tolerance to a retire thread, which copies their
-// coordinates back and frees their memory while the next round runs; queued
-// jobs take the freed budget as it returns.  Latency is measured from
-// sls_submit to the moment the result is on the host.
+// the host-to-device copies off the scheduler's thread).  The scheduler runs
+// rounds: one launch of the batched pass kernel over every active job, each
+// at its own pass index.  After each round it reads every active job's
+// statistics record and hands the jobs that reached their iteration cap or
+// tolerance to a retire thread, which copies their coordinates back and
+// frees their memory while the next round runs; queued jobs take the freed
+// budget as it returns.  Latency is measured from sls_submit to the moment
+// the result is on the host.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
