@@ -279,3 +279,39 @@ def serve_requests(count: int = 10000, rate: float = 2000.0, lo: int = 1024, hi:
         cap = int(rng.integers(10, 201))
         out.append((float(t[r]), side, side, cap, BASE_SEED + 10000 + r))
     return out
+
+
+def edge_case_meshes() -> list[Mesh]:
+    """Small meshes at the edges of the method, for parity tests: a single
+    triangle (every node on the boundary; flags left to be derived), a grid
+    with free nodes moved exactly onto a neighbour or onto the midpoint of
+    the opposite edge (zero-length edges, triangles collapsed to a point or a
+    segment, inverted triangles), a free node in 40 triangles, and an ordinary
+    grid (twice)."""
+    one = Mesh(xy=np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), tri=np.array([[0, 1, 2]], np.int32),
+               boundary=None)
+    deg = jittered_grid(25, 19, 0.3, BASE_SEED + 20, numbering="morton")
+    xy = deg.xy.copy()
+    free = deg.boundary == 0
+    rng = np.random.default_rng(BASE_SEED + 21)
+    for k, t in enumerate(rng.choice(deg.m, 40, replace=False)):
+        a, b, c = deg.tri[t]
+        if not free[a]:
+            continue
+        if k % 3 == 0:
+            xy[a] = xy[b]
+        elif k % 3 == 1:
+            xy[a] = 0.5 * (xy[b] + xy[c])
+        else:
+            xy[a] = xy[b]
+            if free[c]:
+                xy[c] = xy[b]
+    deg.xy = xy
+    k = 40
+    ang = np.linspace(0.0, 2.0 * np.pi, k, endpoint=False)
+    ring = np.c_[np.cos(ang) * (1.0 + 0.3 * np.sin(5.0 * ang)), np.sin(ang)]
+    fan = Mesh(xy=np.vstack([ring, [[0.05, -0.02]]]),
+               tri=np.array([[k, j, (j + 1) % k] for j in range(k)], dtype=np.int32),
+               boundary=(np.arange(k + 1) < k).astype(np.uint8))
+    grid = jittered_grid(31, 17, 0.35, BASE_SEED + 22, numbering="random")
+    return [one, deg, fan, grid, grid]

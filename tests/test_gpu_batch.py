@@ -100,3 +100,23 @@ def test_batch_rejects_bad_input(sls):
     with pytest.raises(sls.SlsError) as e:  # the kernel is built for blocks of at most 128
         sls.Batch([h], [3], block_size=256)
     assert e.value.code == 1
+
+
+def test_batch_edge_meshes(sls):
+    # a single triangle (nothing moves, every pass counts), degenerate
+    # triangles, a node in 40 triangles (the exact path), a zero-pass mesh
+    meshes = meshgen.edge_case_meshes()
+    iters = [5, 9, 4, 0, 13]
+    tols = [0.0, 1e-4, 0.0, 0.0, 1e-6]
+    handles = [sls.Mesh(m.xy, m.tri, m.boundary) for m in meshes]
+    batch = sls.Batch(handles, iters, tols)
+    infos = batch.smooth()
+    for j, m in enumerate(meshes):
+        rxy, rinfo, _ = oracle.OracleMesh(m.xy, m.tri, m.boundary).smooth(m.xy, iters[j], tol=tols[j])
+        assert np.array_equal(batch.coords(j), rxy), j
+        for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
+            assert infos[j][key] == rinfo[key], (j, key)
+    assert infos[0]["iterations"] == 5 and infos[3]["iterations"] == 0
+    batch.close()
+    for h in handles:
+        h.close()

@@ -122,3 +122,20 @@ def test_server_destroyed_with_jobs_in_flight(sls):
     m = meshgen.jittered_grid(30, 30, 0.3, 3)
     with sls.Mesh(m.xy, m.tri, m.boundary) as g:
         assert g.smooth(3)["iterations"] == 3
+
+
+def test_served_edge_meshes(sls):
+    # a single triangle (nothing moves, every pass counts), degenerate
+    # triangles, a node in 40 triangles, a zero-pass job, in one mix
+    meshes = meshgen.edge_case_meshes()
+    caps = [5, 9, 4, 0, 13]
+    tols = [0.0, 1e-4, 0.0, 0.0, 1e-6]
+    srv = sls.Server()
+    ids = [srv.submit(m.xy, m.tri, m.boundary, max_iter=c, tol=t) for m, c, t in zip(meshes, caps, tols)]
+    for m, c, t, jid in zip(meshes, caps, tols, ids):
+        xy, info = srv.wait(jid, timeout=120.0)
+        rxy, rinfo, _ = oracle.OracleMesh(m.xy, m.tri, m.boundary).smooth(m.xy, c, tol=t)
+        assert np.array_equal(xy, rxy)
+        for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
+            assert info[key] == rinfo[key], key
+    srv.close()
