@@ -367,3 +367,46 @@ def test_histogram_against_independent_alpha():
     assert np.array_equal(counts, np.bincount(want, minlength=nb))
     assert qmin == pytest.approx(ref.min(), abs=1e-11)
     assert qmean == pytest.approx(ref.mean(), abs=1e-11)
+
+
+@pytest.mark.parametrize("strict", [False, True])
+def test_accept_rule_holds_over_sweeps_of_a_clustered_grid(strict):
+    # Sections 2.1 and 3.3.4 on the benchmark's kind of mesh (clustered,
+    # skewed, partly inverted triangles): in every pass each free node's
+    # decision is q_new >= q_old (q_new > q_old when strict), both minima
+    # taken on the coordinates before the pass (Eq. 2, Jacobi); the sweep
+    # applies exactly those decisions; spot checks recompute both minima in
+    # exact rational arithmetic at the FP64 centre
+    mesh = meshgen.jittered_grid(40, 36, 0.45, 31, numbering="morton", pull_fraction=0.15)
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary)
+    free = np.flatnonzero(mesh.boundary == 0)
+    tris_of = [[] for _ in range(mesh.n)]
+    for t, v in enumerate(mesh.tri):
+        for i in v:
+            tris_of[int(i)].append(t)
+    rng = np.random.default_rng(3)
+    xy = mesh.xy.copy()
+    inverted = 0
+    for q in range(6):
+        P = xy[mesh.tri]
+        inverted += int((((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])
+                          - (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0])) < 0).sum())
+        out, acc, d2, qo, qn, cand = om.update_nodes(xy, free, strict=strict)
+        assert np.array_equal(acc.astype(bool), qn > qo if strict else qn >= qo)
+        assert np.array_equal(out[acc == 1], cand[acc == 1])
+        assert np.array_equal(out[acc == 0], xy[free][acc == 0])
+        nxt, sacc, maxd2, nacc = om.sweep(xy, strict=strict)
+        assert np.array_equal(nxt[free], out) and np.array_equal(sacc[free], acc)
+        assert np.array_equal(nxt[mesh.boundary == 1], mesh.xy[mesh.boundary == 1])
+        assert nacc == int(acc.sum()) and maxd2 == d2.max()
+        for r in rng.choice(free.size, 20, replace=False):
+            i = int(free[r])
+            X = {int(v): (Fraction(float(xy[v, 0])), Fraction(float(xy[v, 1])))
+                 for t in tris_of[i] for v in mesh.tri[t]}
+            c = (Fraction(float(cand[r, 0])), Fraction(float(cand[r, 1])))
+            before = min(_exact_alpha_ratio([X[int(v)] for v in mesh.tri[t]]) for t in tris_of[i])
+            after = min(_exact_alpha_ratio([c if v == i else X[int(v)] for v in mesh.tri[t]]) for t in tris_of[i])
+            if abs(after - before) > Fraction(1, 10 ** 12):
+                assert bool(acc[r]) == (after > before), (q, i)
+        xy = nxt
+    assert inverted > 0  # the rule was exercised on inverted elements
