@@ -142,7 +142,7 @@ def test_host_build_matches_oracle(hb, case):
         mesh.xy = np.round(mesh.xy * 4) / 4
         bnd = "given"
     elif case == "fan30":
-        mesh, bnd = _fan(30), "given"        # 30 incident triangles: the large-fan path
+        mesh, bnd = _fan(30), "given"        # a free node in 30 triangles, mixed orientations
     else:
         mesh, bnd = _fan(40), None
     _check_against_oracle(hb, mesh, mesh.boundary if bnd == "given" else None)
@@ -158,3 +158,18 @@ def test_host_build_rejects_like_the_oracle(hb):
     bad = xy.copy()
     bad[3, 1] = np.inf
     assert _build(hb, bad, np.array([[0, 1, 2]]), None)[0] == 1        # non-finite coordinate
+
+
+def test_roofline_word_count_matches_the_build(hb):
+    # bench.py's algorithmic bytes use a closed-form count of the adjacency
+    # stream (one meta word per node, degree + triangle count per free node,
+    # degree = triangle count for a free node of a closed fan); it must equal
+    # the words the build writes on the benchmark's kinds of mesh
+    import bench
+    meshes = [meshgen.small_grid(), meshgen.large_grid(96, 80),
+              meshgen.batch_mesh(meshgen.batch_specs(4)[1]), meshgen.delaunay_random(2000, 5)]
+    for mesh in meshes:
+        st, node_off, adj, fixed, n_free, _ = _build(hb, mesh.xy, mesh.tri, mesh.boundary)
+        assert st == 0
+        assert len(adj) == bench.adjacency_words(mesh)
+        assert n_free == int((mesh.boundary == 0).sum())
