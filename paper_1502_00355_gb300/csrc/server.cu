@@ -345,8 +345,8 @@ void scheduler_loop(sls_server *S)
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 ust = J->upload_state;
-                if (ust == 2) {
-                    free_job_device(*J, S->stream);
+                if (ust == 2) {  // freed behind whatever of its copies was enqueued
+                    free_job_device(*J, S->copy_stream);
                     S->used -= J->footprint;
                     fail_job(S, *J, SLS_ERR_OOM, "device allocation or upload failed");
                 }
@@ -443,8 +443,9 @@ void scheduler_loop(sls_server *S)
     if (S->uploader.joinable()) S->uploader.join();
     std::lock_guard<std::mutex> lk(S->mu);
     for (auto *list : {&S->active, &S->uploading}) {
+        // an uploading job's memory is freed behind its own copies
         for (auto &J : *list) {
-            free_job_device(*J, S->stream);
+            free_job_device(*J, list == &S->active ? S->stream : S->copy_stream);
             fail_job(S, *J, SLS_ERR_NOT_FOUND, "server destroyed before the job finished");
         }
         list->clear();
