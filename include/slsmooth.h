@@ -164,7 +164,10 @@ sls_status sls_get_coords(const sls_mesh *mesh, double *xy_out, int32_t dst_is_d
 /* Overwrites the current coordinates (2n float64, interleaved), read from host
  * memory (src_is_device = 0) or from device memory of the mesh's device
  * (src_is_device = 1).  Adjacency, the summation order and D stay those of
- * sls_mesh_create.  Host input is checked to be finite; device input is not. */
+ * sls_mesh_create.  Host input is checked to be finite; device input is not.
+ * Device input is read on the handle's stream, so work on another stream that
+ * writes it must be complete (or ordered before that stream) at the call; the
+ * call returns once the coordinates are in place. */
 sls_status sls_set_coords(sls_mesh *mesh, const double *xy, int32_t src_is_device);
 
 /* Copies the accept decisions of the last executed pass (n uint8, host;
