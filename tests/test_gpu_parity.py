@@ -222,6 +222,27 @@ def test_large_grid_sampled_passes(sls):
             assert np.array_equal(cur[mesh.boundary == 1], mesh.xy[mesh.boundary == 1])
 
 
+def test_large_grid_full_run_bit_exact(sls):
+    # The whole timed configuration: 4096x4096 vertices with clustered pulls,
+    # smoothed to the tolerance in the launch configuration the benchmark
+    # times (default kernel, AoS, ping-pong, no accept mask), every coordinate
+    # against the OpenMP oracle; a second run records the last pass's
+    # decisions
+    mesh = meshgen.large_grid()
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary, openmp=True)
+    rxy, rinfo, racc = om.smooth(mesh.xy, 200, tol=1e-9)
+    assert rinfo["iterations"] == 77 and rinfo["converged"] == 1
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary) as g:
+        info = g.smooth(200, 1e-9)
+        xy = g.coords()
+    _assert_same(xy, rxy, "4096x4096 to tolerance")
+    for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
+        assert info[key] == rinfo[key], key
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, record_accept=True) as g:
+        g.smooth(200, 1e-9)
+        assert np.array_equal(g.accept_mask(), racc)
+
+
 @pytest.mark.parametrize("transform", ["shift_negative", "tiny", "huge", "far_offset", "signed_zeros",
                                        "denormal_scale", "mixed_binades"])
 def test_screened_kernel_domain_edges(sls, transform):
