@@ -24,7 +24,11 @@
  *   R2  alpha = 2*sqrt(3) * cross / (|e1|^2 + |e2|^2 + |e3|^2) with the signed
  *       cross product of the triangle in its stored vertex order, evaluated
  *       with one fixed expression tree (see orc_alpha); 0 when the edge sum
- *       is not positive;
+ *       is not positive.  Parity unpinned against the paper for this one
+ *       definition: the paper names Lee and Lo's measure but prints neither
+ *       its formula nor a value, so alpha is pinned only to textbook values
+ *       (equilateral 1, right isosceles sqrt(3)/2, degenerate 0, Heron's
+ *       formula);
  *   R3  accept iff q_new >= q_old ("does not get worse"); strict mode uses
  *       q_new > q_old, the paper's "is increased";
  *   R4  stop after max_iter passes, or earlier when tol > 0 and the largest
