@@ -250,11 +250,11 @@ sls_status sls_server_destroy(sls_server *srv);
 
 /* ---- smoothing without allocation ---------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
- * cannot allocate device memory when they smooth: code that runs while a
- * stream is being captured into a CUDA graph (cudaMalloc is not allowed in
- * the default capture mode), latency-critical loops that must not pay the
- * device-wide synchronisation of cudaMalloc/cudaFree, and plug-ins whose host
- * application reserves all device memory for its own pool.
+ * cannot allocate device memory when they smooth: latency-critical loops that
+ * must not pay the device-wide synchronisation of cudaMalloc/cudaFree,
+ * plug-ins whose host application has reserved all device memory for its own
+ * pool (a framework's caching allocator, for one), and services that fix
+ * their memory budget at start-up and must not fail for lack of memory later.
  *
  * Runs the same passes as sls_smooth on the mesh's adjacency, but on two
  * coordinate buffers the caller owns, and calls no cudaMalloc, cudaFree or

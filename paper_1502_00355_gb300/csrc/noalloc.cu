@@ -1,15 +1,14 @@
 // noalloc.cu -- sls_smooth_noalloc: smoothing passes that allocate nothing.
 //
 // Some callers cannot allocate device memory at the point where they smooth:
-// code running while a CUDA stream is being captured into a graph (where
-// cudaMalloc is not allowed in the default capture mode), latency-critical
-// loops that must not hit the implicit device synchronisation of
-// cudaMalloc/cudaFree, and plug-ins whose host application owns the whole
-// device memory budget through its own pool.  This entry point runs the same
-// pass kernels as sls_smooth, on two coordinate buffers the caller already
-// owns, and keeps the only scratch the kernels need -- one statistics record
-// per pass -- in a fixed array in device global memory that is part of the
-// library image.
+// latency-critical loops that must not hit the implicit device
+// synchronisation of cudaMalloc/cudaFree, plug-ins whose host application
+// owns the whole device memory budget through its own pool, and services
+// that fix their memory at start-up and must not fail for lack of it later.
+// This entry point runs the same pass kernels as sls_smooth, on two
+// coordinate buffers the caller already owns, and keeps the only scratch the
+// kernels need -- one statistics record per pass -- in a fixed array in
+// device global memory that is part of the library image.
 #include <cmath>
 #include <cstring>
 #include <mutex>

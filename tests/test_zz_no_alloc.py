@@ -1,7 +1,7 @@
 """sls_smooth_noalloc: the entry point for callers that cannot allocate device
-memory while they smooth (inside a stream capture, in a loop that must not
-synchronise the device through cudaMalloc/cudaFree, or under a host
-application that owns the whole memory budget).  It must give the same
+memory while they smooth (in a loop that must not synchronise the device
+through cudaMalloc/cudaFree, under a host application that owns the whole
+memory budget, or in a service whose memory is fixed at start-up).  It must give the same
 coordinates and statistics as sls_smooth, bit for bit, call after call,
 although every call reuses the same fixed scratch array.
 
