@@ -33,7 +33,45 @@ WORKLOAD = "grid4096x4096_jitter0.35_pull5pct_morton"
 MAX_PASSES = 200
 TOL = 1e-9
 METRIC = "node-updates/s"
-BATCH_DRAM_PER_ALG_BYTE = 1078639872 / 994046024
+CSRC = os.path.join(ROOT, "paper_1502_00355_gb300", "csrc")
+
+# Figures that only an ncu capture gives (DRAM bytes, FP64 instruction mix),
+# per kernel, from the capture named in `source` (its summary under
+# profiles/ gives the command).  Each entry holds the SHA-256 of the sources
+# the kernel was built from at capture time; once any of them changes the
+# figures no longer describe the kernel and the bench line reports null.
+PROFILE_FIGURES = {
+    "pass_screened": {
+        "files": ["pass_screened.cu", "node_exact.cuh", "div_small.cuh", "device.cuh"],
+        "sha256": "ca7c0f1638ab409ac1177ac17dc1de9da1207735b7d96b4c388c6504f0bdfa11",
+        "dram_bytes_per_node": 1446.0e6 / (4096 * 4096),
+        "fp64_warp_inst_per_32_nodes": 19.0 + 5.9 + 1.2,
+        "source": "profiles/pass_screened_grid2048.md (2048x2048 capture, per node)",
+    },
+    "batch_pass": {
+        "files": ["pass_screened.cu", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu"],
+        "sha256": "154332ffda9fea2a17e94257e66af6168c0af30aa0f38c0e5e64821104d63d1e",
+        "dram_per_alg_byte": 1078639872 / 994046024,
+        "source": "profiles/batch_pass_batch256.md (round 0 of a 256-mesh batch, scaled by algorithmic bytes)",
+    },
+}
+
+
+def sources_sha256(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def profile_figures(kernel: str):
+    """The ncu figures of `kernel` if they were taken on its current sources, else None."""
+    fig = PROFILE_FIGURES[kernel]
+    if fig["sha256"] is None or sources_sha256(fig["files"]) != fig["sha256"]:
+        return None
+    return fig
 
 
 def _peaks():
@@ -117,6 +155,48 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def edge_count(mesh) -> int:
+    """Distinct edges of the triangle mesh."""
+    tri = mesh.tri.astype(np.int64)
+    a = tri.ravel()
+    b = tri[:, [1, 2, 0]].ravel()
+    key = np.minimum(a, b) * mesh.n + np.maximum(a, b)
+    key.sort()
+    return 1 + int(np.count_nonzero(key[1:] != key[:-1])) if key.size else 0
+
+
+def survey_bytes_per_pass(mesh, n_free: int, coord_bytes: int = 16) -> int:
+    """Algorithmic bytes of one pass in the survey's accounting (each array read
+    once at ideal reuse): coordinates read for every node and written for every
+    free node, int32 CSR neighbour lists (offsets n+1, 2 per edge) and incident
+    triangle lists (offsets n+1, 3 per triangle), the triangles' int32 vertex
+    ids and one boundary flag per node:
+    16n + 16n_free + 8(n+1) + 4 nnz + 4*3m + 12m + n (coordinates 8 B in binary32)."""
+    n, m = mesh.n, mesh.m
+    nnz = 2 * edge_count(mesh)
+    return coord_bytes * n + coord_bytes * n_free + 8 * (n + 1) + 4 * nnz + 12 * m + 12 * m + n
+
+
+def fp64_pipe_peak(device="cuda") -> float:
+    """FP64 lane operations per second the GPU sustains: cuBLAS DGEMM (n^3
+    fused multiply-adds for an n x n product), best of three, CUDA events."""
+    import torch
+    n = 4096
+    a = torch.rand((n, n), dtype=torch.float64, device=device)
+    b = torch.rand((n, n), dtype=torch.float64, device=device)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del a, b
+    return n ** 3 / best
+
+
 def algorithmic_bytes_per_pass(n, n_free, adj_words, coord_bytes=16):
     """Bytes one pass must move at ideal reuse: every node's coordinates read
     once (16 B in FP64, 8 B in binary32), every free node's new coordinates
@@ -183,12 +263,12 @@ def init_ranks():
     return world, rank
 
 
-def cpu_oracle_rate(mesh, passes: int, precision: int = 64, form: str = "A"):
+def cpu_oracle_rate(mesh, passes: int, precision: int = 64, form: str = "A", openmp: bool = True):
     """Times `passes` passes of the oracle: Form A FP64 on all host cores
-    (OpenMP build); binary32 or Form B on one core (the oracle's sequential
-    loops)."""
+    (OpenMP build) when `openmp`; otherwise, and for binary32 or Form B, on
+    one core (the oracle's sequential loops)."""
     import oracle
-    omp = precision == 64 and form == "A"
+    omp = openmp and precision == 64 and form == "A"
     om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary, openmp=omp)
     t0 = time.perf_counter()
     if omp:
@@ -199,6 +279,20 @@ def cpu_oracle_rate(mesh, passes: int, precision: int = 64, form: str = "A"):
         om.smooth(mesh.xy, passes, form=form, precision=precision)
     dt = time.perf_counter() - t0
     return mesh.n * passes / dt, dt, (os.cpu_count() if omp else 1)
+
+
+def large_config(args, mesh, workload: str, world: int) -> dict:
+    """The single-mesh workload as both arms print it."""
+    return {"workload": workload, "n": mesh.n, "m": mesh.m,
+            "n_free": int(np.count_nonzero(mesh.boundary == 0)),
+            "max_passes": MAX_PASSES, "tol_rel": TOL, "kernel": args.kernel,
+            "layout": args.layout, "copy_back": bool(args.copy_back),
+            "form": "A (Jacobi)" if args.form == "A" else "B (coloured Gauss-Seidel, in place)",
+            "precision": args.precision,
+            "l2": "inputs larger than L2 (no flush)" if mesh.n >= 4 * 1024 * 1024
+            else "inputs fit L2 (no flush; see l2_hit_rate)",
+            "parallelism": "replicas" if world > 1 else "single",
+            "skip_unchanged": bool(args.skip_unchanged), "l2_window": bool(args.l2_window)}
 
 
 def run_reference(args, mesh, workload):
@@ -219,7 +313,7 @@ def run_reference(args, mesh, workload):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload, "n": mesh.n, "m": mesh.m},
+           "config": large_config(args, mesh, workload, args.gpus),
            "cpu_baseline": {"value": value, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "node-updates/s", "h2d_bytes_per_step": 0,
@@ -285,10 +379,10 @@ def run_batch(args):
     peak, peak_kind = _peaks()
     dev_mean = sum(dev_ms) / len(dev_ms)
     achieved = step_bytes / (dev_mean * 1e-3) / 1e9
-    # DRAM bytes per algorithmic byte of the batch-pass kernel: ncu
-    # dram__bytes_read.sum + dram__bytes_write.sum of round 0 of a 256-mesh
-    # batch (1,078,639,872 B against 994,046,024 algorithmic), scaled to the step
-    traffic = BATCH_DRAM_PER_ALG_BYTE * step_bytes
+    # DRAM bytes per algorithmic byte of the batch-pass kernel (ncu), scaled
+    # to the step; None once the kernel's sources changed since the capture
+    bfig = profile_figures("batch_pass")
+    traffic = bfig["dram_per_alg_byte"] * step_bytes if bfig else None
     out = {"metric": "node-updates/s (batched)", "value": batched, "unit": "node-updates/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -301,7 +395,7 @@ def run_batch(args):
            "gpu_launches": rounds * args.steps,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                        "traffic_source": "ncu round-0 capture of a 256-mesh batch, scaled by algorithmic bytes",
+                        "traffic_source": bfig["source"] if bfig else "no capture of the current kernel sources",
                         "bytes_per_step": step_bytes, "device_ms_per_step": dev_mean,
                         "timed": "CUDA events on the batch stream around each graph replay (job table upload, "
                                  "statistics clear, the round launches, statistics read-back)"}}
@@ -408,6 +502,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--config", default="large", choices=["large", "small", "medium"],
+                    help="single-mesh workload: large 4096^2 (the headline), small 64^2, medium 1024^2")
+    ap.add_argument("--numbering", default="morton", choices=["morton", "random"],
+                    help="node numbering of the medium mesh")
+    ap.add_argument("--layout", default="aos", choices=["aos", "soa"])
+    ap.add_argument("--copy-back", action="store_true",
+                    help="copy each pass back over the old coordinates (the paper's swap form)")
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--ref-passes", type=int, default=3)
@@ -428,9 +529,26 @@ def main():
     if args.workload == "serve":
         return run_serve(args)
 
+    return run_single(args)
+
+
+def single_workload(args):
+    """(mesh, workload name, max passes, tolerance) of the single-mesh workloads:
+    large (the headline, 4096x4096 with the clustered pull, to the tolerance),
+    small (64x64, 10 passes) and medium (1024x1024, 100 passes, Morton or
+    random numbering)."""
+    if args.config == "small":
+        return meshgen.small_grid(), "grid64x64_jitter0.3_morton_10passes", 10, 0.0
+    if args.config == "medium":
+        return (meshgen.medium_grid(args.numbering), f"grid1024x1024_jitter0.35_{args.numbering}_100passes",
+                100, 0.0)
     mesh = meshgen.large_grid(args.nx, args.ny)
     workload = WORKLOAD if (args.nx, args.ny) == (4096, 4096) else f"grid{args.nx}x{args.ny}_jitter0.35_pull5pct_morton"
+    return mesh, workload, MAX_PASSES, TOL
 
+
+def run_single(args):
+    mesh, workload, max_passes, tol = single_workload(args)
     if args.impl == "reference":
         run_reference(args, mesh, workload)
         return
@@ -448,15 +566,15 @@ def main():
     sls.lib()
 
     stream = torch.cuda.Stream()
-    variant = dict(kernel=args.kernel, precision=args.precision, form=args.form,
-                   skip_unchanged=args.skip_unchanged, l2_window=args.l2_window)
+    variant = dict(kernel=args.kernel, precision=args.precision, form=args.form, layout=args.layout,
+                   copy_back=args.copy_back, skip_unchanged=args.skip_unchanged, l2_window=args.l2_window)
     g = sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, stream=stream.cuda_stream, **variant)
     xy0 = torch.from_numpy(mesh.xy).to("cuda")
     torch.cuda.synchronize()
 
     def step():
         g.set_coords(xy0)
-        return g.smooth(MAX_PASSES, TOL)
+        return g.smooth(max_passes, tol)
 
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
@@ -476,15 +594,18 @@ def main():
         clk.mark_end()
     ms = ev0.elapsed_time(ev1)
     passes = sum(i["iterations"] for i in infos)
-    # kernel-only view: per-pass time of the pass kernel, events around the passes alone
+    # kernel-only view: per-pass time, events around the passes alone (for the
+    # copy-back form this includes its copy kernel)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g.set_coords(xy0)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    info_k = g.smooth(MAX_PASSES, TOL)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    pass_ms = e0.elapsed_time(e1) / max(1, info_k["iterations"])
+    pass_ms = float("inf")
+    for _ in range(2):
+        g.set_coords(xy0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        info_k = g.smooth(max_passes, tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pass_ms = min(pass_ms, e0.elapsed_time(e1) / max(1, info_k["iterations"]))
 
     ms_max, total_updates = reduce_over_ranks(ms, float(mesh.n * passes), device="cuda")
     value = total_updates / (ms_max * 1e-3)
@@ -500,55 +621,66 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with sls.Mesh(xy_h, tri_h, bnd_h, **variant) as h:
-            inf = h.smooth(MAX_PASSES, TOL)
+            inf = h.smooth(max_passes, tol)
             h.coords(out=out_host)
         e2e_times.append(time.perf_counter() - t0)
         e2e_passes += inf["iterations"]
     e2e_value = mesh.n * e2e_passes * world / sum(e2e_times) if e2e_times else None
 
     peak, peak_kind = _peaks()
-    # DRAM bytes of one pass-kernel launch: ncu dram__bytes_read.sum +
-    # dram__bytes_write.sum of a 2048x2048 capture of this kernel (361.5 MB),
-    # scaled by the node count to the 4096x4096 mesh; None for other sizes
     headline = (args.kernel == "auto" and args.precision == 64 and args.form == "A" and not args.skip_unchanged
-                and not args.l2_window)
-    traffic = 1446.0e6 if (mesh.n == 4096 * 4096 and headline) else None
-    adj_words = adjacency_words(mesh)
-    bytes_pass = algorithmic_bytes_per_pass(mesh.n, g.n_free, adj_words, 16 if args.precision == 64 else 8)
+                and not args.l2_window and args.layout == "aos" and not args.copy_back)
+    coord_bytes = 16 if args.precision == 64 else 8
+    bytes_pass = survey_bytes_per_pass(mesh, g.n_free, coord_bytes)
+    bytes_ours = algorithmic_bytes_per_pass(mesh.n, g.n_free, adjacency_words(mesh), coord_bytes)
     achieved = bytes_pass / (pass_ms * 1e-3) / 1e9
+    fig = profile_figures("pass_screened") if headline else None
+    traffic = fig["dram_bytes_per_node"] * mesh.n if fig else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "traffic_source": fig["source"] if fig else "no capture of the current kernel sources",
+                "bytes_per_pass": bytes_pass, "bytes_source": "16n + 16n_free + 8(n+1) + 4nnz + 12m + 12m + n",
+                "bytes_per_pass_library_encoding": bytes_ours, "pass_ms": pass_ms}
+    if fig:
+        # the FP64 pipe: every warp instruction occupies it for all 32 lanes
+        fp64_peak = fp64_pipe_peak()
+        fp64_ops = fig["fp64_warp_inst_per_32_nodes"] * mesh.n
+        fp64_ach = fp64_ops / (pass_ms * 1e-3)
+        roofline["fp64"] = {"achieved": fp64_ach / 1e12, "peak": fp64_peak / 1e12, "unit": "T lane-op/s",
+                            "frac": fp64_ach / fp64_peak,
+                            "peak_source": "cuBLAS DGEMM 4096^3 (n^3 FMA), measured in this run",
+                            "inst_source": fig["source"]}
+        if roofline["fp64"]["frac"] > roofline["frac"]:
+            roofline["bound"] = "alu"
+            roofline["bound_unit"] = "FP64 pipe (see fp64); HBM figures above"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, cores = cpu_oracle_rate(mesh, args.cpu_passes, args.precision, args.form)
+        omp = args.config == "large"
+        cpu_passes = args.cpu_passes if args.config == "large" else max_passes
+        rate, dt, cores = cpu_oracle_rate(mesh, cpu_passes, args.precision, args.form, openmp=omp)
         cpu = {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_passes} Form-{args.form} passes ({'FP64' if args.precision == 64 else 'binary32'}) "
+               "sample": f"{cpu_passes} Form-{args.form} passes ({'FP64' if args.precision == 64 else 'binary32'}) "
                          f"of the same mesh from its initial coordinates ({dt:.1f} s, "
-                         f"{'OpenMP oracle build on all host cores' if cores > 1 else 'sequential oracle'})"}
+                         f"{'OpenMP oracle build on all host cores' if cores > 1 else 'sequential oracle, one core'})"}
 
     if rank == 0:
+        cfg = large_config(args, mesh, workload, world)
+        cfg["n_free"] = g.n_free
         out = {"metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == 64 else "f32",
                "data": "synthetic",
-               "config": {"workload": workload, "n": mesh.n, "m": mesh.m, "n_free": g.n_free,
-                          "max_passes": MAX_PASSES, "tol_rel": TOL,
-                          "passes_per_step": passes / args.steps, "kernel": args.kernel,
-                          "layout": "aos",
-                          "form": "A (Jacobi, ping-pong)" if args.form == "A" else "B (coloured Gauss-Seidel, in place)",
-                          "l2": "inputs larger than L2 (no flush)",
-                          "parallelism": "replicas" if world > 1 else "single",
-                          "skip_unchanged": bool(args.skip_unchanged), "l2_window": bool(args.l2_window),
-                          "nodes_skipped_frac": sum(i["nodes_skipped"] for i in infos)
-                          / (mesh.n * max(1, passes))},
+               "config": cfg,
+               "run": {"passes_per_step": passes / args.steps,
+                       "nodes_skipped_frac": sum(i["nodes_skipped"] for i in infos) / (mesh.n * max(1, passes)),
+                       "fp64_fallbacks_per_pass": sum(i["fp64_fallbacks"] for i in infos) / max(1, passes)},
                "e2e": {"value": e2e_value, "unit": "node-updates/s",
                        "h2d_bytes_per_step": int(mesh.xy.nbytes + mesh.tri.nbytes + mesh.boundary.nbytes),
                        "d2h_bytes_per_step": int(mesh.xy.nbytes)},
                "gpu_launches": sum(i["launches"] for i in infos),
-               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": traffic,
-                            "peak_kind": peak_kind, "bytes_per_pass": bytes_pass,
-                            "pass_ms": pass_ms} if not args.skip_unchanged else None,
+               "roofline": roofline if not args.skip_unchanged else None,
                "cpu_baseline": cpu,
                "clocks": clk.summary()}
         print(json.dumps(out), flush=True)

@@ -261,10 +261,15 @@ sls_status sls_server_destroy(sls_server *srv);
  * other allocating routine.  The only scratch the kernels need -- one
  * 32-byte statistics record per pass -- lives in a fixed array of
  * SLS_NOALLOC_MAX_PASSES records (128 KiB) in device global memory, part of
- * the library image: every GPU that loads the library holds it until the
- * process exits.
- *   mesh     a handle created with the AoS layout (layout = 0); its own
- *            coordinates, accept mask and statistics are not used or changed
+ * the library image.  CUDA loads a library's device code and data lazily;
+ * sls_mesh_create (which allocates anyway) loads this array on the mesh's
+ * device, so this call finds it in place and loads nothing itself.  Every GPU
+ * on which a mesh was created holds the array until the process exits.
+ *   mesh     a handle created with the AoS layout (layout = 0), Form A and
+ *            FP64; its own coordinates, accept mask and statistics are not
+ *            used or changed, and its copy_back, skip_unchanged, l2_window and
+ *            record_accept options are not applied (the results are the
+ *            same: those options never change them)
  *   xy_in    device, 2n float64 interleaved: the starting coordinates; also
  *            serves as the second buffer of the ping-pong, so its contents
  *            are unspecified on return
@@ -274,10 +279,11 @@ sls_status sls_server_destroy(sls_server *srv);
  *   stream   cudaStream_t, or NULL for the mesh's stream; the call returns
  *            after the work on it is done
  * Results are bit-identical to sls_smooth on the same coordinates.  The
- * first call on a device looks up the array's device address (with that
- * device current; the mesh's device must be current); make that first call
- * before any stream capture.  The array is cleared at the start of each
- * call and keeps the last call's records afterwards.  All calls on a device
+ * mesh's device must be current.  The array's device address is looked up
+ * by sls_mesh_create and again after the device's context changes (after
+ * cudaDeviceReset); the lookup neither loads nor allocates once the array is
+ * in place.  The array is cleared at the start of each call and keeps the
+ * last call's records afterwards.  All calls on a device
  * share it: calls whose work overlaps on the GPU (other threads, other
  * streams) race and must be serialised by the caller. */
 #define SLS_NOALLOC_MAX_PASSES 4096

@@ -1,6 +1,7 @@
 // api.cu -- the single-mesh C ABI of slsmooth (see include/slsmooth.h).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -23,6 +24,36 @@ sls_status cuda_fail(cudaError_t e, const char *what)
 {
     cudaGetLastError();  // clear a sticky launch error so the handle stays usable
     return fail(SLS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// The driver's cuCtxGetCurrent and cuCtxGetId, looked up through the runtime
+// so the library does not link the driver library itself (it must load on
+// machines without a GPU driver).
+unsigned long long current_context_id()
+{
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0ull;
+    void *ctx = nullptr;
+    unsigned long long id = 0ull;
+    if (get_current(&ctx) != 0 || !ctx) return 0ull;
+    if (get_id(ctx, &id) != 0) return 0ull;
+    return id;
 }
 
 int device_sm_count()

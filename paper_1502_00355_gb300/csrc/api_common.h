@@ -44,6 +44,14 @@ namespace sls {
 
 sls_status cuda_fail(cudaError_t e, const char *what);
 int device_sm_count();
+// Unique id of the calling thread's current CUDA context, 0 when there is
+// none.  Per-device set-up (constant memory, symbol addresses) is keyed on it,
+// so a context created after cudaDeviceReset is set up again.
+unsigned long long current_context_id();
+// Loads the allocation-free entry point's scratch array on the current
+// device (noalloc.cu); sls_mesh_create calls it, so sls_smooth_noalloc on a
+// mesh never loads code or data itself.
+sls_status noalloc_prepare();
 sls_options resolve_options(const sls_options *opt);
 sls_status check_options(const sls_options &o);
 

@@ -13,8 +13,10 @@ cudaError_t launch_pass_fp64(const PassArgs &a, int layout, int block, int grid,
 // Blocks per SM the FP64 pass kernel can keep resident at `block` threads.
 int pass_fp64_occupancy(int layout, int block);
 
-// One Jacobi pass, screened: integer-pipe sums, FP32 screening of the accept
-// test, FP64 only where the screen cannot decide (bit-identical results).
+// One Jacobi pass, screened: FP64 neighbour sums in the stored order, the
+// division by the degree as one FP64 multiplication plus an exact integer
+// correction, FP32 screening of the accept test, FP64 quality only where the
+// screen cannot decide (bit-identical results).
 cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int grid, cudaStream_t s);
 int pass_screened_occupancy(int layout, int block);
 

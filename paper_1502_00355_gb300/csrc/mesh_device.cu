@@ -74,6 +74,8 @@ static sls_status mesh_setup(sls_mesh *M, const sls_options &o)
             M->l2_persist = 0;
         }
     }
+    sls_status pst = noalloc_prepare();
+    if (pst != SLS_OK) return pst;
     M->grid = device_sm_count() * (M->f32        ? pass_f32_occupancy(o.layout, M->block)
                                    : M->screened ? pass_screened_occupancy(o.layout, M->block)
                                                  : pass_fp64_occupancy(o.layout, M->block));

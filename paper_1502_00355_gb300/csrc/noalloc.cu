@@ -26,27 +26,48 @@ constexpr int kNoAllocMaxPasses = SLS_NOALLOC_MAX_PASSES;
 __device__ __align__(256) PassStats g_noalloc_stats[kNoAllocMaxPasses];
 
 // Host code may not use g_noalloc_stats as an address: it is a host-side
-// stand-in.  The device address is looked up once per device, with that
-// device current, and cached here.
+// stand-in.  The device address is looked up with the device current and
+// cached per device together with the context it belongs to; a new context
+// on the device (after cudaDeviceReset) looks it up again.
 constexpr int kMaxDevices = 64;
-PassStats *g_stats_addr[kMaxDevices] = {};
+struct StatsAddr {
+    unsigned long long ctx = 0ull;
+    PassStats *ptr = nullptr;
+};
+StatsAddr g_stats_addr[kMaxDevices];
 std::mutex g_setup_mu;
 
-sls_status stats_address(int dev, PassStats **out)
+sls_status stats_address(PassStats **out)
 {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(SLS_ERR_INVALID, "device ordinal out of range");
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_stats_addr[dev]) {
+    StatsAddr &c = g_stats_addr[dev];
+    if (!c.ptr || ctx == 0ull || c.ctx != ctx) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stats);
+        e = cudaGetSymbolAddress(&p, g_noalloc_stats);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the pass statistics");
-        g_stats_addr[dev] = static_cast<PassStats *>(p);
+        c.ptr = static_cast<PassStats *>(p);
+        c.ctx = ctx;
     }
-    *out = g_stats_addr[dev];
+    *out = c.ptr;
     return SLS_OK;
 }
 
 }  // namespace
+
+// Called by sls_mesh_create, which allocates anyway: looking the array up
+// loads this file's device code and data on the device (CUDA loads modules
+// lazily), so a later sls_smooth_noalloc on the mesh finds it in place.
+sls_status noalloc_prepare()
+{
+    PassStats *p = nullptr;
+    return stats_address(&p);
+}
+
 }  // namespace sls
 
 using namespace sls;
@@ -67,7 +88,7 @@ extern "C" sls_status sls_smooth_noalloc(const sls_mesh *M, double *xy_in, doubl
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev != M->device) return fail(SLS_ERR_INVALID, "the mesh's device must be the current device");
     PassStats *stats = nullptr;
-    sls_status st = stats_address(dev, &stats);
+    sls_status st = stats_address(&stats);
     if (st != SLS_OK) return st;
     cudaStream_t s = stream ? (cudaStream_t)stream : M->stream;
     const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;

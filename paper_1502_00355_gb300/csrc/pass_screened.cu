@@ -35,6 +35,7 @@
 #include <cfloat>
 #include <mutex>
 
+#include "api_common.h"
 #include "div_small.cuh"
 #include "kernels.h"
 #include "node_exact.cuh"
@@ -580,10 +581,11 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
     }
 }
 
-// Constant memory and function attributes belong to a device: they are set
-// up once per device, with that device current.
+// Constant memory and function attributes belong to a context: they are set
+// up once per device and context, with that device current (a context made
+// after cudaDeviceReset is set up again).
 constexpr int kMaxDevices = 64;
-std::atomic<bool> g_consts_ready[kMaxDevices] = {};
+std::atomic<unsigned long long> g_consts_ctx[kMaxDevices] = {};
 std::mutex g_consts_mu;
 
 cudaError_t ensure_constants()
@@ -592,9 +594,11 @@ cudaError_t ensure_constants()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (g_consts_ready[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    const unsigned long long id = current_context_id();
+    const unsigned long long key = id ? id : ~0ull;  // ~0: the context is not known yet
+    if (g_consts_ctx[dev].load(std::memory_order_acquire) == key) return cudaSuccess;
     std::lock_guard<std::mutex> lock(g_consts_mu);
-    if (g_consts_ready[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    if (g_consts_ctx[dev].load(std::memory_order_relaxed) == key) return cudaSuccess;
     double r[kFastMax + 1];
     double dg[kFastMax + 1];
     r[0] = 0.0;
@@ -612,7 +616,7 @@ cudaError_t ensure_constants()
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
     }
-    g_consts_ready[dev].store(true, std::memory_order_release);
+    g_consts_ctx[dev].store(key, std::memory_order_release);
     return cudaSuccess;
 }
 

@@ -83,3 +83,61 @@ def test_noalloc_rejects_what_it_cannot_do(env):
         st = L.sls_smooth_noalloc(g.handle, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
                                   5, 0.0, None, C.byref(info))
         assert st == 1
+
+
+def _noalloc(L, sls, g, xy_in, xy_out, max_iter, tol, stream=None):
+    info = sls.Info()
+    st = L.sls_smooth_noalloc(g.handle, C.c_void_p(xy_in.data_ptr()), C.c_void_p(xy_out.data_ptr()),
+                              max_iter, tol, None if stream is None else C.c_void_p(stream), C.byref(info))
+    assert st == 0, L.sls_last_error()
+    return info.as_dict()
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(env):
+    """The reason the entry point exists: a caller whose memory budget is
+    fully spoken for can smooth without the library taking any of it.  The
+    device's free memory is the same before and after a call (the scratch
+    array was placed on the device when the mesh was created)."""
+    sls, torch = env
+    L = sls.lib()
+    mesh = meshgen.jittered_grid(128, 96, 0.35, 4242, numbering="morton")
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary) as g:
+        a = torch.from_numpy(mesh.xy.copy()).cuda()
+        b = torch.empty_like(a)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        _noalloc(L, sls, g, a, b, 25, 1e-9)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
+        a.copy_(torch.from_numpy(mesh.xy))
+        free2, _ = torch.cuda.mem_get_info()
+        _noalloc(L, sls, g, a, b, 25, 1e-9)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free2
+
+
+@pytest.mark.parametrize("options", [dict(skip_unchanged=True), dict(copy_back=True)])
+def test_noalloc_on_a_side_stream_at_the_pass_limit(env, options):
+    """A call on a caller's own (non-default) stream, at the largest pass count
+    with the tolerance on, on meshes created with options the entry point does
+    not apply: the results equal sls_smooth's, bit for bit, twice in a row."""
+    sls, torch = env
+    L = sls.lib()
+    mesh = meshgen.jittered_grid(40, 30, 0.3, 99, numbering="morton")
+    ref_xy, ref_info = None, None
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, **options) as r:
+        ref_info = r.smooth(4096, 1e-13)
+        ref_xy = r.coords()
+    side = torch.cuda.Stream()
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, **options) as g:
+        for _ in range(2):
+            with torch.cuda.stream(side):
+                a = torch.from_numpy(mesh.xy.copy()).to("cuda", non_blocking=False)
+                b = torch.empty_like(a)
+            side.synchronize()
+            info = _noalloc(L, sls, g, a, b, 4096, 1e-13, stream=side.cuda_stream)
+            got = b.cpu().numpy()
+            assert np.array_equal(got, ref_xy)
+            for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
+                assert info[key] == ref_info[key], key
