@@ -39,6 +39,7 @@
 #include "div_small.cuh"
 #include "kernels.h"
 #include "node_exact.cuh"
+#include "screen.cuh"
 
 namespace sls {
 
@@ -51,119 +52,7 @@ __constant__ double c_degree[kFastMax + 1]; // N as a double
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
-// Splits the double with bit pattern b into a float head (its sign, exponent
-// and top 24 significant bits) and a float tail (the next 23 bits), with
-// integer operations only; head + tail is within 2^-46 |x| of x.  Returns
-// false outside [2^-80, 2^127) in magnitude (zero is allowed) or for
-// subnormal, infinite or NaN values.
-__device__ __forceinline__ bool head_tail(unsigned long long b, float &hd, float &tl)
-{
-    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
-    const unsigned e = (hw >> 20) & 0x7ffu;
-    const bool zero = (hw & 0x7fffffffu) == 0u && lw == 0u;
-    const unsigned sign = hw & 0x80000000u;
-    const float h = __uint_as_float(sign | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
-    // tail bits 28..6 of the low word, value t * 2^(E - 46): exact in FP32
-    const float t = __uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)) - 8388608.0f;
-    const float l = __uint_as_float(__float_as_uint(t * __uint_as_float((e - 942u) << 23)) | sign);
-    hd = zero ? 0.0f : h;
-    tl = zero ? 0.0f : l;
-    return zero || (e - 943u <= 206u);  // [2^-80, 2^127) in magnitude, normal
-}
-
-// FP32 value of a double, truncated to 24 significant bits (relative error
-// below 2^-23), built with integer operations; zero outside the float range.
-__device__ __forceinline__ float trunc_float(double v)
-{
-    const unsigned long long b = dbits(v);
-    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
-    const unsigned e = (hw >> 20) & 0x7ffu;
-    const float f = __uint_as_float((hw & 0x80000000u) | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
-    return e - 897u <= 253u ? f : 0.0f;
-}
-
-// Screening constants (unit roundoff e = 2^-24).  A local coordinate of a
-// neighbour carries an error below 2e|X| + 2^-44 M (head/tail truncation; M
-// bounds the node's coordinate magnitude plus the ring's extent), which is
-// below 3e R wherever R >= 2^-20 M; the screen requires that.  The centre's
-// local coordinate is within 2e of its exact value (relative).  For a
-// triangle whose three vertices' local coordinates are bounded by R, with
-// g = R^2 / s (s the computed sum of squared edges), the FP32 alpha differs
-// from the exact alpha of the FP64 inputs by at most
-//   e * (13.2 |a| + (264.6 + 194 |a|) g) * (1 + 1.1 e (6.1 + 194 g)),
-// (edge errors 8 e R; cross 76.4 e R^2; edge sum 6.1 e s + 194 e R^2; FP32
-// constant, products and approximate reciprocal 7.1 e |a|), valid for
-// g <= kGMax, where the last factor is at most 1.0128.  The constants carry a
-// further factor 1.5.  Because g >= 1/24 (every squared edge is at most
-// 8 R^2), half of the resulting bound exceeds 8e-7: more than the FP64
-// evaluation's own error (< 2e-15 for |alpha| <= 1) plus the FP32 rounding of
-// a +- b and of the comparisons, so those need no separate term.
-constexpr float kEps = 5.9604645e-8f;
-constexpr float kC1 = 1.5f * 1.0128f * 13.2f * kEps;
-constexpr float kC2 = 1.5f * 1.0128f * 264.6f * kEps;
-constexpr float kC3 = 1.5f * 1.0128f * 194.0f * kEps;
-constexpr float kGMax = 1000.0f;
-constexpr float kTwoSqrt3f = 3.46410161514f;
-constexpr float kLocalRange = 1048576.0f;  // 2^20: R * 2^20 >= M keeps the head/tail error below e R
-
-// FP32 alpha of the triangle (X, A, B) for the screen (sk: orientation sign
-// times 2 sqrt(3); ba2 = |B - A|^2); sv receives the edge sum.  The second
-// candidate loop calls it again and gets the same bits.
-__device__ __forceinline__ float screen_alpha(float2 X, float2 A, float2 B, float ba2, float sk, float &sv)
-{
-    const float e1x = A.x - X.x, e1y = A.y - X.y, e2x = B.x - X.x, e2y = B.y - X.y;
-    const float cr = fmaf(e1x, e2y, -(e1y * e2x));
-    sv = fmaf(e1x, e1x, fmaf(e1y, e1y, fmaf(e2x, e2x, fmaf(e2y, e2y, ba2))));
-    return sk * cr * __fdividef(1.0f, sv);
-}
-
-// Second screen, for a node whose two minima are attained by the same single
-// triangle (X, A, B) (X = 0 before the move, X = C after it; sgn gives the
-// stored orientation).  Then q_new - q_old (FP64) differs from the exact
-// alpha(C) - alpha(0) by at most 2 * kE64, and that exact difference is
-//   sgn * K * N / (s_new * s_old),  N = dcr * s_old - cr_old * ds,
-// with dcr = C x (A - B) and ds = 2|C|^2 - 2 C.(A + B) computed directly from
-// the move (no cancellation between two nearly equal qualities).  Error
-// budget (e = 2^-24; A, B within 3 e R, C within 2 e |C|; R >= every local
-// coordinate of the triangle and the centre, r >= |C| components): dcr
-// 32 e r R, ds 100 e r R, cr_old 16 e R^2, s_old 170 e R^2, s_new 280 e R^2,
-// and the roundings of N.  kE64 bounds |FP64 alpha - exact alpha| (about 14.2
-// units of 2^-53 for |alpha| <= 1, second-order terms included with margin).
-// Returns +1 when q_new > q_old certainly, -1 when q_new < q_old certainly,
-// 0 otherwise.
-constexpr float kE64 = 4e-15f;
-
-__device__ __forceinline__ int diff_screen(float2 A, float2 B, float Cx, float Cy, float sgn, float M2)
-{
-    const float R = fmaxf(fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y))),
-                          fmaxf(fabsf(Cx), fabsf(Cy)));
-    const float r = fmaxf(fabsf(Cx), fabsf(Cy));
-    if (!(R >= 1e-6f && R <= 1e7f)) return 0;  // keep every product a normal float
-    if (!(R * R * (kLocalRange * kLocalRange) >= M2)) return 0;
-    const float bax = B.x - A.x, bay = B.y - A.y;
-    const float ba2 = fmaf(bax, bax, bay * bay);
-    const float cro = fmaf(A.x, B.y, -(A.y * B.x));
-    const float so = fmaf(A.x, A.x, fmaf(A.y, A.y, fmaf(B.x, B.x, fmaf(B.y, B.y, ba2))));
-    const float ax = A.x - Cx, ay = A.y - Cy, bx = B.x - Cx, by = B.y - Cy;
-    const float sn = fmaf(ax, ax, fmaf(ay, ay, fmaf(bx, bx, fmaf(by, by, ba2))));
-    const float dabx = A.x - B.x, daby = A.y - B.y;
-    const float dcr = fmaf(Cx, daby, -(Cy * dabx));
-    const float sabx = A.x + B.x, saby = A.y + B.y;
-    const float t = fmaf(Cx, sabx, Cy * saby);
-    const float c2 = fmaf(Cx, Cx, Cy * Cy);
-    const float ds = 2.0f * (c2 - t);
-    const float N = fmaf(dcr, so, -(cro * ds));
-    const float rR = r * R, R2 = R * R;
-    const float e_dcr = 32.0f * kEps * rR, e_ds = 100.0f * kEps * rR;
-    const float e_cro = 16.0f * kEps * R2, e_so = 170.0f * kEps * R2, e_sn = 280.0f * kEps * R2;
-    if (!(so > e_so && sn > e_sn)) return 0;  // degenerate: no information
-    const float adcr = fabsf(dcr), ads = fabsf(ds), acro = fabsf(cro);
-    const float eN = e_dcr * so + (adcr + e_dcr) * e_so + e_cro * ads + (acro + e_cro) * e_ds +
-                     kEps * (adcr * so + 2.0f * acro * ads);
-    const float need = (2.02f * kE64 / kTwoSqrt3f) * (sn + e_sn) * (so + e_so);
-    if (!(fabsf(N) - 2.0f * eN > need)) return 0;
-    return ((N > 0.0f) == (sgn > 0.0f)) ? 1 : -1;
-}
+using namespace scr;
 
 // Screens free or fixed node i of one mesh (Eq. 2 and the accept test of
 // Section 3.3.4).  Decided nodes are written and counted here; returns true
@@ -217,9 +106,10 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     unsigned long long sxb = v0.x, syb = v0.y;
     float rn = 0.0f, rmin = FLT_MAX;
     {
-        float hx, lx, hy, ly;
-        ok = ok & head_tail(v0.x, hx, lx) & head_tail(v0.y, hy, ly);
-        const float2 L = make_float2((hx - phx) + (lx - plx), (hy - phy) + (ly - ply));
+        float2 L;
+        bool ok0;
+        local_offset(v0.x, v0.y, phx, plx, phy, ply, L.x, L.y, ok0);
+        ok = ok & ok0;
         if (act) loc[0] = L;
         const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
         rn = rl;
@@ -242,9 +132,9 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                 // x + (-0) == x for every x: lanes past their degree add -0
                 sxb = dbits(__dadd_rn(bitsd(sxb), bitsd(v[u].x)));
                 syb = dbits(__dadd_rn(bitsd(syb), bitsd(v[u].y)));
-                float hx, lx, hy, ly;
-                const bool okk = head_tail(v[u].x, hx, lx) & head_tail(v[u].y, hy, ly);
-                const float2 L = make_float2((hx - phx) + (lx - plx), (hy - phy) + (ly - ply));
+                float2 L;
+                bool okk;
+                local_offset(v[u].x, v[u].y, phx, plx, phy, ply, L.x, L.y, okk);
                 if (on) loc[k * nthr] = L;
                 const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
                 rn = on ? fmaxf(rn, rl) : rn;
@@ -272,11 +162,11 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     }
     if (!ok) return true;
     const double dx = __dsub_rn(bitsd(cbx), bitsd(pb.x)), dy = __dsub_rn(bitsd(cby), bitsd(pb.y));
-    const float Cx = trunc_float(dx), Cy = trunc_float(dy);
+    const float Cx = trunc_float(dbits(dx)), Cy = trunc_float(dbits(dy));
     const float rC = fmaxf(fabsf(Cx), fabsf(Cy));
     const float M = fmaxf(fabsf(phx), fabsf(phy)) * 1.0001f + fmaxf(rn, rC);
     const float M2 = M * M;
-    if (!((rmin >= 1e-14f) & (fmaxf(rn, rC) <= 1e15f) & (rmin * kLocalRange >= M))) return true;
+    if (!frame_ok(rmin, fmaxf(rn, rC), M)) return true;
     const float rN = fmaxf(rn, rC);
     float amin_o = FLT_MAX, a2_o = FLT_MAX, amax_o = 0.0f, smin_o = FLT_MAX;
     float amin_n = FLT_MAX, a2_n = FLT_MAX, amax_n = 0.0f, smin_n = FLT_MAX;
@@ -292,11 +182,10 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                 const float2 A = loc[code_first(c[u]) * nthr];
                 const float2 B = loc[code_second(c[u]) * nthr];
                 const float sk = code_slot(c[u]) == 1u ? -kTwoSqrt3f : kTwoSqrt3f;
-                const float bax = B.x - A.x, bay = B.y - A.y;
-                const float ba2 = fmaf(bax, bax, bay * bay);
+                const float ba2 = edge_ba2(A.x, A.y, B.x, B.y);
                 {
                     float sv;
-                    const float av = screen_alpha(make_float2(0.0f, 0.0f), A, B, ba2, sk, sv);
+                    const float av = screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, sk, sv);
                     if (av < amin_o) {
                         a2_o = amin_o;
                         amin_o = av;
@@ -309,7 +198,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                 }
                 {
                     float sv;
-                    const float av = screen_alpha(make_float2(Cx, Cy), A, B, ba2, sk, sv);
+                    const float av = screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, sk, sv);
                     if (av < amin_n) {
                         a2_n = amin_n;
                         amin_n = av;
@@ -325,13 +214,12 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     }
     // per side: q (FP64) lies in [amin - b, amin + b]; the minimum is attained
     // by triangle arg alone when every other alpha lies above amin + b + b
-    const float go = rn * rn * __fdividef(1.0f, smin_o), gn = rN * rN * __fdividef(1.0f, smin_n);
+    const float go = side_g(rn, smin_o), gn = side_g(rN, smin_n);
     int verdict = 0;
     bool single_o = false, single_n = false;
-    const bool bok =
-        (smin_o > 0.0f) & (smin_n > 0.0f) & (go <= kGMax) & (gn <= kGMax) & (amax_o <= 2.0f) & (amax_n <= 2.0f);
-    const float bo = fmaf(kC1, amax_o, fmaf(kC3, amax_o, kC2) * go);
-    const float bn = fmaf(kC1, amax_n, fmaf(kC3, amax_n, kC2) * gn);
+    const bool bok = bound_ok(smin_o, go, amax_o) & bound_ok(smin_n, gn, amax_n);
+    const float bo = side_bound(amax_o, go);
+    const float bn = side_bound(amax_n, gn);
     const float minU_o = amin_o + bo, minU_n = amin_n + bn;
     if (bok) {
         const float minL_o = amin_o - bo, minL_n = amin_n - bn;
@@ -341,8 +229,8 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     }
     if (verdict == 0 && single_o && single_n && arg_o == arg_n) {
         const uint32_t c = __ldg(nb + deg + arg_o);
-        verdict = diff_screen(loc[code_first(c) * nthr], loc[code_second(c) * nthr], Cx, Cy,
-                              code_slot(c) == 1u ? -1.0f : 1.0f, M2);
+        const float2 A = loc[code_first(c) * nthr], B = loc[code_second(c) * nthr];
+        verdict = diff_screen(A.x, A.y, B.x, B.y, Cx, Cy, code_slot(c) == 1u ? -1.0f : 1.0f, M2);
     }
     if (verdict == 0) {
         // candidates for the exact path: every triangle whose interval
@@ -357,12 +245,11 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                 const float2 A = loc[code_first(c) * nthr];
                 const float2 B = loc[code_second(c) * nthr];
                 const float sk = code_slot(c) == 1u ? -kTwoSqrt3f : kTwoSqrt3f;
-                const float bax = B.x - A.x, bay = B.y - A.y;
-                const float ba2 = fmaf(bax, bax, bay * bay);
+                const float ba2 = edge_ba2(A.x, A.y, B.x, B.y);
                 float sv;
-                if (!single_o && screen_alpha(make_float2(0.0f, 0.0f), A, B, ba2, sk, sv) - bo <= minU_o)
+                if (!single_o && screen_alpha(0.0f, 0.0f, A.x, A.y, B.x, B.y, ba2, sk, sv) - bo <= minU_o)
                     mo |= 1u << t;
-                if (!single_n && screen_alpha(make_float2(Cx, Cy), A, B, ba2, sk, sv) - bn <= minU_n)
+                if (!single_n && screen_alpha(Cx, Cy, A.x, A.y, B.x, B.y, ba2, sk, sv) - bn <= minU_n)
                     mn |= 1u << t;
             }
         }

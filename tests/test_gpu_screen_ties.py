@@ -1,0 +1,82 @@
+"""Rounding-level ties on the GPU: nodes placed a few ulps from the centre of
+their ring, so that the move changes the worst quality only at the level of
+FP64 rounding.  The FP32 screen cannot decide these; the screened kernel must
+hand them to its exact FP64 path (counted in fp64_fallbacks) and still agree
+with the oracle bit for bit, decision by decision.
+
+The planted nodes form an independent set (grid nodes whose both grid indices
+are multiples of 3), so their rings keep the coordinates the centres were
+computed from; the oracle computes each centre in the canonical summation
+order."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1502_00355_gb300 as mod
+    mod.build()
+    mod.lib()
+    return mod
+
+
+def _planted(nx, ny, seed, numbering):
+    mesh = meshgen.jittered_grid(nx, ny, 0.3, seed, numbering=numbering)
+    gi, gj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    gi, gj = gi.ravel(), gj.ravel()
+    pick = (gi % 3 == 0) & (gj % 3 == 0) & (gi > 0) & (gj > 0) & (gi < nx - 1) & (gj < ny - 1)
+    nodes = mesh.perm[np.flatnonzero(pick)]
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary)
+    _, _, _, _, _, centre = om.update_nodes(mesh.xy, nodes)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    xy = mesh.xy.copy()
+    for k, i in enumerate(nodes):
+        cx, cy = centre[k]
+        sx, sy = rng.integers(-4, 5, size=2)
+        for _ in range(abs(int(sx))):
+            cx = np.nextafter(cx, np.inf if sx > 0 else -np.inf)
+        for _ in range(abs(int(sy))):
+            cy = np.nextafter(cy, np.inf if sy > 0 else -np.inf)
+        xy[i] = (cx, cy)
+    return meshgen.Mesh(xy=xy, tri=mesh.tri, boundary=mesh.boundary, nx=nx, ny=ny, perm=mesh.perm), nodes
+
+
+@pytest.mark.parametrize("strict", [False, True])
+@pytest.mark.parametrize("numbering", ["morton", "random"])
+def test_rounding_level_ties_take_the_exact_path(sls, strict, numbering):
+    mesh, nodes = _planted(150, 120, 31337, numbering)
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary)
+    # pass 1 alone: the planted nodes sit a few ulps from their centres
+    ref_xy, ref_acc, ref_d2, ref_nacc = om.sweep(mesh.xy, strict=strict)
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, strict=strict, record_accept=True, kernel="filtered") as g:
+        info = g.smooth(1)
+        xy = g.coords()
+        acc = g.accept_mask()
+    assert np.array_equal(xy, ref_xy)
+    assert np.array_equal(acc, ref_acc)
+    assert info["accepted_last"] == ref_nacc and info["maxd2_last"] == ref_d2
+    # most planted nodes cannot be decided in FP32 (the rest are exact ties,
+    # which need no quality at all, or were decided by the difference screen)
+    assert info["fp64_fallbacks"] >= nodes.size // 2, (info["fp64_fallbacks"], nodes.size)
+    # both outcomes occur among the planted nodes
+    planted = ref_acc[nodes]
+    assert planted.min() == 0 and planted.max() == 1
+
+
+def test_ties_over_several_passes(sls):
+    mesh, _ = _planted(97, 61, 4711, "morton")
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary)
+    ref_xy, ref_info, ref_acc = om.smooth(mesh.xy, 6)
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, record_accept=True) as g:
+        info = g.smooth(6)
+        assert np.array_equal(g.coords(), ref_xy)
+        assert np.array_equal(g.accept_mask(), ref_acc)
+    assert info["iterations"] == ref_info["iterations"] and info["fp64_fallbacks"] > 0
