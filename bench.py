@@ -402,91 +402,204 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+class ResultPrint:
+    """A 64-bit fingerprint of a coordinate array: the wrapping sum of its
+    words times fixed odd random weights.  Two results with the same print
+    are taken as identical (an accidental collision has probability 2^-64)."""
+
+    def __init__(self, max_words: int, seed: int = 7):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.w = rng.integers(0, 2 ** 63, size=max_words, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+
+    def __call__(self, xy: np.ndarray) -> int:
+        v = np.ascontiguousarray(xy).view(np.uint64).ravel()
+        with np.errstate(over="ignore"):
+            return int(np.sum(v * self.w[:v.size], dtype=np.uint64))
+
+
+def serve_stream(args, world: int, rank: int):
+    """This rank's requests (arrival_s, nx, ny, cap, seed) of the served workload."""
+    return shard(meshgen.serve_requests(args.serve_requests * world, rate=args.serve_rate * world,
+                                        hi=args.serve_max_n), rank, world)
+
+
+class Prefetch:
+    """Makes the requests' meshes ahead of their turn on a few threads
+    (meshgen.fast_grid releases the GIL), at most `depth` ahead of the
+    consumer, so the stream never has to exist in memory at once."""
+
+    def __init__(self, reqs, threads: int, depth: int):
+        from concurrent.futures import ThreadPoolExecutor
+        self.reqs = reqs
+        self.ex = ThreadPoolExecutor(max_workers=threads)
+        self.depth = depth
+        self.fut = {}
+        self.next = 0
+
+    def _fill(self, k):
+        while self.next < len(self.reqs) and self.next < k + self.depth:
+            _, nx, ny, _, seed = self.reqs[self.next]
+            self.fut[self.next] = self.ex.submit(meshgen.fast_grid, nx, ny, 0.3, seed)
+            self.next += 1
+
+    def get(self, k):
+        self._fill(k)
+        m = self.fut.pop(k).result()
+        self._fill(k + 1)
+        return m
+
+    def close(self):
+        self.ex.shutdown(wait=True, cancel_futures=True)
+
+
 def run_serve(args):
     """Served form: a Poisson stream of smoothing requests through the
-    continuous-batching server, against one request at a time (FIFO)."""
+    continuous-batching server, against one request at a time (FIFO, one
+    sls_mesh_create + sls_smooth + sls_get_coords per request).  Latency runs
+    from a request's scheduled arrival to its result on the host, so it
+    includes any wait for the client to get the request in (the server's
+    queue holds at most --serve-queue jobs; a client that finds it full waits
+    and retries)."""
     import threading
     import torch
     import torch.distributed as dist
     import paper_1502_00355_gb300 as sls
     world, rank = init_ranks()
     sls.lib()
-    # weak scaling: every rank serves its own stream at the configured rate
-    reqs = shard(meshgen.serve_requests(args.serve_requests * world, rate=args.serve_rate * world,
-                                        hi=args.serve_max_n), rank, world)
-    meshes = [meshgen.jittered_grid(nx, ny, 0.3, seed, numbering="morton") for _, nx, ny, _, seed in reqs]
-    caps = [r[3] for r in reqs]
+    meshgen.build()
+    reqs = serve_stream(args, world, rank)
     arrivals = [r[0] for r in reqs]
+    caps = [r[3] for r in reqs]
+    sizes = [r[1] * r[2] for r in reqs]
+    fp = ResultPrint(2 * max(sizes))
+    # warm-up: a few requests through a server
     srv = sls.Server()
-    # warm-up: a few requests through the server
-    for m, cap in zip(meshes[:4], caps[:4]):
-        srv.wait(srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=TOL))
+    for k in range(min(4, len(reqs))):
+        m = meshgen.fast_grid(64, 64, 0.3, 1 + k)
+        srv.wait(srv.submit(m.xy, m.tri, m.boundary, max_iter=10, tol=TOL))
     srv.close()
-    srv = sls.Server()
-    results = [None] * len(reqs)
-    ids = [None] * len(reqs)
+
+    # ---- served: continuous batching ----
+    srv = sls.Server(max_queue=args.serve_queue)
+    pre = Prefetch(reqs, args.gen_threads, args.gen_depth)
+    done_t = [None] * len(reqs)
+    prints = [None] * len(reqs)
+    iters = [0] * len(reqs)
+    pending = {}  # job id -> (request index, output buffer)
+    lock = threading.Lock()
+    submitted = threading.Event()
+    busy_retries = [0]
     if world > 1:
         dist.barrier()
     t_start = time.perf_counter()
 
     def submitter():
-        for k, (m, cap) in enumerate(zip(meshes, caps)):
+        for k in range(len(reqs)):
+            m = pre.get(k)
             delay = arrivals[k] - (time.perf_counter() - t_start)
             if delay > 0:
                 time.sleep(delay)
-            ids[k] = srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=TOL)
+            while True:
+                try:
+                    jid = srv.submit(m.xy, m.tri, m.boundary, max_iter=caps[k], tol=TOL)
+                    break
+                except sls.SlsError as e:
+                    if e.code != 6:  # SLS_ERR_BUSY: the queue is full, try again shortly
+                        raise
+                    busy_retries[0] += 1
+                    time.sleep(0.0005)
+            with lock:
+                pending[jid] = (k, np.empty((sizes[k], 2), np.float64))
+        submitted.set()
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    th.join()
-    for k in range(len(reqs)):
-        results[k] = srv.wait(ids[k])
+    def poller():
+        while True:
+            with lock:
+                items = list(pending.items())
+            if not items and submitted.is_set():
+                with lock:
+                    if not pending:
+                        return
+            for jid, (k, buf) in items:
+                info = srv.try_wait(jid, buf)
+                if info is None:
+                    continue
+                done_t[k] = time.perf_counter() - t_start
+                prints[k] = fp(buf)
+                iters[k] = info["iterations"]
+                with lock:
+                    del pending[jid]
+            time.sleep(0.0005)
+
+    ths = [threading.Thread(target=submitter), threading.Thread(target=poller)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
     wall = time.perf_counter() - t_start
+    pre.close()
     st = srv.stats()
     srv.close()
-    updates = sum(m.n * r[1]["iterations"] for m, r in zip(meshes, results))
-    # FIFO baseline: one job on the GPU at a time, same kernels, same arrivals
-    lat = []
+    lat = [1e3 * (d - a) for d, a in zip(done_t, arrivals)]
+    updates = float(sum(n * it for n, it in zip(sizes, iters)))
+
+    # ---- FIFO: one request at a time, same arrivals, same kernels ----
+    pre = Prefetch(reqs, args.gen_threads, args.gen_depth)
     if world > 1:
         dist.barrier()
+    fifo_lat, busy, same = [], 0.0, True
     t_start = time.perf_counter()
-    busy = 0.0
-    same = True
-    for k, (m, cap) in enumerate(zip(meshes, caps)):
+    for k in range(len(reqs)):
+        m = pre.get(k)
         now = time.perf_counter() - t_start
         if now < arrivals[k]:
             time.sleep(arrivals[k] - now)
         t0 = time.perf_counter()
         with sls.Mesh(m.xy, m.tri, m.boundary) as g:
-            inf = g.smooth(cap, TOL)
+            inf = g.smooth(caps[k], TOL)
             xy = g.coords()
         busy += time.perf_counter() - t0
-        lat.append(1e3 * (time.perf_counter() - t_start - arrivals[k]))
-        same = same and np.array_equal(xy, results[k][0]) and inf["iterations"] == results[k][1]["iterations"]
+        fifo_lat.append(1e3 * (time.perf_counter() - t_start - arrivals[k]))
+        same = same and fp(xy) == prints[k] and inf["iterations"] == iters[k]
     fifo_wall = time.perf_counter() - t_start
+    pre.close()
+
     # over ranks: slowest wall times, summed work, worst percentiles
-    wall_ms, all_updates = reduce_over_ranks(1e3 * wall, float(updates), device="cuda")
+    wall_ms, all_updates = reduce_over_ranks(1e3 * wall, updates, device="cuda")
     fifo_ms, _ = reduce_over_ranks(1e3 * fifo_wall, 0.0, device="cuda")
-    p50, _ = reduce_over_ranks(st["p50_ms"], 0.0, device="cuda")
-    p99, _ = reduce_over_ranks(st["p99_ms"], 0.0, device="cuda")
-    f50, _ = reduce_over_ranks(float(np.percentile(lat, 50)), 0.0, device="cuda")
-    f99, _ = reduce_over_ranks(float(np.percentile(lat, 99)), 0.0, device="cuda")
+    busy_ms, _ = reduce_over_ranks(1e3 * busy, 0.0, device="cuda")
+    p50, _ = reduce_over_ranks(float(np.percentile(lat, 50)), 0.0, device="cuda")
+    p99, _ = reduce_over_ranks(float(np.percentile(lat, 99)), 0.0, device="cuda")
+    f50, _ = reduce_over_ranks(float(np.percentile(fifo_lat, 50)), 0.0, device="cuda")
+    f99, _ = reduce_over_ranks(float(np.percentile(fifo_lat, 99)), 0.0, device="cuda")
     same = reduce_flag(same, device="cuda")
     if rank != 0:
         return
     served = all_updates / (wall_ms * 1e-3)
     fifo = all_updates / (fifo_ms * 1e-3)
+    fifo_busy = all_updates / (busy_ms * 1e-3)
     out = {"metric": "node-updates/s (served)", "value": served, "unit": "node-updates/s", "n_gpus": world,
            "steps": 1, "warmup": 1, "ms_per_step": wall_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"serve{len(reqs)}_poisson{args.serve_rate:g}_logu1K-{args.serve_max_n}_cap10-200_tol1e-9",
+           "config": {"workload": f"serve{len(reqs) * world}_poisson{args.serve_rate:g}_logu1K-"
+                                  f"{'4M' if args.serve_max_n == 4 * 1024 * 1024 else args.serve_max_n}"
+                                  "_cap10-200_tol1e-9",
                       "requests_per_gpu": len(reqs), "requests": len(reqs) * world,
+                      "offered_req_per_s_per_gpu": args.serve_rate, "nodes_rank0": int(sum(sizes)),
+                      "mesh_generator": "meshgen.fast_grid (jittered grid, J = 0.3, Morton)",
+                      "server_queue_limit": args.serve_queue,
                       "parallelism": f"{world} ranks, one server each (no collective)" if world > 1 else "single"},
-           "served": {"p50_ms": p50, "p99_ms": p99, "node_updates_per_s_busy_rank0": st["node_updates_per_s"],
-                      "wall_s": wall_ms * 1e-3},
+           "served": {"p50_ms": p50, "p99_ms": p99, "wall_s": wall_ms * 1e-3,
+                      "req_per_s": len(reqs) * world / (wall_ms * 1e-3),
+                      "node_updates_per_s_busy_rank0": st["node_updates_per_s"],
+                      "server_p50_ms_from_submit": st["p50_ms"], "server_p99_ms_from_submit": st["p99_ms"],
+                      "busy_retries_rank0": busy_retries[0]},
            "fifo": {"p50_ms": f50, "p99_ms": f99, "node_updates_per_s": fifo, "wall_s": fifo_ms * 1e-3,
-                    "busy_s_rank0": busy},
-           "speedup_vs_fifo": served / fifo, "identical_results": bool(same)}
+                    "node_updates_per_s_busy": fifo_busy, "busy_s": busy_ms * 1e-3},
+           "speedup_vs_fifo": served / fifo,
+           "speedup_vs_fifo_busy": served / fifo_busy,
+           "identical_results": bool(same),
+           "latency": "scheduled arrival to result on the host"}
     print(json.dumps(out), flush=True)
 
 
@@ -494,9 +607,13 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="large", choices=["large", "batch", "serve"])
     ap.add_argument("--batch-meshes", type=int, default=2048)
-    ap.add_argument("--serve-requests", type=int, default=3000)
+    ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-max-n", type=int, default=262144)
+    ap.add_argument("--serve-max-n", type=int, default=4 * 1024 * 1024)
+    ap.add_argument("--serve-queue", type=int, default=64,
+                    help="jobs the server queues before a client must wait (host memory of queued inputs)")
+    ap.add_argument("--gen-threads", type=int, default=6)
+    ap.add_argument("--gen-depth", type=int, default=24)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

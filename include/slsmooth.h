@@ -219,19 +219,32 @@ sls_status sls_batch_reset(sls_batch *batch);
 sls_status sls_batch_destroy(sls_batch *batch);
 
 /* ---- served form: jobs arrive over time (continuous batching) -----------
- * A scheduler thread admits queued jobs while their device footprint fits
- * the memory budget, runs every admitted job's next pass in one launch, and
+ * A scheduler thread admits queued jobs in arrival order while a bound on
+ * their device footprint (coordinates, adjacency, statistics and the
+ * adjacency build's scratch, about 58n + 84m bytes) fits the memory budget;
+ * a job is also admitted when the server holds nothing else.  Builder
+ * threads, each with its own stream, upload admitted jobs and build their
+ * adjacency on the device (stream-ordered allocations from the device's
+ * default memory pool, so the running rounds are never synchronised; a mesh
+ * with a node in more than 32 triangles is built on the host).  The
+ * scheduler runs every built job's next pass in one launch per round and
  * retires each job at its own iteration cap or tolerance. */
 
 /* hbm_budget: bytes of device memory the server may hold for jobs (0 = 80%
- * of the free memory at creation).  max_queue: pending jobs allowed (0 =
- * unlimited). */
+ * of the free memory at creation).  max_queue: jobs submitted but not yet
+ * admitted that sls_submit accepts (0 = unlimited); beyond it sls_submit
+ * returns SLS_ERR_BUSY.  opt: FP64 Form A with the AoS layout only
+ * (SLS_ERR_INVALID otherwise).  The default memory pool of the device is set
+ * to keep freed memory (release threshold: unlimited). */
 sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_options *opt,
                              sls_server **out);
 
 /* Queues one smoothing job; inputs are copied before returning.  *job
- * receives its id.  Errors: SLS_ERR_INVALID / NONMANIFOLD (bad mesh),
- * SLS_ERR_REJECTED (larger than the whole budget), SLS_ERR_BUSY (queue full). */
+ * receives its id.  Errors: SLS_ERR_INVALID (bad sizes or stop rule),
+ * SLS_ERR_REJECTED (its coordinates and offsets alone exceed the budget),
+ * SLS_ERR_BUSY (queue full).  A mesh that fails validation (bad index,
+ * repeated vertex, non-finite coordinate, non-manifold edge) is reported by
+ * sls_wait with the same status sls_mesh_create would return. */
 sls_status sls_submit(sls_server *srv, const double *xy, int64_t n, const int32_t *tri, int64_t m,
                       const uint8_t *boundary, int32_t max_iter, double tol_rel, uint64_t *job);
 

@@ -20,13 +20,52 @@ fixed) serve for the large workloads:
 * node numbering natural (row-major), Morton (Z-order of the grid indices) or
   a seeded random permutation.  Triangles keep their vertex order under
   renumbering.
+
+``fast_grid`` makes grids of the same construction in C (``fastgrid.c``,
+built by ``build()``) with a counter-based generator, for request streams too
+large to generate with numpy ahead of time; its meshes are of the same kind
+as ``jittered_grid``'s, not the same meshes.
 """
 from __future__ import annotations
 
+import ctypes as _C
 import math
+import os
+import subprocess
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_FAST_SRC = os.path.join(_HERE, "fastgrid.c")
+_FAST_LIB = os.path.join(_HERE, "_build", "libfastgrid.so")
+_fast = None
+_fast_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compiles fastgrid.c into _build/libfastgrid.so (portable C, no
+    machine-specific flags)."""
+    os.makedirs(os.path.dirname(_FAST_LIB), exist_ok=True)
+    if force or not os.path.exists(_FAST_LIB) or os.path.getmtime(_FAST_LIB) < os.path.getmtime(_FAST_SRC):
+        tmp = _FAST_LIB + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _FAST_SRC, "-o", tmp], check=True)
+        os.replace(tmp, _FAST_LIB)
+    return _FAST_LIB
+
+
+def _fastlib():
+    global _fast
+    with _fast_lock:
+        if _fast is None:
+            build()
+            L = _C.CDLL(_FAST_LIB)
+            L.fastgrid.restype = _C.c_int
+            L.fastgrid.argtypes = [_C.c_int64, _C.c_int64, _C.c_double, _C.c_double, _C.c_uint64, _C.c_int,
+                                   _C.c_void_p, _C.c_void_p, _C.c_void_p]
+            _fast = L
+        return _fast
 
 BASE_SEED = 150200355
 
@@ -216,6 +255,29 @@ def delaunay_random(n: int, seed: int, *, numbering: str = "morton", perm_seed: 
     tri = perm[tri_nat].astype(np.int32)
     return Mesh(xy=xy, tri=tri, boundary=boundary, perm=perm,
                 meta=dict(kind="delaunay", n=n, seed=seed, numbering=numbering))
+
+
+def fast_grid(nx: int, ny: int, jitter: float, seed: int, *, numbering: str = "morton",
+              h: float | None = None) -> Mesh:
+    """Jittered grid made by fastgrid.c: the construction of ``jittered_grid``
+    (random diagonals, interior jitter U(-J h, J h), outer ring fixed, Morton
+    or natural numbering) with counter-based random numbers.  Releases the GIL
+    while it works, so threads can make several meshes at once."""
+    if numbering not in ("morton", "natural"):
+        raise ValueError(numbering)
+    if h is None:
+        h = 1.0 / (ny - 1)
+    n, m = nx * ny, 2 * (nx - 1) * (ny - 1)
+    xy = np.empty((n, 2), np.float64)
+    tri = np.empty((m, 3), np.int32)
+    boundary = np.empty(n, np.uint8)
+    rc = _fastlib().fastgrid(nx, ny, float(jitter), float(h), seed & 0xFFFFFFFFFFFFFFFF,
+                             1 if numbering == "morton" else 0, xy.ctypes.data, tri.ctypes.data,
+                             boundary.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"fastgrid failed for {nx}x{ny}")
+    return Mesh(xy=xy, tri=tri, boundary=boundary, nx=nx, ny=ny,
+                meta=dict(kind="fast_grid", nx=nx, ny=ny, h=h, jitter=jitter, seed=seed, numbering=numbering))
 
 
 def unpermute(xy: np.ndarray, mesh: Mesh) -> np.ndarray:

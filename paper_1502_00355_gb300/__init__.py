@@ -314,6 +314,17 @@ class Server:
         self._sizes.pop(job, None)
         return out, info.as_dict()
 
+    def try_wait(self, job: int, out: np.ndarray):
+        """Non-blocking sls_wait: None while the job runs; once it is done,
+        fills `out` (a contiguous (n, 2) float64 array) and returns its info."""
+        info = Info()
+        code = lib().sls_wait(self._h, C.c_uint64(job), 0.0, _p(out), C.byref(info))
+        if code == 5:  # SLS_ERR_TIMEOUT: not finished yet
+            return None
+        _check(code, "sls_wait")
+        self._sizes.pop(job, None)
+        return info.as_dict()
+
     def stats(self) -> dict:
         p50, p99, nups = C.c_double(), C.c_double(), C.c_double()
         done = C.c_int64()

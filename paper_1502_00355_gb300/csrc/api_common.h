@@ -61,7 +61,21 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
 // (host build as a fallback for very high-valence nodes).
 sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const int32_t *tri, int64_t m,
                                  const uint8_t *boundary, const sls_options &o);
-// Device adjacency build (mesh_build_gpu.cu); SLS_ERR_NOT_FOUND = use the host build.
+// Adjacency built on the device (mesh_build_gpu.cu).
+struct DeviceAdjacency {
+    uint32_t *node_off = nullptr;  // n+1
+    uint32_t *adj = nullptr;       // adj_words
+    uint64_t adj_words = 0;
+    int64_t n_free = 0;
+    double diag = 0.0;
+};
+// Validates the mesh and builds its adjacency from device copies of the
+// coordinates (AoS) and triangles; every allocation is stream-ordered on s
+// when `async` (the caller then frees the outputs with cudaFreeAsync).
+// SLS_ERR_NOT_FOUND = a node is in too many triangles: use the host build.
+sls_status build_device_adjacency(int64_t n, int64_t m, const double *d_xy, const int32_t *d_tri,
+                                  const uint8_t *h_boundary, bool async, cudaStream_t s, DeviceAdjacency &out);
+// Device adjacency build of a mesh handle; SLS_ERR_NOT_FOUND = use the host build.
 sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
                              cudaStream_t s);
 // The processing order of the free nodes, from the adjacency on the device

@@ -308,10 +308,31 @@ __global__ void scan_final_kernel(const unsigned *__restrict__ in, int64_t len,
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[len] = (uint32_t)offs[gridDim.x];
 }
 
+// A scratch buffer of the build.  With `async` it comes from the device's
+// stream-ordered pool on `s` and returns there (the served form builds jobs
+// while other streams run, and cudaFree would wait for the whole device);
+// otherwise plain cudaMalloc / cudaFree.
 struct DevBuf {
     void *p = nullptr;
-    ~DevBuf() { cudaFree(p); }
+    bool async = false;
+    cudaStream_t s = nullptr;
+    ~DevBuf()
+    {
+        if (!p) return;
+        if (async) cudaFreeAsync(p, s);
+        else cudaFree(p);
+    }
 };
+
+struct Alloc {
+    bool async;
+    cudaStream_t s;
+};
+
+cudaError_t raw_alloc(const Alloc &a, void **p, size_t bytes)
+{
+    return a.async ? cudaMallocAsync(p, bytes, a.s) : cudaMalloc(p, bytes);
+}
 
 #define GB_TRY(expr, what)                                  \
     do {                                                    \
@@ -320,9 +341,11 @@ struct DevBuf {
     } while (0)
 
 template <class T>
-sls_status dalloc(DevBuf &b, size_t count, T **out, const char *what)
+sls_status dalloc(DevBuf &b, size_t count, T **out, const char *what, const Alloc &a = Alloc{false, nullptr})
 {
-    cudaError_t e = cudaMalloc(&b.p, sizeof(T) * (count > 0 ? count : 1));
+    b.async = a.async;
+    b.s = a.s;
+    cudaError_t e = raw_alloc(a, &b.p, sizeof(T) * (count > 0 ? count : 1));
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return fail(SLS_ERR_OOM, std::string("device allocation failed: ") + what);
@@ -333,13 +356,14 @@ sls_status dalloc(DevBuf &b, size_t count, T **out, const char *what)
 }
 
 // scan of len uint32 values into len+1 offsets; total returned (uint64)
-sls_status scan_u32(const unsigned *in, int64_t len, uint32_t *out, unsigned long long *total, cudaStream_t s)
+sls_status scan_u32(const unsigned *in, int64_t len, uint32_t *out, unsigned long long *total, cudaStream_t s,
+                    bool async = false)
 {
     const int64_t per_block = (int64_t)kScanBlock * kScanItems;
     const int64_t nblocks = (len + per_block - 1) / per_block;
     DevBuf sb;
     unsigned long long *sums = nullptr;
-    sls_status st = dalloc(sb, (size_t)nblocks + 1, &sums, "scan");
+    sls_status st = dalloc(sb, (size_t)nblocks + 1, &sums, "scan", Alloc{async, s});
     if (st != SLS_OK) return st;
     if (nblocks > 0) {
         scan_sums_kernel<<<(unsigned)nblocks, kScanBlock, 0, s>>>(in, len, sums);
@@ -619,27 +643,29 @@ sls_status build_node_order(sls_mesh *M, cudaStream_t s)
 }
 
 // Builds the adjacency of a mesh whose coordinates (AoS) and triangles are
-// already on the device.  On success fills M->node_off, M->adj, n_free and
-// diag.  Returns SLS_ERR_NOT_FOUND (with nothing allocated) when a node has
-// more incident triangles than the device build handles, so the caller can
-// use the host build instead.
-sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
-                             cudaStream_t s)
+// already on the device.  On success out holds the node offsets and the
+// adjacency words (allocated as `async` says; the caller owns them), the
+// free-node count and D.  Returns SLS_ERR_NOT_FOUND (with nothing allocated)
+// when a node has more incident triangles than the device build handles, so
+// the caller can use the host build instead.  Synchronises only stream s.
+sls_status build_device_adjacency(int64_t n, int64_t m, const double *d_xy, const int32_t *d_tri,
+                                  const uint8_t *h_boundary, bool async, cudaStream_t s, DeviceAdjacency &out)
 {
-    const int64_t n = M->n, m = M->m;
+    out = DeviceAdjacency{};
     if (3 * m >= (int64_t(1) << 32)) return SLS_ERR_NOT_FOUND;
     const int sms = device_sm_count();
     const int grid = sms * 8, block = 256;
+    const Alloc al{async, s};
 
-    DevBuf b_flags, b_cnt, b_ptr, b_inc, b_nbtmp, b_words, b_fixed, b_deg, b_bnd, b_keys;
+    DevBuf b_flags, b_cnt, b_ptr, b_inc, b_nbtmp, b_words, b_fixed, b_deg, b_bnd, b_keys, b_off, b_adj;
     unsigned *flags = nullptr, *cnt = nullptr, *words = nullptr, *deg = nullptr;
     uint32_t *ptr = nullptr;
     int32_t *inc = nullptr, *nbtmp = nullptr;
     uint8_t *fixed = nullptr, *bnd = nullptr;
     unsigned long long *keys = nullptr;
     sls_status st;
-    if ((st = dalloc(b_flags, 2, &flags, "build flags")) != SLS_OK) return st;
-    if ((st = dalloc(b_keys, 8, &keys, "build keys")) != SLS_OK) return st;
+    if ((st = dalloc(b_flags, 2, &flags, "build flags", al)) != SLS_OK) return st;
+    if ((st = dalloc(b_keys, 8, &keys, "build keys", al)) != SLS_OK) return st;
     // keys: [0] first bad triangle, [1] first bad coordinate, [2..5] bbox, [6] free count
     GB_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), s), "build");
     GB_TRY(cudaMemsetAsync(keys, 0xff, 2 * sizeof(unsigned long long), s), "build");
@@ -660,24 +686,24 @@ sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_t
                                          ((hfirst[0] & 1ull) ? " repeats a vertex" : " has a vertex id out of range"));
     }
 
-    if ((st = dalloc(b_cnt, (size_t)n + 1, &cnt, "incidence counts")) != SLS_OK) return st;
-    if ((st = dalloc(b_ptr, (size_t)n + 1, &ptr, "incidence offsets")) != SLS_OK) return st;
-    if ((st = dalloc(b_inc, (size_t)(3 * m), &inc, "incidences")) != SLS_OK) return st;
+    if ((st = dalloc(b_cnt, (size_t)n + 1, &cnt, "incidence counts", al)) != SLS_OK) return st;
+    if ((st = dalloc(b_ptr, (size_t)n + 1, &ptr, "incidence offsets", al)) != SLS_OK) return st;
+    if ((st = dalloc(b_inc, (size_t)(3 * m), &inc, "incidences", al)) != SLS_OK) return st;
     GB_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (n + 1), s), "build");
     count_kernel<<<grid, block, 0, s>>>(d_tri, 3 * m, cnt);
     GB_TRY(cudaGetLastError(), "count");
     unsigned long long total = 0ull;
-    if ((st = scan_u32(cnt, n, ptr, &total, s)) != SLS_OK) return st;
+    if ((st = scan_u32(cnt, n, ptr, &total, s, async)) != SLS_OK) return st;
     GB_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (n + 1), s), "build");
     scatter_kernel<<<grid, block, 0, s>>>(d_tri, 3 * m, ptr, cnt, inc);
     GB_TRY(cudaGetLastError(), "scatter");
 
-    if ((st = dalloc(b_nbtmp, (size_t)(6 * m), &nbtmp, "neighbour scratch")) != SLS_OK) return st;
-    if ((st = dalloc(b_words, (size_t)n + 1, &words, "word counts")) != SLS_OK) return st;
-    if ((st = dalloc(b_fixed, (size_t)n, &fixed, "fixed flags")) != SLS_OK) return st;
-    if ((st = dalloc(b_deg, (size_t)n, &deg, "degrees")) != SLS_OK) return st;
+    if ((st = dalloc(b_nbtmp, (size_t)(6 * m), &nbtmp, "neighbour scratch", al)) != SLS_OK) return st;
+    if ((st = dalloc(b_words, (size_t)n + 1, &words, "word counts", al)) != SLS_OK) return st;
+    if ((st = dalloc(b_fixed, (size_t)n, &fixed, "fixed flags", al)) != SLS_OK) return st;
+    if ((st = dalloc(b_deg, (size_t)n, &deg, "degrees", al)) != SLS_OK) return st;
     if (h_boundary) {
-        if ((st = dalloc(b_bnd, (size_t)n, &bnd, "boundary flags")) != SLS_OK) return st;
+        if ((st = dalloc(b_bnd, (size_t)n, &bnd, "boundary flags", al)) != SLS_OK) return st;
         GB_TRY(cudaMemcpyAsync(bnd, h_boundary, (size_t)n, cudaMemcpyHostToDevice, s), "upload flags");
     }
     node_pass1_kernel<<<grid, block, 0, s>>>(n, reinterpret_cast<const double2 *>(d_xy), d_tri, ptr, inc, bnd,
@@ -688,15 +714,13 @@ sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_t
     if (hflags & kErrManifold) return fail(SLS_ERR_NONMANIFOLD, "an edge is shared by more than two triangles");
     if (hflags & kErrTooMany) return SLS_ERR_NOT_FOUND;
 
-    uint32_t *node_off = nullptr;
-    GB_TRY(cudaMalloc(&node_off, sizeof(uint32_t) * (n + 1)), "node offsets");
-    M->node_off = node_off;
+    uint32_t *node_off = nullptr, *adj = nullptr;
+    if ((st = dalloc(b_off, (size_t)n + 1, &node_off, "node offsets", al)) != SLS_OK) return st;
     unsigned long long wtotal = 0ull;
-    if ((st = scan_u32(words, n, node_off, &wtotal, s)) != SLS_OK) return st;
+    if ((st = scan_u32(words, n, node_off, &wtotal, s, async)) != SLS_OK) return st;
     if (wtotal >= (1ull << 32)) return fail(SLS_ERR_INVALID, "adjacency exceeds 2^32 words");
-    M->adj_words = wtotal;
-    GB_TRY(cudaMalloc(&M->adj, sizeof(uint32_t) * (wtotal > 0 ? wtotal : 1)), "adjacency");
-    node_pass2_kernel<<<grid, block, 0, s>>>(n, d_tri, ptr, inc, nbtmp, deg, fixed, node_off, M->adj);
+    if ((st = dalloc(b_adj, (size_t)wtotal, &adj, "adjacency", al)) != SLS_OK) return st;
+    node_pass2_kernel<<<grid, block, 0, s>>>(n, d_tri, ptr, inc, nbtmp, deg, fixed, node_off, adj);
     GB_TRY(cudaGetLastError(), "node pass 2");
 
     GB_TRY(cudaMemsetAsync(keys + 2, 0xff, 2 * sizeof(unsigned long long), s), "bbox");
@@ -713,8 +737,27 @@ sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_t
         return v;
     };
     const double xmin = unkey(hk[0]), ymin = unkey(hk[1]), xmax = unkey(hk[2]), ymax = unkey(hk[3]);
-    M->diag = bbox_diagonal(xmin, xmax, ymin, ymax);
-    M->n_free = (int64_t)hk[4];
+    out.diag = bbox_diagonal(xmin, xmax, ymin, ymax);
+    out.n_free = (int64_t)hk[4];
+    out.adj_words = wtotal;
+    out.node_off = node_off;
+    out.adj = adj;
+    b_off.p = nullptr;  // handed to the caller
+    b_adj.p = nullptr;
+    return SLS_OK;
+}
+
+sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
+                             cudaStream_t s)
+{
+    DeviceAdjacency da;
+    sls_status st = build_device_adjacency(M->n, M->m, d_xy, d_tri, h_boundary, false, s, da);
+    if (st != SLS_OK) return st;
+    M->node_off = da.node_off;
+    M->adj = da.adj;
+    M->adj_words = da.adj_words;
+    M->n_free = da.n_free;
+    M->diag = da.diag;
     return SLS_OK;
 }
 

@@ -1,12 +1,15 @@
 // server.cu -- the served form: smoothing jobs arriving over time, run with
 // continuous batching.
 //
-// sls_submit copies a job's inputs and hands them to builder threads, which
-// validate the mesh and build its adjacency on the host.  A scheduler thread
-// admits built jobs in arrival order while their device footprint fits the
-// memory budget and hands them to an uploader thread, which copies them to
-// the device on a copy stream (overlapping the running round, and keeping
-// the host-to-device copies off the scheduler's thread).  The scheduler runs
+// sls_submit copies a job's inputs and queues it.  A scheduler thread admits
+// queued jobs in arrival order while a bound on their device footprint
+// (coordinates, adjacency, statistics and the build's scratch) fits the
+// memory budget, and hands them to builder threads.  Each builder owns a
+// stream: it uploads the job's coordinates and triangles and builds the
+// adjacency on the device (validation, neighbour finding and constraints,
+// Sections 3.3.2 and 3.3.3), with stream-ordered allocations so that nothing
+// waits for the rounds running on the other streams; a mesh with a node in
+// more than 32 triangles is built on the host instead.  The scheduler runs
 // rounds: one launch of the batched pass kernel over every active job, each
 // at its own pass index.  After each round it reads every active job's
 // statistics record and hands the jobs that reached their iteration cap or
@@ -35,29 +38,33 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-enum JobState { kBuilding, kQueued, kUploading, kActive, kRetiring, kDone, kFailed };
+constexpr int kBuilders = 4;  // builder threads (and streams) per server
+
+enum JobState { kQueued, kBuilding, kActive, kRetiring, kDone, kFailed };
 
 struct ServerJob {
     uint64_t id = 0;
-    // inputs, released once uploaded
+    // inputs, released once the job is on the device
     std::vector<double> xy;
     std::vector<int32_t> tri;
     std::vector<uint8_t> boundary;
     bool has_boundary = false;
-    HostMesh hm;
+    int64_t n = 0, m = 0;
+    double diag = 0.0;
     int32_t max_iter = 0;
     double tol = 0.0;
-    size_t footprint = 0;
-    // device state
+    size_t reserved = 0;   // budget held: the bound at admission, the exact footprint once built
+    // device state (stream-ordered allocations)
     double *d_xy[2] = {nullptr, nullptr};
     uint32_t *d_off = nullptr, *d_adj = nullptr;
     PassStats *d_stats = nullptr;
+    cudaStream_t build_stream = nullptr;  // the builder stream the memory was allocated on
     cudaEvent_t uploaded = nullptr;
-    int upload_state = 0;  // 0 pending, 1 copies enqueued (event recorded), 2 failed
+    int upload_state = 0;  // 0 pending, 1 built (event recorded), 2 failed
     int base_round = 0;
     int iterations = 0;
     // result
-    JobState state = kBuilding;
+    JobState state = kQueued;
     sls_status status = SLS_OK;
     std::string error;
     std::vector<double> result;
@@ -72,18 +79,20 @@ struct sls_server {
     size_t budget = 0, used = 0;
     int32_t max_queue = 0;
     int device = 0;
-    cudaStream_t stream = nullptr, copy_stream = nullptr, retire_stream = nullptr;
+    cudaStream_t stream = nullptr, retire_stream = nullptr;
+    std::vector<cudaStream_t> build_streams;
     cudaMemPool_t pool = nullptr;
 
     std::mutex mu;
-    std::condition_variable cv_build, cv_sched, cv_done, cv_upload, cv_retire;
-    std::deque<std::shared_ptr<ServerJob>> to_build, queued, to_upload, to_retire;
+    std::condition_variable cv_build, cv_sched, cv_done, cv_retire;
+    std::deque<std::shared_ptr<ServerJob>> queued, to_build, to_retire;
     std::vector<std::shared_ptr<ServerJob>> uploading, active;
     std::unordered_map<uint64_t, std::shared_ptr<ServerJob>> jobs;
     uint64_t next_id = 1;
     bool stop = false, retire_stop = false;
+    int builders_live = 0;
     std::vector<std::thread> builders;
-    std::thread sched, uploader, retirer;
+    std::thread sched, retirer;
 
     // job table and warp tasks of the active set
     JobDesc *d_jobs = nullptr, *h_jobs = nullptr;
@@ -106,43 +115,30 @@ struct sls_server {
 
 namespace {
 
-size_t job_footprint(const HostMesh &hm, int32_t max_iter)
+// Device bytes a job holds once built: two coordinate arrays, node offsets,
+// adjacency words, one statistics record per pass.
+size_t built_footprint(int64_t n, uint64_t adj_words, int32_t max_iter)
 {
-    return 2 * sizeof(double) * 2 * (size_t)hm.n + sizeof(uint32_t) * (size_t)(hm.n + 1) +
-           sizeof(uint32_t) * hm.adj.size() + sizeof(PassStats) * (size_t)std::max(1, max_iter);
+    return 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1) + sizeof(uint32_t) * adj_words +
+           sizeof(PassStats) * (size_t)std::max(1, max_iter);
 }
 
-void builder_loop(sls_server *S)
+// A bound on what a job holds while it is built: the built footprint with
+// at most n + 9m adjacency words (a meta word per node; per corner of a
+// triangle at most two neighbours and one triangle code), plus the build's
+// scratch (triangles, incidences, neighbour candidates, counts and flags).
+size_t admission_bound(int64_t n, int64_t m, int32_t max_iter)
 {
-    for (;;) {
-        std::shared_ptr<ServerJob> J;
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_build.wait(lk, [S] { return S->stop || !S->to_build.empty(); });
-            if (S->to_build.empty()) return;
-            J = S->to_build.front();
-            S->to_build.pop_front();
-        }
-        const int64_t n = (int64_t)J->xy.size() / 2, m = (int64_t)J->tri.size() / 3;
-        sls_status st = build_host_mesh(J->xy.data(), n, J->tri.data(), m,
-                                        J->has_boundary ? J->boundary.data() : nullptr, J->hm, 1);
-        std::lock_guard<std::mutex> lk(S->mu);
-        J->tri.clear();
-        J->tri.shrink_to_fit();
-        J->boundary.clear();
-        if (st != SLS_OK) {
-            J->state = kFailed;
-            J->status = st;
-            J->error = sls_last_error();
-            J->t_done = Clock::now();
-            S->cv_done.notify_all();
-            continue;
-        }
-        J->footprint = job_footprint(J->hm, J->max_iter);
-        J->state = kQueued;
-        S->queued.push_back(J);
-        S->cv_sched.notify_all();
-    }
+    return built_footprint(n, (uint64_t)(n + 9 * m), max_iter) + 18 * (size_t)n + 48 * (size_t)m + 65536;
+}
+
+void fail_job(sls_server *S, ServerJob &J, sls_status st, const std::string &msg)
+{
+    J.state = kFailed;
+    J.status = st;
+    J.error = msg;
+    J.t_done = Clock::now();
+    S->cv_done.notify_all();
 }
 
 void free_job_device(ServerJob &J, cudaStream_t s)
@@ -159,48 +155,112 @@ void free_job_device(ServerJob &J, cudaStream_t s)
     J.uploaded = nullptr;
 }
 
-// Allocates (stream-ordered, from the server's pool) and uploads a job on
-// the copy stream; completion is tracked by J.uploaded.
-bool start_upload(sls_server *S, ServerJob &J)
+// Uploads job J on stream s and builds its adjacency there.  On success the
+// job's device state is complete once J.uploaded has fired; *footprint is
+// what it holds.  On failure everything is freed behind the stream's work.
+sls_status build_job(ServerJob &J, cudaStream_t s, size_t *footprint)
 {
-    const int64_t n = J.hm.n;
+    const int64_t n = J.n, m = J.m;
     const size_t cbytes = sizeof(double) * 2 * (size_t)n;
-    cudaStream_t cs = S->copy_stream;
-    bool ok = cudaMallocAsync((void **)&J.d_xy[0], cbytes, cs) == cudaSuccess &&
-              cudaMallocAsync((void **)&J.d_xy[1], cbytes, cs) == cudaSuccess &&
-              cudaMallocAsync((void **)&J.d_off, sizeof(uint32_t) * (n + 1), cs) == cudaSuccess &&
-              cudaMallocAsync((void **)&J.d_adj, sizeof(uint32_t) * std::max<size_t>(1, J.hm.adj.size()), cs) == cudaSuccess &&
-              cudaMallocAsync((void **)&J.d_stats, sizeof(PassStats) * std::max(1, J.max_iter), cs) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(J.d_xy[0], J.xy.data(), cbytes, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-         cudaMemcpyAsync(J.d_xy[1], J.xy.data(), cbytes, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-         cudaMemcpyAsync(J.d_off, J.hm.node_off.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-         cudaMemcpyAsync(J.d_adj, J.hm.adj.data(), sizeof(uint32_t) * J.hm.adj.size(), cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-         cudaMemsetAsync(J.d_stats, 0, sizeof(PassStats) * std::max(1, J.max_iter), cs) == cudaSuccess &&
-         cudaEventCreateWithFlags(&J.uploaded, cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventRecord(J.uploaded, cs) == cudaSuccess;
-    if (!ok) cudaGetLastError();
-    return ok;
+    int32_t *d_tri = nullptr;
+    auto cleanup = [&](sls_status st) {
+        cudaFreeAsync(d_tri, s);
+        free_job_device(J, s);
+        return st;
+    };
+    auto cuda_err = [&](cudaError_t e, const char *what) { return cleanup(cuda_fail(e, what)); };
+    cudaError_t e = cudaSuccess;
+    for (void **p : {(void **)&J.d_xy[0], (void **)&J.d_xy[1]})
+        if (e == cudaSuccess) e = cudaMallocAsync(p, cbytes, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_tri, sizeof(int32_t) * 3 * (size_t)m, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&J.d_stats, sizeof(PassStats) * (size_t)std::max(1, J.max_iter), s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return cleanup(fail(SLS_ERR_OOM, "device allocation failed"));
+    }
+    if (e != cudaSuccess) return cuda_err(e, "device allocation");
+    e = cudaMemcpyAsync(J.d_xy[0], J.xy.data(), cbytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_tri, J.tri.data(), sizeof(int32_t) * 3 * (size_t)m, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_err(e, "upload");
+    DeviceAdjacency da;
+    sls_status st = build_device_adjacency(n, m, J.d_xy[0], d_tri, J.has_boundary ? J.boundary.data() : nullptr,
+                                           true, s, da);
+    if (st == SLS_ERR_NOT_FOUND) {
+        // a node in more triangles than the device build handles: host build
+        HostMesh hm;
+        st = build_host_mesh(J.xy.data(), n, J.tri.data(), m, J.has_boundary ? J.boundary.data() : nullptr, hm, 1);
+        if (st != SLS_OK) return cleanup(st);
+        da.adj_words = hm.node_off[n];
+        da.n_free = hm.n_free;
+        da.diag = hm.diag;
+        e = cudaMallocAsync((void **)&da.node_off, sizeof(uint32_t) * (size_t)(n + 1), s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&da.adj, sizeof(uint32_t) * std::max<uint64_t>(1, da.adj_words), s);
+        J.d_off = da.node_off;  // freed with the job on any failure below
+        J.d_adj = da.adj;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(da.node_off, hm.node_off.data(), sizeof(uint32_t) * (size_t)(n + 1),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(da.adj, hm.adj.data(), sizeof(uint32_t) * da.adj_words, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors go out of scope
+        if (e != cudaSuccess) return cuda_err(e, "upload adjacency");
+    } else if (st != SLS_OK) {
+        return cleanup(st);
+    }
+    J.d_off = da.node_off;
+    J.d_adj = da.adj;
+    J.diag = da.diag;
+    e = cudaFreeAsync(d_tri, s);
+    d_tri = nullptr;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(J.d_xy[1], J.d_xy[0], cbytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(J.d_stats, 0, sizeof(PassStats) * (size_t)std::max(1, J.max_iter), s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&J.uploaded, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(J.uploaded, s);
+    if (e != cudaSuccess) return cuda_err(e, "build");
+    *footprint = built_footprint(n, da.adj_words, J.max_iter);
+    return SLS_OK;
 }
 
-// Uploads admitted jobs in admission order, off the scheduler's thread (the
-// host buffers are pageable, so each copy occupies the calling thread).
-void uploader_loop(sls_server *S)
+// Builds admitted jobs on the device, one at a time, on this thread's stream.
+void builder_loop(sls_server *S, cudaStream_t s)
 {
     cudaSetDevice(S->device);
     for (;;) {
         std::shared_ptr<ServerJob> J;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_upload.wait(lk, [S] { return S->stop || !S->to_upload.empty(); });
-            if (S->stop) return;
-            J = S->to_upload.front();
-            S->to_upload.pop_front();
+            S->cv_build.wait(lk, [S] { return S->stop || !S->to_build.empty(); });
+            if (S->stop) break;
+            J = S->to_build.front();
+            S->to_build.pop_front();
         }
-        const bool ok = start_upload(S, *J);
+        size_t fp = 0;
+        J->build_stream = s;
+        const sls_status st = build_job(*J, s, &fp);
+        const std::string err = st == SLS_OK ? std::string() : std::string(sls_last_error());
         std::lock_guard<std::mutex> lk(S->mu);
-        J->upload_state = ok ? 1 : 2;
+        J->tri.clear();
+        J->tri.shrink_to_fit();
+        J->boundary.clear();
+        J->boundary.shrink_to_fit();
+        if (st == SLS_OK) {
+            S->used = S->used - J->reserved + fp;  // the scratch and the bound's slack return
+            J->reserved = fp;
+            J->upload_state = 1;
+        } else {
+            S->used -= J->reserved;
+            J->reserved = 0;
+            J->upload_state = 2;
+            J->status = st;
+            J->error = err;
+        }
         S->cv_sched.notify_all();
     }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->builders_live -= 1;
+    S->cv_sched.notify_all();
 }
 
 template <class T>
@@ -221,21 +281,12 @@ bool grow_pair(T *&h, T *&d, size_t &cap, size_t need)
     return true;
 }
 
-void fail_job(sls_server *S, ServerJob &J, sls_status st, const char *msg)
-{
-    J.state = kFailed;
-    J.status = st;
-    J.error = msg;
-    J.t_done = Clock::now();
-    S->cv_done.notify_all();
-}
-
 // Rebuilds the job table and the warp-task list of the active set.
 bool rebuild_table(sls_server *S)
 {
     const size_t na = S->active.size();
     size_t ntasks = 0;
-    for (auto &J : S->active) ntasks += (size_t)((J->hm.n + 31) / 32);
+    for (auto &J : S->active) ntasks += (size_t)((J->n + 31) / 32);
     if (!grow_pair(S->h_jobs, S->d_jobs, S->jobs_cap, na) ||
         !grow_pair(S->h_tasks, S->d_tasks, S->tasks_cap, std::max<size_t>(1, ntasks)))
         return false;
@@ -247,9 +298,9 @@ bool rebuild_table(sls_server *S)
         D.xy[1] = J.d_xy[1];
         D.node_off = J.d_off;
         D.adj = J.d_adj;
-        D.n = J.hm.n;
+        D.n = J.n;
         D.stats = J.d_stats;
-        const double thr = tolerance_threshold(J.tol, J.hm.diag);
+        const double thr = tolerance_threshold(J.tol, J.diag);
         std::memcpy(&D.thr_bits, &thr, sizeof thr);
         D.strict = S->opt.accept_strict;
         D.tol_active = J.tol > 0.0 ? 1 : 0;
@@ -258,7 +309,7 @@ bool rebuild_table(sls_server *S)
         D.cur0 = 0;
         D.pad = 0;
         D.accept = nullptr;
-        for (int64_t f = 0; f < J.hm.n; f += 32) S->h_tasks[t++] = WarpTask{(int32_t)j, (int32_t)f};
+        for (int64_t f = 0; f < J.n; f += 32) S->h_tasks[t++] = WarpTask{(int32_t)j, (int32_t)f};
     }
     S->ntasks = (int64_t)t;
     return cudaMemcpyAsync(S->d_jobs, S->h_jobs, sizeof(JobDesc) * na, cudaMemcpyHostToDevice, S->stream) == cudaSuccess &&
@@ -282,7 +333,7 @@ void retire_loop(sls_server *S)
         bool ok = true;
         for (auto &Jp : batch) {
             ServerJob &J = *Jp;
-            J.result.resize(2 * (size_t)J.hm.n);
+            J.result.resize(2 * (size_t)J.n);
             ok = ok && cudaMemcpyAsync(J.result.data(), J.d_xy[J.iterations & 1], sizeof(double) * J.result.size(),
                                        cudaMemcpyDeviceToHost, S->retire_stream) == cudaSuccess;
         }
@@ -293,21 +344,31 @@ void retire_loop(sls_server *S)
         for (auto &Jp : batch) {
             ServerJob &J = *Jp;
             free_job_device(J, S->retire_stream);
-            S->used -= J.footprint;
+            S->used -= J.reserved;
+            J.reserved = 0;
             if (ok) {
                 J.t_done = now;
                 J.state = kDone;
                 S->latency_ms.push_back(std::chrono::duration<double, std::milli>(J.t_done - J.t_submit).count());
-                S->node_updates += (double)J.hm.n * (double)J.iterations;
+                S->node_updates += (double)J.n * (double)J.iterations;
                 S->completed += 1;
             } else {
                 fail_job(S, J, SLS_ERR_CUDA, "copying the result to the host failed");
             }
-            J.hm = HostMesh();
         }
         S->cv_done.notify_all();
         S->cv_sched.notify_all();
     }
+}
+
+// Whether the first queued job may be admitted: its bound fits the budget,
+// or nothing else holds any (a job larger than its bound allows still gets
+// its chance alone; its own allocations decide).
+bool can_admit(const sls_server *S)
+{
+    if (S->queued.empty()) return false;
+    const size_t need = S->queued.front()->reserved;
+    return S->used + need <= S->budget || S->used == 0;
 }
 
 void scheduler_loop(sls_server *S)
@@ -321,47 +382,52 @@ void scheduler_loop(sls_server *S)
                 if (S->stop || !S->active.empty()) return true;
                 for (auto &J : S->uploading)
                     if (J->upload_state != 0) return true;
-                return !S->queued.empty() && S->used + S->queued.front()->footprint <= S->budget;
+                return can_admit(S);
             });
             if (S->stop) break;
-            while (!S->queued.empty() && S->used + S->queued.front()->footprint <= S->budget) {
+            bool handed = false;
+            while (can_admit(S)) {
                 auto J = S->queued.front();
                 S->queued.pop_front();
-                S->used += J->footprint;
-                J->state = kUploading;
+                S->used += J->reserved;
+                J->state = kBuilding;
                 J->upload_state = 0;
                 S->uploading.push_back(J);
-                S->to_upload.push_back(J);
+                S->to_build.push_back(J);
+                handed = true;
             }
-            if (!S->to_upload.empty()) S->cv_upload.notify_one();
+            if (handed) S->cv_build.notify_all();
         }
-        // jobs whose upload has finished join in this round (the copies
-        // overlap the previous round); with nothing running, wait for them.
-        // One uploader thread and one copy stream finish uploads in admission
-        // order, so the scan stops at the first one still pending or running.
+        // built jobs join in this round (their builds overlap the previous
+        // rounds); with nothing running, wait for the first one to be built.
         for (size_t k = 0; k < S->uploading.size();) {
             auto J = S->uploading[k];
             int ust;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 ust = J->upload_state;
-                if (ust == 2) {  // freed behind whatever of its copies was enqueued
-                    free_job_device(*J, S->copy_stream);
-                    S->used -= J->footprint;
-                    fail_job(S, *J, SLS_ERR_OOM, "device allocation or upload failed");
-                }
+                if (ust == 2) fail_job(S, *J, J->status, J->error);  // the builder freed its memory
             }
             if (ust == 2) {
                 S->uploading.erase(S->uploading.begin() + k);
                 continue;
             }
-            if (ust == 0) break;  // copies not enqueued yet, nor those of later jobs
+            if (ust == 0) {
+                ++k;
+                continue;
+            }
             if (S->active.empty()) cudaEventSynchronize(J->uploaded);
-            if (cudaEventQuery(J->uploaded) != cudaSuccess) break;
-            J->xy.clear();
-            J->xy.shrink_to_fit();
-            J->base_round = S->round;
-            J->state = kActive;
+            if (cudaEventQuery(J->uploaded) != cudaSuccess) {
+                ++k;
+                continue;
+            }
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                J->xy.clear();
+                J->xy.shrink_to_fit();
+                J->base_round = S->round;
+                J->state = kActive;
+            }
             S->active.push_back(J);
             S->uploading.erase(S->uploading.begin() + k);
             dirty = true;
@@ -406,7 +472,7 @@ void scheduler_loop(sls_server *S)
                 J.info.accepted_last = (int64_t)r.nacc;
                 std::memcpy(&J.info.max_d2_last, &r.maxd2_bits, sizeof(double));
                 J.info.fp64_fallbacks += (int64_t)r.fallbacks;
-                const double thr = tolerance_threshold(J.tol, J.hm.diag);
+                const double thr = tolerance_threshold(J.tol, J.diag);
                 unsigned long long tb;
                 std::memcpy(&tb, &thr, sizeof tb);
                 const bool conv = J.tol > 0.0 && r.maxd2_bits < tb;
@@ -434,28 +500,32 @@ void scheduler_loop(sls_server *S)
             dirty = true;
         }
     }
-    // cancel what is left, once the uploader has stopped touching jobs
-    {
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->stop = true;
+    // cancel what is left, once no builder touches a job any more
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv_build.notify_all();
+    S->cv_sched.wait(lk, [S] { return S->builders_live == 0; });
+    for (auto &J : S->active) {
+        free_job_device(*J, S->stream);
+        S->used -= J->reserved;
+        fail_job(S, *J, SLS_ERR_NOT_FOUND, "server destroyed before the job finished");
     }
-    S->cv_upload.notify_all();
-    if (S->uploader.joinable()) S->uploader.join();
-    std::lock_guard<std::mutex> lk(S->mu);
-    for (auto *list : {&S->active, &S->uploading}) {
-        // an uploading job's memory is freed behind its own copies
-        for (auto &J : *list) {
-            free_job_device(*J, list == &S->active ? S->stream : S->copy_stream);
-            fail_job(S, *J, SLS_ERR_NOT_FOUND, "server destroyed before the job finished");
-        }
-        list->clear();
+    S->active.clear();
+    for (auto &J : S->uploading) {
+        // built or failed by a builder (memory on its stream), or never started
+        if (J->upload_state == 1) free_job_device(*J, J->build_stream);
+        if (J->upload_state != 2) S->used -= J->reserved;
+        fail_job(S, *J, SLS_ERR_NOT_FOUND, "server destroyed before the job finished");
     }
+    S->uploading.clear();
+    S->to_build.clear();
     for (auto &J : S->queued) fail_job(S, *J, SLS_ERR_NOT_FOUND, "server destroyed before the job started");
     S->queued.clear();
     if (!S->sched_error.empty())
         for (auto &kv : S->jobs)
             if (kv.second->state != kDone && kv.second->state != kFailed && kv.second->state != kRetiring)
                 fail_job(S, *kv.second, SLS_ERR_CUDA, "scheduler stopped on a CUDA error");
+    lk.unlock();
     cudaStreamSynchronize(S->stream);
 }
 
@@ -473,6 +543,7 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
     if (st != SLS_OK) return st;
     if (o.form != 0 || o.precision != 64) return fail(SLS_ERR_INVALID, "the server runs FP64 Form A only");
     if (o.skip_unchanged) return fail(SLS_ERR_INVALID, "the server computes every tile (skip_unchanged is for single meshes)");
+    if (o.layout != 0) return fail(SLS_ERR_INVALID, "the server keeps coordinates interleaved (layout = 0)");
     auto S = std::make_unique<sls_server>();
     S->opt = o;
     S->max_queue = max_queue;
@@ -480,10 +551,21 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(SLS_ERR_CUDA, "cudaMemGetInfo failed");
     S->budget = hbm_budget ? hbm_budget : (size_t)(0.8 * (double)free_b);
-    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->retire_stream, cudaStreamNonBlocking) != cudaSuccess)
+    // builders: each uploads and builds one job at a time on its own stream
+    const int nb = std::min(kBuilders, std::max(1, (int)std::thread::hardware_concurrency()));
+    S->build_streams.assign(nb, nullptr);
+    bool streams_ok = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaStreamCreateWithFlags(&S->retire_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &bs : S->build_streams)
+        streams_ok = streams_ok && cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
+    if (!streams_ok) {
+        cudaGetLastError();
+        for (cudaStream_t x : S->build_streams)
+            if (x) cudaStreamDestroy(x);
+        if (S->stream) cudaStreamDestroy(S->stream);
+        if (S->retire_stream) cudaStreamDestroy(S->retire_stream);
         return fail(SLS_ERR_CUDA, "cudaStreamCreate failed");
+    }
     if (cudaDeviceGetDefaultMemPool(&S->pool, S->device) == cudaSuccess) {
         uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
         cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
@@ -491,10 +573,8 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
     S->block = (opt != nullptr && opt->block_size >= 32 && opt->block_size <= 128) ? opt->block_size : 128;
     S->grid = device_sm_count() * batch_pass_occupancy(o.layout, S->block);
     sls_server *raw = S.release();
-    // one single-threaded adjacency build per host core (jobs are small and many)
-    const int nb = std::max(2, (int)std::thread::hardware_concurrency());
-    for (int b = 0; b < nb; ++b) raw->builders.emplace_back(builder_loop, raw);
-    raw->uploader = std::thread(uploader_loop, raw);
+    raw->builders_live = nb;
+    for (int b = 0; b < nb; ++b) raw->builders.emplace_back(builder_loop, raw, raw->build_streams[b]);
     raw->retirer = std::thread(retire_loop, raw);
     raw->sched = std::thread(scheduler_loop, raw);
     *out = raw;
@@ -508,7 +588,7 @@ sls_status sls_submit(sls_server *S, const double *xy, int64_t n, const int32_t 
     if (n < 3 || m < 1 || n >= (int64_t(1) << 31) || m >= (int64_t(1) << 31))
         return fail(SLS_ERR_INVALID, "bad mesh size");
     if (max_iter < 0 || std::isnan(tol_rel)) return fail(SLS_ERR_INVALID, "bad stop rule");
-    // quick lower bound of the footprint: coordinates and offsets alone
+    // what the job holds at least once built: coordinates and offsets alone
     const size_t least = 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1);
     if (least > S->budget) return fail(SLS_ERR_REJECTED, "job larger than the server's memory budget");
     auto J = std::make_shared<ServerJob>();
@@ -520,15 +600,18 @@ sls_status sls_submit(sls_server *S, const double *xy, int64_t n, const int32_t 
         J->boundary.assign(boundary, boundary + n);
         J->has_boundary = true;
     }
+    J->n = n;
+    J->m = m;
     J->max_iter = max_iter;
     J->tol = tol_rel;
+    J->reserved = admission_bound(n, m, max_iter);
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->max_queue > 0 && (int64_t)(S->to_build.size() + S->queued.size()) >= S->max_queue)
         return fail(SLS_ERR_BUSY, "server queue is full");
     J->id = S->next_id++;
     S->jobs[J->id] = J;
-    S->to_build.push_back(J);
-    S->cv_build.notify_one();
+    S->queued.push_back(J);
+    S->cv_sched.notify_all();
     *job = J->id;
     return SLS_OK;
 }
@@ -585,9 +668,9 @@ sls_status sls_server_destroy(sls_server *S)
     }
     S->cv_build.notify_all();
     S->cv_sched.notify_all();
-    S->cv_upload.notify_all();
-    for (auto &t : S->builders) t.join();
+    // the scheduler cancels what is left once every builder has stopped
     if (S->sched.joinable()) S->sched.join();
+    for (auto &t : S->builders) t.join();
     {
         // the scheduler has stopped handing over jobs: finish what it handed over
         std::lock_guard<std::mutex> lk(S->mu);
@@ -595,7 +678,7 @@ sls_status sls_server_destroy(sls_server *S)
     }
     S->cv_retire.notify_all();
     if (S->retirer.joinable()) S->retirer.join();
-    cudaStreamSynchronize(S->copy_stream);
+    for (cudaStream_t bs : S->build_streams) cudaStreamSynchronize(bs);
     cudaStreamSynchronize(S->retire_stream);
     cudaFreeHost(S->h_jobs);
     cudaFree(S->d_jobs);
@@ -604,8 +687,8 @@ sls_status sls_server_destroy(sls_server *S)
     cudaFreeHost(S->h_round);
     cudaFree(S->d_round);
     cudaStreamDestroy(S->stream);
-    cudaStreamDestroy(S->copy_stream);
     cudaStreamDestroy(S->retire_stream);
+    for (cudaStream_t bs : S->build_streams) cudaStreamDestroy(bs);
     delete S;
     return SLS_OK;
 }

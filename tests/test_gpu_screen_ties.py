@@ -63,9 +63,17 @@ def test_rounding_level_ties_take_the_exact_path(sls, strict, numbering):
     assert np.array_equal(xy, ref_xy)
     assert np.array_equal(acc, ref_acc)
     assert info["accepted_last"] == ref_nacc and info["maxd2_last"] == ref_d2
-    # most planted nodes cannot be decided in FP32 (the rest are exact ties,
-    # which need no quality at all, or were decided by the difference screen)
-    assert info["fp64_fallbacks"] >= nodes.size // 2, (info["fp64_fallbacks"], nodes.size)
+    # a planted node whose centre differs from it but whose FP64 qualities tie
+    # (q_new == q_old) can be decided by neither screen: it must take the
+    # exact path.  (Nodes exactly at their centre need no quality at all;
+    # the difference screen decides gaps above about 1e-14.)
+    _, _, _, qo, qn, centre = om.update_nodes(mesh.xy, nodes, strict=strict)
+    must = int((((centre != mesh.xy[nodes]).any(1)) & (qn == qo)).sum())
+    assert must > 0 and info["fp64_fallbacks"] >= must, (info["fp64_fallbacks"], must)
+    # and the screen defers a large share of the planted nodes: 631 of 1,911
+    # when this was written, against 625 planted nodes whose FP64 gap is at
+    # most 8e-15 (the difference screen's resolution)
+    assert info["fp64_fallbacks"] >= 300, info["fp64_fallbacks"]
     # both outcomes occur among the planted nodes
     planted = ref_acc[nodes]
     assert planted.min() == 0 and planted.max() == 1

@@ -139,3 +139,37 @@ def test_served_edge_meshes(sls):
         for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
             assert info[key] == rinfo[key], key
     srv.close()
+
+
+def test_served_million_node_job_in_a_mix(sls):
+    """A 1024x1024 (1,048,576-node) job submitted between small ones, built
+    on the device by the server's builders, equals the oracle bit for bit;
+    so does a job from meshgen.fast_grid, the served benchmark's generator."""
+    big = meshgen.jittered_grid(1024, 1024, 0.3, 777, numbering="morton")
+    fast = meshgen.fast_grid(300, 280, 0.3, 4242)
+    small = _jobs(12, 5)
+    srv = sls.Server()
+    ids = [srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=tol) for m, cap, tol in small[:6]]
+    jb = srv.submit(big.xy, big.tri, big.boundary, max_iter=12, tol=1e-9)
+    jf = srv.submit(fast.xy, fast.tri, fast.boundary, max_iter=40, tol=1e-9)
+    ids += [srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=tol) for m, cap, tol in small[6:]]
+    xy_b, info_b = srv.wait(jb, timeout=300.0)
+    xy_f, info_f = srv.wait(jf, timeout=300.0)
+    for (m, cap, tol), jid in zip(small, ids):
+        xy, info = srv.wait(jid, timeout=300.0)
+        rxy, rinfo, _ = oracle.OracleMesh(m.xy, m.tri, m.boundary).smooth(m.xy, cap, tol=tol)
+        assert np.array_equal(xy, rxy)
+    srv.close()
+    rxy, rinfo, _ = oracle.OracleMesh(big.xy, big.tri, big.boundary, openmp=True).smooth(big.xy, 12, tol=1e-9)
+    assert np.array_equal(xy_b, rxy)
+    for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
+        assert info_b[key] == rinfo[key], key
+    rxy, rinfo, _ = oracle.OracleMesh(fast.xy, fast.tri, fast.boundary).smooth(fast.xy, 40, tol=1e-9)
+    assert np.array_equal(xy_f, rxy)
+    assert info_f["iterations"] == rinfo["iterations"]
+
+
+def test_server_rejects_the_soa_layout(sls):
+    with pytest.raises(sls.SlsError) as e:
+        sls.Server(layout="soa")
+    assert e.value.code == 1

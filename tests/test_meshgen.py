@@ -99,3 +99,40 @@ def test_delaunay_numberings_are_permutations_of_one_mesh():
     ta = np.sort(np.sort(a.perm.argsort()[a.tri], axis=1), axis=0)
     tr = np.sort(np.sort(r.perm.argsort()[r.tri], axis=1), axis=0)
     assert np.array_equal(np.unique(ta, axis=0), np.unique(tr, axis=0))
+
+
+def test_fast_grid_construction():
+    """fastgrid.c against the numpy construction: the Morton numbering equals
+    morton_order, the triangles are grid_triangles of the diagonals it drew,
+    the outer ring is fixed and exact, the interior jitter stays within J h,
+    and the same arguments give the same mesh."""
+    for nx, ny in [(2, 2), (5, 3), (17, 33), (64, 64), (100, 37)]:
+        m = meshgen.fast_grid(nx, ny, 0.3, 12345 + nx)
+        h = 1.0 / (ny - 1)
+        gi, gj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+        gi, gj = gi.ravel(), gj.ravel()
+        perm = meshgen.morton_order(gi, gj)
+        nat = m.xy[perm]
+        ring = (gi == 0) | (gj == 0) | (gi == nx - 1) | (gj == ny - 1)
+        assert np.array_equal(m.boundary[perm], ring.astype(np.uint8))
+        assert np.array_equal(nat[ring, 0], gi[ring] * h) and np.array_equal(nat[ring, 1], gj[ring] * h)
+        assert np.all(np.abs(nat[:, 0] - gi * h) <= 0.3 * h * (1 + 1e-12))
+        assert np.all(np.abs(nat[:, 1] - gj * h) <= 0.3 * h * (1 + 1e-12))
+        if (~ring).any():
+            assert np.any(nat[~ring, 0] != gi[~ring] * h)
+        # recover the diagonals from the first triangle of each quad
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        t_nat = inv[m.tri]
+        nq = (nx - 1) * (ny - 1)
+        diag = (t_nat[0::2, 2] != t_nat[0::2, 1] + nx).astype(np.int64)
+        assert np.array_equal(t_nat, meshgen.grid_triangles(nx, ny, diag))
+        if nq >= 64:
+            assert 0.3 < diag.mean() < 0.7
+        again = meshgen.fast_grid(nx, ny, 0.3, 12345 + nx)
+        assert np.array_equal(again.xy, m.xy) and np.array_equal(again.tri, m.tri)
+    nat = meshgen.fast_grid(9, 7, 0.3, 1, numbering="natural")
+    mor = meshgen.fast_grid(9, 7, 0.3, 1, numbering="morton")
+    gi, gj = np.meshgrid(np.arange(9), np.arange(7), indexing="xy")
+    perm = meshgen.morton_order(gi.ravel(), gj.ravel())
+    assert np.array_equal(mor.xy[perm], nat.xy)
