@@ -638,6 +638,8 @@ def main():
                     help="A: Jacobi (the headline); B: multicolour Gauss-Seidel")
     ap.add_argument("--skip-unchanged", action="store_true",
                     help="leave unchanged tiles as they are (identical results; not the headline)")
+    ap.add_argument("--decompose", action="store_true",
+                    help="split the single mesh over the ranks (domain decomposition) instead of replicas")
     ap.add_argument("--l2-window", action="store_true",
                     help="persisting L2 window over the gathered coordinates (identical results)")
     args = ap.parse_args()
@@ -664,11 +666,73 @@ def single_workload(args):
     return mesh, workload, MAX_PASSES, TOL
 
 
+def run_decomposed(args, mesh, workload, max_passes, tol):
+    """The single mesh split over the ranks by domain decomposition (one
+    subdomain per GPU, a ghost exchange and a max all-reduce per pass;
+    paper_1502_00355_gb300/domain.py).  Strong scaling: the whole mesh's
+    node-updates over the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    import paper_1502_00355_gb300 as sls
+    from paper_1502_00355_gb300 import domain
+    world, rank = init_ranks()
+    sls.lib()
+    sub = domain.partition(mesh.n, mesh.tri, mesh.boundary, world, rank)
+    stream = torch.cuda.Stream()
+    be = domain.LibraryBackend(sub, mesh.xy[sub.nodes], stream=stream.cuda_stream)
+    dm = domain.DistributedMesh(sub, be, mesh.xy[sub.lo:sub.hi], device="cuda")
+    xy0 = torch.from_numpy(np.ascontiguousarray(mesh.xy[sub.nodes])).cuda()
+
+    def step():
+        be.mesh.set_coords(xy0)
+        return dm.smooth(max_passes, tol)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        clk.mark_start()
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk.mark_end()
+    if world > 1:
+        dist.barrier()
+    passes = sum(i["iterations"] for i in infos)
+    ms_max, _ = reduce_over_ranks(e0.elapsed_time(e1), 0.0, device="cuda")
+    value = mesh.n * passes / (ms_max * 1e-3)
+    be.close()
+    if rank == 0:
+        cfg = large_config(args, mesh, workload, world)
+        cfg["parallelism"] = f"domain decomposition over {world} ranks (ghost exchange + max all-reduce per pass)"
+        out = {"metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+               "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": cfg,
+               "run": {"passes_per_step": passes / args.steps, "owned_nodes_rank0": sub.hi - sub.lo,
+                       "local_nodes_rank0": sub.n_local},
+               "gpu_launches": passes * (1 + 2 * len(sub.send)),
+               "timed": "CUDA events on rank 0's library stream around the steps (every pass ends in a host "
+                        "synchronisation for the exchange)",
+               "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_single(args):
     mesh, workload, max_passes, tol = single_workload(args)
     if args.impl == "reference":
         run_reference(args, mesh, workload)
         return
+    if args.decompose:
+        return run_decomposed(args, mesh, workload, max_passes, tol)
 
     import torch
     import torch.distributed as dist

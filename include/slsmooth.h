@@ -170,6 +170,22 @@ sls_status sls_get_coords(const sls_mesh *mesh, double *xy_out, int32_t dst_is_d
  * call returns once the coordinates are in place. */
 sls_status sls_set_coords(sls_mesh *mesh, const double *xy, int32_t src_is_device);
 
+/* Ghost exchange of a mesh split over several GPUs (a build addition: the
+ * paper runs on one GPU).  Form A reads only the previous pass (Eq. 2), so a
+ * mesh split into subdomains, each holding its nodes plus a one-ring of
+ * ghost nodes (fixed in the subdomain's mesh), gives the same passes as the
+ * whole mesh when every ghost gets its owner's coordinates between passes.
+ *   sls_gather_coords  copies the current coordinates of the k nodes idx[]
+ *                      (device int32, ids of this mesh) to out (device, 2k
+ *                      float64 interleaved);
+ *   sls_scatter_coords writes in (device, 2k float64) into both coordinate
+ *                      arrays of the k listed nodes (distinct ids).
+ * Both run on the handle's stream and return when done.  FP64 meshes only.
+ * Errors: SLS_ERR_INVALID for an id outside [0, n) (nothing is written for
+ * it) or a binary32 mesh. */
+sls_status sls_gather_coords(sls_mesh *mesh, const int32_t *idx, int64_t k, double *out);
+sls_status sls_scatter_coords(sls_mesh *mesh, const int32_t *idx, int64_t k, const double *in);
+
 /* Copies the accept decisions of the last executed pass (n uint8, host;
  * 1 = moved to the centre).  Needs opt->record_accept = 1. */
 sls_status sls_get_accept(const sls_mesh *mesh, uint8_t *accept_out);

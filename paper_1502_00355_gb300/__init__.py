@@ -78,6 +78,8 @@ def lib() -> C.CDLL:
                 "sls_get_coords": (S, [P, P, I32]),
                 "sls_set_coords": (S, [P, P, I32]),
                 "sls_get_accept": (S, [P, P]),
+                "sls_gather_coords": (S, [P, P, I64, P]),
+                "sls_scatter_coords": (S, [P, P, I64, P]),
                 "sls_quality_histogram": (S, [P, I32, D, D, P, P, P]),
                 "sls_mesh_stats": (S, [P, P, P, P, P]),
                 "sls_mesh_destroy": (S, [P]),
@@ -228,6 +230,19 @@ class Mesh:
         if xy.shape[0] != self.n:
             raise ValueError("wrong number of nodes")
         _check(lib().sls_set_coords(self.handle, _p(xy), 0), "sls_set_coords")
+
+    def gather(self, idx, out):
+        """Current coordinates of the nodes idx (int32 CUDA tensor) into out
+        (float64 CUDA tensor of shape (k, 2))."""
+        _check(lib().sls_gather_coords(self.handle, C.c_void_p(idx.data_ptr()), int(idx.numel()),
+                                       C.c_void_p(out.data_ptr())), "sls_gather_coords")
+        return out
+
+    def scatter(self, idx, values):
+        """Overwrite the coordinates of the nodes idx (int32 CUDA tensor) with
+        values (float64 CUDA tensor of shape (k, 2))."""
+        _check(lib().sls_scatter_coords(self.handle, C.c_void_p(idx.data_ptr()), int(idx.numel()),
+                                        C.c_void_p(values.data_ptr())), "sls_scatter_coords")
 
     def accept_mask(self) -> np.ndarray:
         out = np.empty(self.n, np.uint8)

@@ -196,6 +196,20 @@ sls_status sls_set_coords(sls_mesh *M, const double *xy, int32_t src_is_device)
     return mesh_set_coords(M, xy, src_is_device != 0);
 }
 
+sls_status sls_gather_coords(sls_mesh *M, const int32_t *idx, int64_t k, double *out)
+{
+    if (!M) return fail(SLS_ERR_INVALID, "mesh must not be NULL");
+    if (k < 0 || (k > 0 && (!idx || !out))) return fail(SLS_ERR_INVALID, "need k >= 0 and device idx and out");
+    return mesh_transfer_nodes(M, idx, k, out, false);
+}
+
+sls_status sls_scatter_coords(sls_mesh *M, const int32_t *idx, int64_t k, const double *in)
+{
+    if (!M) return fail(SLS_ERR_INVALID, "mesh must not be NULL");
+    if (k < 0 || (k > 0 && (!idx || !in))) return fail(SLS_ERR_INVALID, "need k >= 0 and device idx and in");
+    return mesh_transfer_nodes(M, idx, k, const_cast<double *>(in), true);
+}
+
 sls_status sls_get_accept(const sls_mesh *M, uint8_t *accept_out)
 {
     if (!M || !accept_out) return fail(SLS_ERR_INVALID, "mesh and accept_out must not be NULL");

@@ -35,6 +35,7 @@ struct sls_mesh {
     uint32_t *accm = nullptr;     // per tile: nodes accepted when the tile was last computed
     size_t l2_persist = 0;        // l2_window: persisting L2 bytes set aside for this context
     size_t l2_win_max = 0;        //            largest access-policy window the device accepts
+    unsigned *xfer_bad = nullptr; // gather/scatter: set when an id was out of range
     int block = 256, grid = 0;
     bool screened = true;         // screened kernel (else the plain FP64 kernel)
     sls_info last{};
@@ -88,6 +89,9 @@ void mesh_release(sls_mesh *M);
 sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info);
 sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device);
 sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device);
+// Device gather (scatter = false: buf <- current coordinates of the listed
+// nodes) or scatter (buf -> both coordinate arrays) of k nodes; returns when done.
+sls_status mesh_transfer_nodes(sls_mesh *M, const int32_t *idx, int64_t k, double *buf, bool scatter);
 sls_status mesh_histogram(const sls_mesh *M, int nbins, double lo, double hi, int64_t *counts,
                           double *qmin, double *qmean);
 

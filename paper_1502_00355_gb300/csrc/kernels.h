@@ -50,6 +50,14 @@ cudaError_t launch_copy_back_f32(const float *src, float *dst, int64_t count, co
 cudaError_t launch_narrow(const double *aos, float *dst, int64_t n, int layout, int grid, cudaStream_t s);
 cudaError_t launch_widen(const float *src, double *aos, int64_t n, int layout, int grid, cudaStream_t s);
 
+// Ghost exchange of a domain-decomposed mesh: the listed nodes' coordinates
+// (interleaved out / in, 2k doubles) from the current array, or into both
+// arrays; an id outside [0, n) sets *bad and is skipped.
+cudaError_t launch_gather_nodes(const double *xy, int layout, int64_t n, const int32_t *idx, int64_t k,
+                                double *out, unsigned *bad, int grid, cudaStream_t s);
+cudaError_t launch_scatter_nodes(double *xy0, double *xy1, int layout, int64_t n, const int32_t *idx, int64_t k,
+                                 const double *in, unsigned *bad, int grid, cudaStream_t s);
+
 // Layout conversions on the device (SoA <-> interleaved).
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int64_t n, int grid, cudaStream_t s);

@@ -211,6 +211,7 @@ void mesh_release(sls_mesh *M)
     cudaFree(M->chg[0]);
     cudaFree(M->chg[1]);
     cudaFree(M->accm);
+    cudaFree(M->xfer_bad);
     if (M->h_stats) cudaFreeHost(M->h_stats);
     if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
     M->stream = nullptr;
@@ -435,6 +436,31 @@ sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
     SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[M->cur ^ 1], M->xy[M->cur], cbytes, cudaMemcpyDeviceToDevice,
                                  M->stream), "copy");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "set coordinates");
+    return SLS_OK;
+}
+
+sls_status mesh_transfer_nodes(sls_mesh *M, const int32_t *idx, int64_t k, double *buf, bool scatter)
+{
+    if (M->f32) return fail(SLS_ERR_INVALID, "node gather/scatter needs an FP64 mesh");
+    if (k == 0) return SLS_OK;
+    if (!M->xfer_bad) {
+        sls_status st = dev_alloc((void **)&M->xfer_bad, sizeof(unsigned), "transfer flag");
+        if (st != SLS_OK) return st;
+    }
+    const int grid = device_sm_count() * 4;
+    SLS_CUDA_TRY(cudaMemsetAsync(M->xfer_bad, 0, sizeof(unsigned), M->stream), "transfer");
+    if (scatter)
+        SLS_CUDA_TRY(launch_scatter_nodes(M->xy[0], M->xy[1], M->opt.layout, M->n, idx, k, buf, M->xfer_bad, grid,
+                                          M->stream), "scatter");
+    else
+        SLS_CUDA_TRY(launch_gather_nodes(M->xy[M->cur], M->opt.layout, M->n, idx, k, buf, M->xfer_bad, grid,
+                                         M->stream), "gather");
+    SLS_CUDA_TRY(cudaMemcpyAsync(M->h_stats, M->xfer_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, M->stream),
+                 "transfer");
+    SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "transfer");
+    unsigned bad;
+    std::memcpy(&bad, M->h_stats, sizeof bad);
+    if (bad) return fail(SLS_ERR_INVALID, "a node id is outside [0, n)");
     return SLS_OK;
 }
 

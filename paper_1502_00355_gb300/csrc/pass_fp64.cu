@@ -155,6 +155,67 @@ cudaError_t launch_histogram(const double *xy, int layout, int64_t n, const int3
     return cudaGetLastError();
 }
 
+namespace {
+
+// Coordinates of the listed nodes out of the current array (ghost exchange
+// of a domain-decomposed mesh); an id outside [0, n) sets *bad and is skipped.
+template <int LAYOUT>
+__global__ void gather_nodes_kernel(const double *__restrict__ xy, int64_t n, const int32_t *__restrict__ idx,
+                                    int64_t k, double2 *__restrict__ out, unsigned *bad)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += stride) {
+        const int32_t i = __ldg(idx + t);
+        if (i < 0 || (int64_t)i >= n) {
+            atomicOr(bad, 1u);
+            continue;
+        }
+        out[t] = Coords<LAYOUT>::get(xy, n, i);
+    }
+}
+
+// The listed nodes' coordinates written into both arrays of the ping-pong.
+template <int LAYOUT>
+__global__ void scatter_nodes_kernel(double *xy0, double *xy1, int64_t n, const int32_t *__restrict__ idx,
+                                     int64_t k, const double2 *__restrict__ in, unsigned *bad)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += stride) {
+        const int32_t i = __ldg(idx + t);
+        if (i < 0 || (int64_t)i >= n) {
+            atomicOr(bad, 1u);
+            continue;
+        }
+        const double2 v = __ldg(in + t);
+        Coords<LAYOUT>::put(xy0, n, i, v);
+        Coords<LAYOUT>::put(xy1, n, i, v);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gather_nodes(const double *xy, int layout, int64_t n, const int32_t *idx, int64_t k,
+                                double *out, unsigned *bad, int grid, cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    if (layout == 0)
+        gather_nodes_kernel<0><<<grid, 256, 0, s>>>(xy, n, idx, k, reinterpret_cast<double2 *>(out), bad);
+    else
+        gather_nodes_kernel<1><<<grid, 256, 0, s>>>(xy, n, idx, k, reinterpret_cast<double2 *>(out), bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_nodes(double *xy0, double *xy1, int layout, int64_t n, const int32_t *idx, int64_t k,
+                                 const double *in, unsigned *bad, int grid, cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    if (layout == 0)
+        scatter_nodes_kernel<0><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, reinterpret_cast<const double2 *>(in), bad);
+    else
+        scatter_nodes_kernel<1><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, reinterpret_cast<const double2 *>(in), bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int64_t n, int grid, cudaStream_t s)
 {
     soa_to_aos_kernel<<<grid, 256, 0, s>>>(soa, reinterpret_cast<double2 *>(aos), n);
