@@ -214,9 +214,11 @@ sls_status sls_mesh_destroy(sls_mesh *mesh);
  * iters (k int32) and tol_rel (k float64, may be NULL = off) are the per-mesh
  * stop rules.  The handles must outlive the batch; sls_batch_smooth advances
  * their coordinates in place.  The coordinates at packing time are saved for
- * sls_batch_reset.  With opt == NULL or opt->block_size == 0 the block size
- * is autotuned by timing one full batch smooth per candidate (64, 96, 128
- * threads), restoring the saved coordinates after each trial; an explicit
+ * sls_batch_reset.  The launch shape is autotuned by timing one full batch
+ * smooth per candidate, restoring the saved coordinates after each trial:
+ * the chunk of consecutive 32-node tasks a warp takes in the grid stride
+ * (0 = one contiguous share per warp, 1, 4, 16) and, with opt == NULL or
+ * opt->block_size == 0, the block size (64 or 128 threads); an explicit
  * block_size must be 32, 64, 96 or 128 (SLS_ERR_INVALID otherwise). */
 sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *iters,
                             const double *tol_rel, const sls_options *opt, sls_batch **out);
@@ -248,7 +250,8 @@ sls_status sls_batch_destroy(sls_batch *batch);
 
 /* hbm_budget: bytes of device memory the server may hold for jobs (0 = 80%
  * of the free memory at creation).  max_queue: jobs submitted but not yet
- * admitted that sls_submit accepts (0 = unlimited); beyond it sls_submit
+ * built on the device (the jobs whose inputs the server still holds in host
+ * memory) that sls_submit accepts (0 = unlimited); beyond it sls_submit
  * returns SLS_ERR_BUSY.  opt: FP64 Form A with the AoS layout only
  * (SLS_ERR_INVALID otherwise).  The default memory pool of the device is set
  * to keep freed memory (release threshold: unlimited). */

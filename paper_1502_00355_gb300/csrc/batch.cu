@@ -38,6 +38,7 @@ struct sls_batch {
     std::vector<double *> d_start;     // per mesh: the packed starting coordinates
     int rounds = 0;
     int block = 128, grid = 0;
+    int64_t chunk = 0;                 // tasks per warp chunk (0: one contiguous share per warp)
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -73,7 +74,7 @@ sls_status build_graph(sls_batch *B)
     cudaError_t err = cudaSuccess;
     for (int r = 0; r < B->rounds && err == cudaSuccess; ++r)
         err = launch_batch_pass(B->d_jobs, B->d_tasks, B->round_tasks[r], r, B->layout, B->block, B->grid,
-                                B->stream);
+                                B->stream, B->chunk);
     cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
     if (err != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -144,6 +145,7 @@ sls_status run(sls_batch *B, sls_info *infos)
             info.converged = (tol > 0.0 && st[it - 1].maxd2_bits < thr_bits) ? 1 : 0;
         }
         M->cur ^= (it & 1);
+        M->split_ok = false;  // the batch kernel keeps no screen splits
         M->last = info;
         if (infos) infos[mi] = info;
     }
@@ -158,24 +160,42 @@ sls_status reset(sls_batch *B)
         BATCH_TRY(cudaMemcpyAsync(M->xy[0], B->d_start[mi], cbytes, cudaMemcpyDeviceToDevice, B->stream), "reset");
         BATCH_TRY(cudaMemcpyAsync(M->xy[1], B->d_start[mi], cbytes, cudaMemcpyDeviceToDevice, B->stream), "reset");
         M->cur = 0;
+        M->split_ok = false;
     }
     BATCH_TRY(cudaStreamSynchronize(B->stream), "reset");
     return SLS_OK;
 }
 
-// Picks the block size (nodes per CTA) by timing a whole batch smooth for
-// each candidate, restoring the starting coordinates after every trial.
-sls_status autotune(sls_batch *B)
+// Picks the launch shape by timing a whole batch smooth for each candidate,
+// restoring the starting coordinates after every trial: the block size (32-
+// node tasks a CTA runs at once, 4 per 128 threads) and the chunk of
+// consecutive tasks a warp takes in the grid stride (0: one contiguous share
+// of the task list per warp).  Every round of a call is one node of one
+// CUDA graph, so all passes of a call are one launch whatever the shape.
+sls_status autotune(sls_batch *B, bool tune_block)
 {
-    const int candidates[3] = {64, 96, 128};  // the kernel is built for 6 blocks of <= 128
+    struct Shape {
+        int block;
+        int64_t chunk;
+    };
+    std::vector<Shape> cands;
+    const int blocks[2] = {64, 128};  // the kernel is built for 6 blocks of <= 128
+    const int64_t chunks[4] = {0, 1, 4, 16};
+    for (int b : blocks) {
+        if (!tune_block && b != B->block) continue;
+        for (int64_t c : chunks) cands.push_back(Shape{b, c});
+    }
+    if (cands.empty())
+        for (int64_t c : chunks) cands.push_back(Shape{B->block, c});
     float best_ms = -1.0f;
-    int best_block = 128;
+    Shape best = cands[0];
     cudaEvent_t e0, e1;
     BATCH_TRY(cudaEventCreate(&e0), "event");
     BATCH_TRY(cudaEventCreate(&e1), "event");
     sls_status st = SLS_OK;
-    for (int c = 0; c < 3 && st == SLS_OK; ++c) {
-        B->block = candidates[c];
+    for (size_t c = 0; c < cands.size() && st == SLS_OK; ++c) {
+        B->block = cands[c].block;
+        B->chunk = cands[c].chunk;
         B->grid = device_sm_count() * batch_pass_occupancy(B->layout, B->block);
         if (B->rounds > 0) st = build_graph(B);
         if (st != SLS_OK) break;
@@ -187,7 +207,7 @@ sls_status autotune(sls_batch *B)
         cudaEventElapsedTime(&ms, e0, e1);
         if (st == SLS_OK && (best_ms < 0.0f || ms < best_ms)) {
             best_ms = ms;
-            best_block = candidates[c];
+            best = cands[c];
         }
         if (st == SLS_OK) st = reset(B);
     }
@@ -198,7 +218,8 @@ sls_status autotune(sls_batch *B)
         cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;
     }
-    B->block = best_block;
+    B->block = best.block;
+    B->chunk = best.chunk;
     B->grid = device_sm_count() * batch_pass_occupancy(B->layout, B->block);
     return SLS_OK;
 }
@@ -296,9 +317,10 @@ sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *i
         B->block = opt->block_size;
     }
     B->grid = device_sm_count() * batch_pass_occupancy(B->layout, B->block);
-    if (opt == nullptr || opt->block_size == 0) {
-        // autotune on the packed meshes, then restore their coordinates
-        sls_status st = autotune(B);
+    {
+        // autotune on the packed meshes (the block size too unless it was
+        // given), then restore their coordinates
+        sls_status st = autotune(B, opt == nullptr || opt->block_size == 0);
         if (st != SLS_OK) return fail_free(st);
     }
     *out = B;

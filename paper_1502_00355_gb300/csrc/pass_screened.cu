@@ -71,7 +71,30 @@ using namespace scr;
 // grows with |a| and g, so the side's largest |a|, its largest local
 // coordinate R (every vertex of every triangle of that side lies within it)
 // and its smallest edge sum s bound every triangle at once.
-template <int LAYOUT>
+//
+// With CACHED the head/tail splits of every node's coordinates come from the
+// pass's split arrays (a.fin, written by the pass that wrote the coordinates,
+// a.fout for this pass's output) instead of being recomputed at every visit
+// of a neighbour; the splits are a function of the coordinate bits alone, so
+// the screen sees the same floats either way.
+template <bool CACHED>
+__device__ __forceinline__ Split4 node_split(const PassArgs &a, uint32_t id, unsigned long long bx,
+                                             unsigned long long by)
+{
+    if (CACHED) {
+        const float4 f = __ldg(a.fin + id);
+        return Split4{f.x, f.y, f.z, f.w};
+    }
+    return split4(bx, by);
+}
+
+template <bool CACHED>
+__device__ __forceinline__ void put_split(const PassArgs &a, int64_t i, const Split4 &s)
+{
+    if (CACHED) a.fout[i] = make_float4(s.hx, s.tx, s.hy, s.ty);
+}
+
+template <int LAYOUT, bool CACHED>
 __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_t i, float2 *loc, int nthr,
                                             Deferred &d, unsigned long long &best, unsigned long long &nacc,
                                             uint32_t &res)
@@ -97,19 +120,21 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     const uint32_t dmax = __reduce_max_sync(0xffffffffu, act ? deg : 0u);
 
     ulonglong2 pb = make_ulonglong2(0ull, 0ull), v0 = make_ulonglong2(0ull, 0ull);
+    Split4 P = {0.0f, 0.0f, 0.0f, 0.0f}, S0 = {0.0f, 0.0f, 0.0f, 0.0f};
     if (act) {
+        const uint32_t id0 = __ldg(nb);
         pb = CoordBits<LAYOUT>::get(a.in, a.n, i);
-        v0 = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb));
+        v0 = CoordBits<LAYOUT>::get(a.in, a.n, id0);
+        P = node_split<CACHED>(a, (uint32_t)i, pb.x, pb.y);
+        S0 = node_split<CACHED>(a, id0, v0.x, v0.y);
     }
-    float phx, plx, phy, ply;
-    bool ok = head_tail(pb.x, phx, plx) & head_tail(pb.y, phy, ply);
+    const float phx = P.hx, plx = P.tx, phy = P.hy, ply = P.ty;
+    bool ok = !isnan(phx);
     unsigned long long sxb = v0.x, syb = v0.y;
     float rn = 0.0f, rmin = FLT_MAX;
     {
-        float2 L;
-        bool ok0;
-        local_offset(v0.x, v0.y, phx, plx, phy, ply, L.x, L.y, ok0);
-        ok = ok & ok0;
+        const float2 L = make_float2((S0.hx - phx) + (S0.tx - plx), (S0.hy - phy) + (S0.ty - ply));
+        ok = ok & !isnan(S0.hx);
         if (act) loc[0] = L;
         const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
         rn = rl;
@@ -124,6 +149,12 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         for (int u = 0; u < 4; ++u)
             v[u] = (act && k0 + u < deg) ? CoordBits<LAYOUT>::get(a.in, a.n, id[u])
                                          : make_ulonglong2(0x8000000000000000ull, 0x8000000000000000ull);
+        float4 f[4];
+        if (CACHED) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                f[u] = (act && k0 + u < deg) ? __ldg(a.fin + id[u]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t k = k0 + (uint32_t)u;
@@ -132,9 +163,9 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                 // x + (-0) == x for every x: lanes past their degree add -0
                 sxb = dbits(__dadd_rn(bitsd(sxb), bitsd(v[u].x)));
                 syb = dbits(__dadd_rn(bitsd(syb), bitsd(v[u].y)));
-                float2 L;
-                bool okk;
-                local_offset(v[u].x, v[u].y, phx, plx, phy, ply, L.x, L.y, okk);
+                const Split4 S = CACHED ? Split4{f[u].x, f[u].y, f[u].z, f[u].w} : split4(v[u].x, v[u].y);
+                const float2 L = make_float2((S.hx - phx) + (S.tx - plx), (S.hy - phy) + (S.ty - ply));
+                const bool okk = !isnan(S.hx);
                 if (on) loc[k * nthr] = L;
                 const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
                 rn = on ? fmaxf(rn, rl) : rn;
@@ -155,6 +186,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         // the centre is the node itself: q_new == q_old exactly
         const bool acc = !a.strict;
         CoordBits<LAYOUT>::put(a.out, a.n, i, pb);
+        put_split<CACHED>(a, i, P);
         if (a.accept) a.accept[i] = acc ? 1 : 0;
         nacc += acc ? 1ull : 0ull;
         res = acc ? 1u : 0u;
@@ -267,6 +299,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         res = 3u;  // the centre differs from the node (equal centres return above)
     }
     CoordBits<LAYOUT>::put(a.out, a.n, i, outp);
+    if (CACHED) put_split<CACHED>(a, i, acc ? split4(cbx, cby) : P);
     if (a.accept) a.accept[i] = acc ? 1 : 0;
     return false;
 }
@@ -318,9 +351,13 @@ __device__ __forceinline__ void warp_flush_stats(PassStats *st, unsigned long lo
     }
 }
 
-template <int LAYOUT>
-// 128 threads, 7 blocks per SM: 28 warps per SM (72 registers a thread).
-__global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
+#ifndef SLS_CACHED_BLOCKS
+#define SLS_CACHED_BLOCKS 6
+#endif
+template <int LAYOUT, bool CACHED>
+// 128 threads, 7 blocks per SM: 28 warps per SM (72 registers a thread);
+// with the split cache SLS_CACHED_BLOCKS blocks.
+__global__ void __launch_bounds__(128, CACHED ? SLS_CACHED_BLOCKS : 7) pass_screened_kernel(PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;
@@ -361,7 +398,7 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
         Deferred d;
         const bool have = j < cnt;
         uint32_t res;
-        const bool defer = screen_node<LAYOUT>(a, have, have ? (a.order ? (int64_t)__ldg(a.order + j) : j) : 0,
+        const bool defer = screen_node<LAYOUT, CACHED>(a, have, have ? (a.order ? (int64_t)__ldg(a.order + j) : j) : 0,
                                                loc, nthr, d, best, nacc, res);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (a.halo) {  // before any drain: deferred nodes add their bits there
@@ -387,15 +424,19 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
 }
 
 // ---- batched / served form: many meshes, one launch per round -----------
-// Work is a list of warp tasks (32 consecutive nodes of one job).  Each warp
-// walks a contiguous chunk of tasks; a job takes part in round r as its pass
-// q = r - base_round while q < max_iter and its tolerance is not met.  The
-// deferred queue is drained and the statistics flushed whenever the warp
-// moves to another job, so every record gets exactly its own job's counts.
+// Work is a list of warp tasks (32 consecutive nodes of one job).  The warps
+// take chunks of `chunk` consecutive tasks in a grid stride (warp w: chunks
+// w, w + W, w + 2W, ...), so that at any moment they work on a window of
+// neighbouring tasks and share its gathers in L1 and L2; chunk = 0 gives
+// each warp one contiguous share of the list instead.  A job takes part in
+// round r as its pass q = r - base_round while q < max_iter and its
+// tolerance is not met.  The deferred queue is drained and the statistics
+// flushed whenever the warp moves to another job, so every record gets
+// exactly its own job's counts.
 template <int LAYOUT>
 __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__restrict__ jobs,
                                                           const WarpTask *__restrict__ tasks, int64_t ntasks,
-                                                          int round)
+                                                          int round, int64_t chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;
@@ -407,16 +448,23 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
 
     const int64_t nwarps = (int64_t)gridDim.x * (nthr >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (nthr >> 5) + warp;
-    const int64_t per = (ntasks + nwarps - 1) / nwarps;
-    const int64_t t0 = gw * per, t1 = t0 + per < ntasks ? t0 + per : ntasks;
+    const int64_t per = chunk > 0 ? chunk : (ntasks + nwarps - 1) / nwarps;
+    const int64_t cstride = chunk > 0 ? nwarps * chunk : ntasks;  // one share per warp when chunk == 0
+    int64_t c0 = gw * per;                                       // first task of the current chunk
+    int64_t t = c0;
 
     int cur_job = -1;
     bool active = false;
     PassArgs a{};
     unsigned long long best = 0ull, nacc = 0ull, nfb = 0ull;
     int qn = 0;
-    for (int64_t t = t0; t <= t1; ++t) {
-        const int job = t < t1 ? tasks[t].job : -2;
+    for (;;) {
+        if (t >= c0 + per || t >= ntasks) {  // next chunk of this warp
+            c0 += cstride;
+            t = c0;
+        }
+        const bool more = t < ntasks && c0 < ntasks;
+        const int job = more ? tasks[t].job : -2;
         if (job != cur_job) {
             if (cur_job >= 0 && active) {
                 __syncwarp();
@@ -450,13 +498,17 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
                 a.accept = J->accept;
             }
         }
-        if (!active) continue;
+        if (!active) {
+            ++t;
+            continue;
+        }
         const int64_t first = tasks[t].first;
+        ++t;
         if (first == 0 && lane == 0) a.stats[a.q].executed = 1u;
         const int64_t i = first + lane;
         Deferred d;
         uint32_t res;
-        const bool defer = screen_node<LAYOUT>(a, i < a.n, i < a.n ? i : 0, loc, nthr, d, best, nacc, res);
+        const bool defer = screen_node<LAYOUT, false>(a, i < a.n, i < a.n ? i : 0, loc, nthr, d, best, nacc, res);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
@@ -497,8 +549,9 @@ cudaError_t ensure_constants()
     e = cudaMemcpyToSymbol(c_recip, r, sizeof r);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_degree, dg, sizeof dg);
     if (e != cudaSuccess) return e;
-    const void *fns[4] = {(const void *)pass_screened_kernel<0>, (const void *)pass_screened_kernel<1>,
-                          (const void *)batch_pass_kernel<0>, (const void *)batch_pass_kernel<1>};
+    const void *fns[6] = {(const void *)pass_screened_kernel<0, false>, (const void *)pass_screened_kernel<1, false>,
+                          (const void *)pass_screened_kernel<0, true>,  (const void *)pass_screened_kernel<1, true>,
+                          (const void *)batch_pass_kernel<0>,           (const void *)batch_pass_kernel<1>};
     for (const void *f : fns) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
@@ -508,6 +561,30 @@ cudaError_t ensure_constants()
 }
 
 }  // namespace
+
+namespace {
+
+// The screen's head/tail splits of every node's coordinates.
+template <int LAYOUT>
+__global__ void splits_kernel(const double *__restrict__ xy, int64_t n, float4 *__restrict__ out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const ulonglong2 b = CoordBits<LAYOUT>::get(xy, n, i);
+        const Split4 s = split4(b.x, b.y);
+        out[i] = make_float4(s.hx, s.tx, s.hy, s.ty);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_splits(const double *xy, int layout, int64_t n, float4 *out, int grid, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (layout == 0) splits_kernel<0><<<grid, 256, 0, s>>>(xy, n, out);
+    else splits_kernel<1><<<grid, 256, 0, s>>>(xy, n, out);
+    return cudaGetLastError();
+}
 
 size_t screened_smem_bytes(int block)
 {
@@ -519,20 +596,26 @@ cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int g
     cudaError_t e = ensure_constants();
     if (e != cudaSuccess) return e;
     const size_t smem = screened_smem_bytes(block);
-    if (layout == 0) pass_screened_kernel<0><<<grid, block, smem, s>>>(a);
-    else pass_screened_kernel<1><<<grid, block, smem, s>>>(a);
+    const bool cached = a.fin != nullptr;
+    if (layout == 0) {
+        if (cached) pass_screened_kernel<0, true><<<grid, block, smem, s>>>(a);
+        else pass_screened_kernel<0, false><<<grid, block, smem, s>>>(a);
+    } else {
+        if (cached) pass_screened_kernel<1, true><<<grid, block, smem, s>>>(a);
+        else pass_screened_kernel<1, false><<<grid, block, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_pass(const JobDesc *jobs, const WarpTask *tasks, int64_t ntasks, int round,
-                              int layout, int block, int grid, cudaStream_t s)
+                              int layout, int block, int grid, cudaStream_t s, int64_t chunk)
 {
     cudaError_t e = ensure_constants();
     if (e != cudaSuccess) return e;
     if (ntasks <= 0) return cudaSuccess;
     const size_t smem = screened_smem_bytes(block);
-    if (layout == 0) batch_pass_kernel<0><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round);
-    else batch_pass_kernel<1><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round);
+    if (layout == 0) batch_pass_kernel<0><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round, chunk);
+    else batch_pass_kernel<1><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round, chunk);
     return cudaGetLastError();
 }
 
@@ -576,9 +659,9 @@ int pass_screened_occupancy(int layout, int block)
     int nb = 0;
     const size_t smem = screened_smem_bytes(block);
     if (layout == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_screened_kernel<0>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_screened_kernel<0, true>, block, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_screened_kernel<1>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_screened_kernel<1, true>, block, smem);
     return nb > 0 ? nb : 1;
 }
 

@@ -39,6 +39,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kBuilders = 4;  // builder threads (and streams) per server
+constexpr int64_t kServerChunk = 4;  // tasks per warp chunk of a round (grid stride)
 
 enum JobState { kQueued, kBuilding, kActive, kRetiring, kDone, kFailed };
 
@@ -89,6 +90,7 @@ struct sls_server {
     std::vector<std::shared_ptr<ServerJob>> uploading, active;
     std::unordered_map<uint64_t, std::shared_ptr<ServerJob>> jobs;
     uint64_t next_id = 1;
+    int64_t holding = 0;  // jobs whose inputs are still on the host (submitted, not yet built)
     bool stop = false, retire_stop = false;
     int builders_live = 0;
     std::vector<std::thread> builders;
@@ -241,10 +243,13 @@ void builder_loop(sls_server *S, cudaStream_t s)
         const sls_status st = build_job(*J, s, &fp);
         const std::string err = st == SLS_OK ? std::string() : std::string(sls_last_error());
         std::lock_guard<std::mutex> lk(S->mu);
+        J->xy.clear();
+        J->xy.shrink_to_fit();
         J->tri.clear();
         J->tri.shrink_to_fit();
         J->boundary.clear();
         J->boundary.shrink_to_fit();
+        S->holding -= 1;
         if (st == SLS_OK) {
             S->used = S->used - J->reserved + fp;  // the scratch and the bound's slack return
             J->reserved = fp;
@@ -423,8 +428,6 @@ void scheduler_loop(sls_server *S)
             }
             {
                 std::lock_guard<std::mutex> lk(S->mu);
-                J->xy.clear();
-                J->xy.shrink_to_fit();
                 J->base_round = S->round;
                 J->state = kActive;
             }
@@ -447,7 +450,7 @@ void scheduler_loop(sls_server *S)
         }
         const auto t0 = Clock::now();
         cudaError_t e = launch_batch_pass(S->d_jobs, S->d_tasks, S->ntasks, S->round, S->opt.layout, S->block,
-                                          S->grid, S->stream);
+                                          S->grid, S->stream, kServerChunk);
         // every job's record of this round, gathered by one kernel, read back by one copy
         if (e == cudaSuccess) e = launch_gather_round(S->d_jobs, (int)na, S->round, S->d_round, S->stream);
         if (e == cudaSuccess)
@@ -606,8 +609,9 @@ sls_status sls_submit(sls_server *S, const double *xy, int64_t n, const int32_t 
     J->tol = tol_rel;
     J->reserved = admission_bound(n, m, max_iter);
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->max_queue > 0 && (int64_t)(S->to_build.size() + S->queued.size()) >= S->max_queue)
+    if (S->max_queue > 0 && S->holding >= S->max_queue)
         return fail(SLS_ERR_BUSY, "server queue is full");
+    S->holding += 1;
     J->id = S->next_id++;
     S->jobs[J->id] = J;
     S->queued.push_back(J);
