@@ -36,8 +36,6 @@ struct sls_mesh {
     size_t l2_persist = 0;        // l2_window: persisting L2 bytes set aside for this context
     size_t l2_win_max = 0;        //            largest access-policy window the device accepts
     unsigned *xfer_bad = nullptr; // gather/scatter: set when an id was out of range
-    float4 *split[2] = {nullptr, nullptr};  // the screen's head/tail splits of xy[0], xy[1] (headline path)
-    bool split_ok = false;        // whether split[] describe xy[] (refreshed before a pass when not)
     int block = 256, grid = 0;
     bool screened = true;         // screened kernel (else the plain FP64 kernel)
     sls_info last{};
@@ -88,9 +86,6 @@ sls_status build_node_order(sls_mesh *M, cudaStream_t s);
 // when opt.skip_unchanged is set.
 sls_status build_tile_halo(sls_mesh *M, cudaStream_t s);
 void mesh_release(sls_mesh *M);
-// Recomputes the screen's split arrays from both coordinate arrays when the
-// mesh keeps them and they may be stale (after coordinates changed outside a pass).
-sls_status mesh_refresh_splits(sls_mesh *M);
 sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info);
 sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device);
 sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device);

@@ -145,7 +145,6 @@ sls_status run(sls_batch *B, sls_info *infos)
             info.converged = (tol > 0.0 && st[it - 1].maxd2_bits < thr_bits) ? 1 : 0;
         }
         M->cur ^= (it & 1);
-        M->split_ok = false;  // the batch kernel keeps no screen splits
         M->last = info;
         if (infos) infos[mi] = info;
     }
@@ -160,7 +159,6 @@ sls_status reset(sls_batch *B)
         BATCH_TRY(cudaMemcpyAsync(M->xy[0], B->d_start[mi], cbytes, cudaMemcpyDeviceToDevice, B->stream), "reset");
         BATCH_TRY(cudaMemcpyAsync(M->xy[1], B->d_start[mi], cbytes, cudaMemcpyDeviceToDevice, B->stream), "reset");
         M->cur = 0;
-        M->split_ok = false;
     }
     BATCH_TRY(cudaStreamSynchronize(B->stream), "reset");
     return SLS_OK;

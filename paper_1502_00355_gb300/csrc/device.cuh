@@ -31,12 +31,6 @@ struct PassArgs {
     int tol_active;            // 1: skip the pass when pass q-1 met the tolerance or was skipped
     unsigned long long thr_bits;  // bits of (tol * D)^2
     uint8_t *accept;           // n decisions, or nullptr
-    // The screen's head/tail splits of every node's coordinates in `in`
-    // (x head, x tail, y head, y tail; head NaN where a split is invalid),
-    // and where the pass writes those of `out`; both null when the mesh
-    // keeps no splits (they are then computed per neighbour visit).
-    const float4 *fin;
-    float4 *fout;
     // Skipping of unchanged tiles (tiles of 32 consecutive nodes; all null
     // and skip = 0 when the mesh does not use it).  A tile whose nodes and
     // whose nodes' neighbours all kept their coordinates in the previous pass

@@ -19,9 +19,6 @@ int pass_fp64_occupancy(int layout, int block);
 // screen cannot decide (bit-identical results).
 cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int grid, cudaStream_t s);
 int pass_screened_occupancy(int layout, int block);
-// The screen's head/tail splits (x head, x tail, y head, y tail) of every
-// node's coordinates in xy, for a pass with a.fin / a.fout.
-cudaError_t launch_splits(const double *xy, int layout, int64_t n, float4 *out, int grid, cudaStream_t s);
 
 // One round of the batched / served form over all active jobs' tasks.
 // chunk: tasks per warp chunk, taken in a grid stride; 0 = one contiguous
@@ -57,14 +54,11 @@ cudaError_t launch_widen(const float *src, double *aos, int64_t n, int layout, i
 
 // Ghost exchange of a domain-decomposed mesh: the listed nodes' coordinates
 // (interleaved out / in, 2k doubles) from the current array, or into both
-// arrays (and, when sp0 / sp1 are given, the screen's splits of the new
-// coordinates into both split arrays); an id outside [0, n) sets *bad and is
-// skipped.
+// arrays; an id outside [0, n) sets *bad and is skipped.
 cudaError_t launch_gather_nodes(const double *xy, int layout, int64_t n, const int32_t *idx, int64_t k,
                                 double *out, unsigned *bad, int grid, cudaStream_t s);
 cudaError_t launch_scatter_nodes(double *xy0, double *xy1, int layout, int64_t n, const int32_t *idx, int64_t k,
-                                 const double *in, unsigned *bad, float4 *sp0, float4 *sp1, int grid,
-                                 cudaStream_t s);
+                                 const double *in, unsigned *bad, int grid, cudaStream_t s);
 
 // Layout conversions on the device (SoA <-> interleaved).
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int64_t n, int grid, cudaStream_t s);

@@ -76,14 +76,6 @@ static sls_status mesh_setup(sls_mesh *M, const sls_options &o)
     }
     sls_status pst = noalloc_prepare();
     if (pst != SLS_OK) return pst;
-    // The screened FP64 Form-A ping-pong pass keeps every node's head/tail
-    // splits beside its coordinates (32 bytes per node for the two arrays):
-    // each split is then computed once per pass instead of at every visit.
-    if (M->screened && !M->f32 && o.form == 0 && !o.copy_back)
-        for (int b = 0; b < 2; ++b)
-            if ((pst = dev_alloc((void **)&M->split[b], sizeof(float4) * (size_t)M->n, "screen splits")) != SLS_OK)
-                return pst;
-    M->split_ok = false;
     M->grid = device_sm_count() * (M->f32        ? pass_f32_occupancy(o.layout, M->block)
                                    : M->screened ? pass_screened_occupancy(o.layout, M->block)
                                                  : pass_fp64_occupancy(o.layout, M->block));
@@ -220,8 +212,6 @@ void mesh_release(sls_mesh *M)
     cudaFree(M->chg[1]);
     cudaFree(M->accm);
     cudaFree(M->xfer_bad);
-    cudaFree(M->split[0]);
-    cudaFree(M->split[1]);
     if (M->h_stats) cudaFreeHost(M->h_stats);
     if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
     M->stream = nullptr;
@@ -251,22 +241,10 @@ static cudaError_t launch_pass(const sls_mesh *M, const PassArgs &a)
                        : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream);
 }
 
-sls_status mesh_refresh_splits(sls_mesh *M)
-{
-    if (!M->split[0] || M->split_ok) return SLS_OK;
-    const int grid = device_sm_count() * 4;
-    for (int b = 0; b < 2; ++b)
-        SLS_CUDA_TRY(launch_splits(M->xy[b], M->opt.layout, M->n, M->split[b], grid, M->stream), "screen splits");
-    M->split_ok = true;
-    return SLS_OK;
-}
-
 sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info)
 {
     info = sls_info{};
     if (max_iter == 0) return SLS_OK;
-    sls_status sst = mesh_refresh_splits(M);
-    if (sst != SLS_OK) return sst;
     if (M->stats_cap < max_iter) {
         cudaStreamSynchronize(M->stream);
         cudaFree(M->stats);
@@ -322,8 +300,6 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
             const int src = cb ? M->cur : (M->cur ^ (q & 1));
             a.in = M->xy[src];
             a.out = M->xy[src ^ 1];
-            a.fin = M->split[src];  // null when the mesh keeps no splits
-            a.fout = M->split[src ^ 1];
             a.order = nullptr;
             a.norder = 0;
             if (M->halo) {  // unchanged-tile skipping from the second pass of a call on
@@ -422,7 +398,6 @@ sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device)
 
 sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
 {
-    M->split_ok = false;
     if (M->f32) {
         const size_t fbytes = sizeof(float) * 2 * (size_t)M->n;
         float *f = reinterpret_cast<float *>(M->xy[M->cur]);
@@ -476,7 +451,6 @@ sls_status mesh_transfer_nodes(sls_mesh *M, const int32_t *idx, int64_t k, doubl
     SLS_CUDA_TRY(cudaMemsetAsync(M->xfer_bad, 0, sizeof(unsigned), M->stream), "transfer");
     if (scatter)
         SLS_CUDA_TRY(launch_scatter_nodes(M->xy[0], M->xy[1], M->opt.layout, M->n, idx, k, buf, M->xfer_bad,
-                                          M->split_ok ? M->split[0] : nullptr, M->split_ok ? M->split[1] : nullptr,
                                           grid, M->stream), "scatter");
     else
         SLS_CUDA_TRY(launch_gather_nodes(M->xy[M->cur], M->opt.layout, M->n, idx, k, buf, M->xfer_bad, grid,

@@ -5,7 +5,6 @@
 #pragma once
 
 #include "device.cuh"
-#include "screen.cuh"
 
 namespace sls {
 
@@ -114,11 +113,6 @@ __device__ __forceinline__ void exact_update(const PassArgs &a, int64_t i, uint3
         o = make_double2(cx, cy);
     }
     Coords<LAYOUT>::put(a.out, a.n, i, o);
-    if (a.fout) {
-        const scr::Split4 s = scr::split4((unsigned long long)__double_as_longlong(o.x),
-                                          (unsigned long long)__double_as_longlong(o.y));
-        a.fout[i] = make_float4(s.hx, s.tx, s.hy, s.ty);
-    }
     if (a.accept) a.accept[i] = ok ? 1 : 0;
     accepted = ok;
 }

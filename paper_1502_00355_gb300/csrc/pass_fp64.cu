@@ -12,7 +12,6 @@
 // The FP64 pipe of GB300 is narrow, so this kernel is the exact baseline and
 // the fallback of the screened kernel, not the fast path.
 #include "kernels.h"
-#include "screen.cuh"
 #include "node_exact.cuh"
 
 namespace sls {
@@ -178,8 +177,7 @@ __global__ void gather_nodes_kernel(const double *__restrict__ xy, int64_t n, co
 // The listed nodes' coordinates written into both arrays of the ping-pong.
 template <int LAYOUT>
 __global__ void scatter_nodes_kernel(double *xy0, double *xy1, int64_t n, const int32_t *__restrict__ idx,
-                                     int64_t k, const double2 *__restrict__ in, unsigned *bad, float4 *sp0,
-                                     float4 *sp1)
+                                     int64_t k, const double2 *__restrict__ in, unsigned *bad)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += stride) {
@@ -191,11 +189,6 @@ __global__ void scatter_nodes_kernel(double *xy0, double *xy1, int64_t n, const 
         const double2 v = __ldg(in + t);
         Coords<LAYOUT>::put(xy0, n, i, v);
         Coords<LAYOUT>::put(xy1, n, i, v);
-        if (sp0) {  // the screen's splits of the new coordinates
-            const scr::Split4 s = scr::split4((unsigned long long)__double_as_longlong(v.x),
-                                              (unsigned long long)__double_as_longlong(v.y));
-            sp0[i] = sp1[i] = make_float4(s.hx, s.tx, s.hy, s.ty);
-        }
     }
 }
 
@@ -213,14 +206,14 @@ cudaError_t launch_gather_nodes(const double *xy, int layout, int64_t n, const i
 }
 
 cudaError_t launch_scatter_nodes(double *xy0, double *xy1, int layout, int64_t n, const int32_t *idx, int64_t k,
-                                 const double *in, unsigned *bad, float4 *sp0, float4 *sp1, int grid, cudaStream_t s)
+                                 const double *in, unsigned *bad, int grid, cudaStream_t s)
 {
     if (k <= 0) return cudaSuccess;
     const double2 *v = reinterpret_cast<const double2 *>(in);
     if (layout == 0)
-        scatter_nodes_kernel<0><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, v, bad, sp0, sp1);
+        scatter_nodes_kernel<0><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, v, bad);
     else
-        scatter_nodes_kernel<1><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, v, bad, sp0, sp1);
+        scatter_nodes_kernel<1><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, v, bad);
     return cudaGetLastError();
 }
 

@@ -71,30 +71,7 @@ using namespace scr;
 // grows with |a| and g, so the side's largest |a|, its largest local
 // coordinate R (every vertex of every triangle of that side lies within it)
 // and its smallest edge sum s bound every triangle at once.
-//
-// With CACHED the head/tail splits of every node's coordinates come from the
-// pass's split arrays (a.fin, written by the pass that wrote the coordinates,
-// a.fout for this pass's output) instead of being recomputed at every visit
-// of a neighbour; the splits are a function of the coordinate bits alone, so
-// the screen sees the same floats either way.
-template <bool CACHED>
-__device__ __forceinline__ Split4 node_split(const PassArgs &a, uint32_t id, unsigned long long bx,
-                                             unsigned long long by)
-{
-    if (CACHED) {
-        const float4 f = __ldg(a.fin + id);
-        return Split4{f.x, f.y, f.z, f.w};
-    }
-    return split4(bx, by);
-}
-
-template <bool CACHED>
-__device__ __forceinline__ void put_split(const PassArgs &a, int64_t i, const Split4 &s)
-{
-    if (CACHED) a.fout[i] = make_float4(s.hx, s.tx, s.hy, s.ty);
-}
-
-template <int LAYOUT, bool CACHED>
+template <int LAYOUT>
 __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_t i, float2 *loc, int nthr,
                                             Deferred &d, unsigned long long &best, unsigned long long &nacc,
                                             uint32_t &res)
@@ -120,21 +97,19 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     const uint32_t dmax = __reduce_max_sync(0xffffffffu, act ? deg : 0u);
 
     ulonglong2 pb = make_ulonglong2(0ull, 0ull), v0 = make_ulonglong2(0ull, 0ull);
-    Split4 P = {0.0f, 0.0f, 0.0f, 0.0f}, S0 = {0.0f, 0.0f, 0.0f, 0.0f};
     if (act) {
-        const uint32_t id0 = __ldg(nb);
         pb = CoordBits<LAYOUT>::get(a.in, a.n, i);
-        v0 = CoordBits<LAYOUT>::get(a.in, a.n, id0);
-        P = node_split<CACHED>(a, (uint32_t)i, pb.x, pb.y);
-        S0 = node_split<CACHED>(a, id0, v0.x, v0.y);
+        v0 = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb));
     }
-    const float phx = P.hx, plx = P.tx, phy = P.hy, ply = P.ty;
-    bool ok = !isnan(phx);
+    float phx, plx, phy, ply;
+    bool ok = head_tail(pb.x, phx, plx) & head_tail(pb.y, phy, ply);
     unsigned long long sxb = v0.x, syb = v0.y;
     float rn = 0.0f, rmin = FLT_MAX;
     {
-        const float2 L = make_float2((S0.hx - phx) + (S0.tx - plx), (S0.hy - phy) + (S0.ty - ply));
-        ok = ok & !isnan(S0.hx);
+        float2 L;
+        bool ok0;
+        local_offset(v0.x, v0.y, phx, plx, phy, ply, L.x, L.y, ok0);
+        ok = ok & ok0;
         if (act) loc[0] = L;
         const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
         rn = rl;
@@ -149,12 +124,6 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         for (int u = 0; u < 4; ++u)
             v[u] = (act && k0 + u < deg) ? CoordBits<LAYOUT>::get(a.in, a.n, id[u])
                                          : make_ulonglong2(0x8000000000000000ull, 0x8000000000000000ull);
-        float4 f[4];
-        if (CACHED) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                f[u] = (act && k0 + u < deg) ? __ldg(a.fin + id[u]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t k = k0 + (uint32_t)u;
@@ -163,9 +132,9 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
                 // x + (-0) == x for every x: lanes past their degree add -0
                 sxb = dbits(__dadd_rn(bitsd(sxb), bitsd(v[u].x)));
                 syb = dbits(__dadd_rn(bitsd(syb), bitsd(v[u].y)));
-                const Split4 S = CACHED ? Split4{f[u].x, f[u].y, f[u].z, f[u].w} : split4(v[u].x, v[u].y);
-                const float2 L = make_float2((S.hx - phx) + (S.tx - plx), (S.hy - phy) + (S.ty - ply));
-                const bool okk = !isnan(S.hx);
+                float2 L;
+                bool okk;
+                local_offset(v[u].x, v[u].y, phx, plx, phy, ply, L.x, L.y, okk);
                 if (on) loc[k * nthr] = L;
                 const float rl = fmaxf(fabsf(L.x), fabsf(L.y));
                 rn = on ? fmaxf(rn, rl) : rn;
@@ -186,7 +155,6 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         // the centre is the node itself: q_new == q_old exactly
         const bool acc = !a.strict;
         CoordBits<LAYOUT>::put(a.out, a.n, i, pb);
-        put_split<CACHED>(a, i, P);
         if (a.accept) a.accept[i] = acc ? 1 : 0;
         nacc += acc ? 1ull : 0ull;
         res = acc ? 1u : 0u;
@@ -299,7 +267,6 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         res = 3u;  // the centre differs from the node (equal centres return above)
     }
     CoordBits<LAYOUT>::put(a.out, a.n, i, outp);
-    if (CACHED) put_split<CACHED>(a, i, acc ? split4(cbx, cby) : P);
     if (a.accept) a.accept[i] = acc ? 1 : 0;
     return false;
 }
@@ -351,13 +318,9 @@ __device__ __forceinline__ void warp_flush_stats(PassStats *st, unsigned long lo
     }
 }
 
-#ifndef SLS_CACHED_BLOCKS
-#define SLS_CACHED_BLOCKS 6
-#endif
-template <int LAYOUT, bool CACHED>
-// 128 threads, 7 blocks per SM: 28 warps per SM (72 registers a thread);
-// with the split cache SLS_CACHED_BLOCKS blocks.
-__global__ void __launch_bounds__(128, CACHED ? SLS_CACHED_BLOCKS : 7) pass_screened_kernel(PassArgs a)
+template <int LAYOUT>
+// 128 threads, 7 blocks per SM: 28 warps per SM (72 registers a thread).
+__global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;
@@ -398,7 +361,7 @@ __global__ void __launch_bounds__(128, CACHED ? SLS_CACHED_BLOCKS : 7) pass_scre
         Deferred d;
         const bool have = j < cnt;
         uint32_t res;
-        const bool defer = screen_node<LAYOUT, CACHED>(a, have, have ? (a.order ? (int64_t)__ldg(a.order + j) : j) : 0,
+        const bool defer = screen_node<LAYOUT>(a, have, have ? (a.order ? (int64_t)__ldg(a.order + j) : j) : 0,
                                                loc, nthr, d, best, nacc, res);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (a.halo) {  // before any drain: deferred nodes add their bits there
@@ -508,7 +471,7 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
         const int64_t i = first + lane;
         Deferred d;
         uint32_t res;
-        const bool defer = screen_node<LAYOUT, false>(a, i < a.n, i < a.n ? i : 0, loc, nthr, d, best, nacc, res);
+        const bool defer = screen_node<LAYOUT>(a, i < a.n, i < a.n ? i : 0, loc, nthr, d, best, nacc, res);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
@@ -549,9 +512,8 @@ cudaError_t ensure_constants()
     e = cudaMemcpyToSymbol(c_recip, r, sizeof r);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_degree, dg, sizeof dg);
     if (e != cudaSuccess) return e;
-    const void *fns[6] = {(const void *)pass_screened_kernel<0, false>, (const void *)pass_screened_kernel<1, false>,
-                          (const void *)pass_screened_kernel<0, true>,  (const void *)pass_screened_kernel<1, true>,
-                          (const void *)batch_pass_kernel<0>,           (const void *)batch_pass_kernel<1>};
+    const void *fns[4] = {(const void *)pass_screened_kernel<0>, (const void *)pass_screened_kernel<1>,
+                          (const void *)batch_pass_kernel<0>, (const void *)batch_pass_kernel<1>};
     for (const void *f : fns) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
@@ -561,30 +523,6 @@ cudaError_t ensure_constants()
 }
 
 }  // namespace
-
-namespace {
-
-// The screen's head/tail splits of every node's coordinates.
-template <int LAYOUT>
-__global__ void splits_kernel(const double *__restrict__ xy, int64_t n, float4 *__restrict__ out)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const ulonglong2 b = CoordBits<LAYOUT>::get(xy, n, i);
-        const Split4 s = split4(b.x, b.y);
-        out[i] = make_float4(s.hx, s.tx, s.hy, s.ty);
-    }
-}
-
-}  // namespace
-
-cudaError_t launch_splits(const double *xy, int layout, int64_t n, float4 *out, int grid, cudaStream_t s)
-{
-    if (n <= 0) return cudaSuccess;
-    if (layout == 0) splits_kernel<0><<<grid, 256, 0, s>>>(xy, n, out);
-    else splits_kernel<1><<<grid, 256, 0, s>>>(xy, n, out);
-    return cudaGetLastError();
-}
 
 size_t screened_smem_bytes(int block)
 {
@@ -596,14 +534,8 @@ cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int g
     cudaError_t e = ensure_constants();
     if (e != cudaSuccess) return e;
     const size_t smem = screened_smem_bytes(block);
-    const bool cached = a.fin != nullptr;
-    if (layout == 0) {
-        if (cached) pass_screened_kernel<0, true><<<grid, block, smem, s>>>(a);
-        else pass_screened_kernel<0, false><<<grid, block, smem, s>>>(a);
-    } else {
-        if (cached) pass_screened_kernel<1, true><<<grid, block, smem, s>>>(a);
-        else pass_screened_kernel<1, false><<<grid, block, smem, s>>>(a);
-    }
+    if (layout == 0) pass_screened_kernel<0><<<grid, block, smem, s>>>(a);
+    else pass_screened_kernel<1><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -659,9 +591,9 @@ int pass_screened_occupancy(int layout, int block)
     int nb = 0;
     const size_t smem = screened_smem_bytes(block);
     if (layout == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_screened_kernel<0, true>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_screened_kernel<0>, block, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_screened_kernel<1, true>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_screened_kernel<1>, block, smem);
     return nb > 0 ? nb : 1;
 }
 

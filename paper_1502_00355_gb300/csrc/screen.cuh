@@ -82,20 +82,6 @@ SLS_SC_HD bool head_tail(unsigned long long b, float &hd, float &tl)
     return zero || (e - 943u <= 206u);  // [2^-80, 2^127) in magnitude, normal
 }
 
-// Splits of both coordinates of a node, (hx, tx, hy, ty), as the screen's
-// cache stores them: hx is a quiet NaN when either split is invalid.
-struct Split4 {
-    float hx, tx, hy, ty;
-};
-
-SLS_SC_HD Split4 split4(unsigned long long bx, unsigned long long by)
-{
-    Split4 s;
-    const bool ok = head_tail(bx, s.hx, s.tx) & head_tail(by, s.hy, s.ty);
-    if (!ok) s.hx = u2f(0x7fc00000u);
-    return s;
-}
-
 // FP32 value of a double, truncated to 24 significant bits (relative error
 // below 2^-23), built with integer operations; zero outside the float range.
 SLS_SC_HD float trunc_float(unsigned long long b)
