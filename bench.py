@@ -42,15 +42,15 @@ CSRC = os.path.join(ROOT, "paper_1502_00355_gb300", "csrc")
 # figures no longer describe the kernel and the bench line reports null.
 PROFILE_FIGURES = {
     "pass_screened": {
-        "files": ["pass_screened.cu", "node_exact.cuh", "div_small.cuh", "device.cuh"],
-        "sha256": "ca7c0f1638ab409ac1177ac17dc1de9da1207735b7d96b4c388c6504f0bdfa11",
-        "dram_bytes_per_node": 1446.0e6 / (4096 * 4096),
+        "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh"],
+        "sha256": "0c3d8c7e549e6613c97e08adddb98f3712b9aa1c046c25469679437f985dfb1c",
+        "dram_bytes_per_node": 361.5e6 / (2048 * 2048),
         "fp64_warp_inst_per_32_nodes": 19.0 + 5.9 + 1.2,
         "source": "profiles/pass_screened_grid2048.md (2048x2048 capture, per node)",
     },
     "batch_pass": {
-        "files": ["pass_screened.cu", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu"],
-        "sha256": "154332ffda9fea2a17e94257e66af6168c0af30aa0f38c0e5e64821104d63d1e",
+        "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu"],
+        "sha256": None,
         "dram_per_alg_byte": 1078639872 / 994046024,
         "source": "profiles/batch_pass_batch256.md (round 0 of a 256-mesh batch, scaled by algorithmic bytes)",
     },
@@ -388,7 +388,7 @@ def run_batch(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"batch{len(meshes)}_logu1K-256K_aspect1-4_iters10-100",
                       "meshes_per_gpu": len(meshes), "meshes": len(meshes) * world,
-                      "nodes_rank0": total_nodes, "block": None,
+                      "nodes_rank0": total_nodes, "launch_shape": {"block": batch.shape[0], "chunk": batch.shape[1]},
                       "parallelism": f"{world} ranks, independent meshes (no collective)" if world > 1 else "single"},
            "per_request": {"value": per_request, "unit": "node-updates/s", "seconds": per_req_s},
            "speedup_vs_per_request": batched / per_request, "identical_results": bool(same),

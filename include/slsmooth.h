@@ -216,8 +216,9 @@ sls_status sls_mesh_destroy(sls_mesh *mesh);
  * their coordinates in place.  The coordinates at packing time are saved for
  * sls_batch_reset.  The launch shape is autotuned by timing one full batch
  * smooth per candidate, restoring the saved coordinates after each trial:
- * the chunk of consecutive 32-node tasks a warp takes in the grid stride
- * (0 = one contiguous share per warp, 1, 4, 16) and, with opt == NULL or
+ * the chunk of consecutive 32-node tasks a warp takes (1, 4 or 16 in a grid
+ * stride, 2 or 8 claimed in order from a per-round counter, or one contiguous
+ * share of the list per warp) and, with opt == NULL or
  * opt->block_size == 0, the block size (64 or 128 threads); an explicit
  * block_size must be 32, 64, 96 or 128 (SLS_ERR_INVALID otherwise). */
 sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *iters,
@@ -233,6 +234,17 @@ sls_status sls_batch_get_coords(const sls_batch *batch, int32_t j, double *xy_ou
 
 /* Restores every mesh of the batch to the coordinates it had when packed. */
 sls_status sls_batch_reset(sls_batch *batch);
+
+/* The launch shape in use (chosen by the autotuner, or set below): threads
+ * per block and the warp chunk (> 0: tasks per chunk in a grid stride; < 0:
+ * chunks of -chunk tasks claimed in order from a per-round counter; 0: one
+ * contiguous share of the task list per warp).  Either pointer may be NULL. */
+sls_status sls_batch_shape(const sls_batch *batch, int32_t *block, int64_t *chunk);
+
+/* Sets the launch shape (block 32, 64, 96 or 128; |chunk| <= 2^20) for the
+ * following sls_batch_smooth calls, e.g. to repeat a tuned shape without
+ * tuning again.  Results do not depend on the shape. */
+sls_status sls_batch_set_shape(sls_batch *batch, int32_t block, int64_t chunk);
 
 sls_status sls_batch_destroy(sls_batch *batch);
 

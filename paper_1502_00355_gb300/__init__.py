@@ -87,6 +87,8 @@ def lib() -> C.CDLL:
                 "sls_batch_smooth": (S, [P, P]),
                 "sls_batch_get_coords": (S, [P, I32, P]),
                 "sls_batch_reset": (S, [P]),
+                "sls_batch_shape": (S, [P, P, P]),
+                "sls_batch_set_shape": (S, [P, I32, I64]),
                 "sls_batch_destroy": (S, [P]),
                 "sls_server_create": (S, [C.c_size_t, I32, P, PP]),
                 "sls_submit": (S, [P, P, I64, P, I64, P, I32, D, C.POINTER(C.c_uint64)]),
@@ -286,6 +288,16 @@ class Batch:
 
     def reset(self):
         _check(lib().sls_batch_reset(self._h), "sls_batch_reset")
+
+    @property
+    def shape(self) -> tuple[int, int]:
+        """(threads per block, warp chunk) of the launches."""
+        b, c = C.c_int32(), C.c_int64()
+        _check(lib().sls_batch_shape(self._h, C.byref(b), C.byref(c)), "sls_batch_shape")
+        return b.value, c.value
+
+    def set_shape(self, block: int, chunk: int):
+        _check(lib().sls_batch_set_shape(self._h, int(block), int(chunk)), "sls_batch_set_shape")
 
     def close(self):
         if getattr(self, "_h", None) is not None:

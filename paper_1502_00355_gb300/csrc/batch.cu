@@ -38,7 +38,8 @@ struct sls_batch {
     std::vector<double *> d_start;     // per mesh: the packed starting coordinates
     int rounds = 0;
     int block = 128, grid = 0;
-    int64_t chunk = 0;                 // tasks per warp chunk (0: one contiguous share per warp)
+    int64_t chunk = 0;                 // tasks per warp chunk (launch_batch_pass)
+    unsigned long long *d_claim = nullptr;  // one chunk counter per round (dynamic chunks)
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -57,6 +58,7 @@ void release(sls_batch *B)
     cudaFree(B->d_jobs);
     cudaFree(B->d_tasks);
     cudaFree(B->d_stats);
+    cudaFree(B->d_claim);
     if (B->h_jobs) cudaFreeHost(B->h_jobs);
     for (double *p : B->d_start) cudaFree(p);
     if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
@@ -74,7 +76,7 @@ sls_status build_graph(sls_batch *B)
     cudaError_t err = cudaSuccess;
     for (int r = 0; r < B->rounds && err == cudaSuccess; ++r)
         err = launch_batch_pass(B->d_jobs, B->d_tasks, B->round_tasks[r], r, B->layout, B->block, B->grid,
-                                B->stream, B->chunk);
+                                B->stream, B->chunk, B->d_claim + r);
     cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
     if (err != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -114,6 +116,8 @@ sls_status run(sls_batch *B, sls_info *infos)
     BATCH_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs, sizeof(JobDesc) * k, cudaMemcpyHostToDevice, B->stream),
               "upload job table");
     BATCH_TRY(cudaMemsetAsync(B->d_stats, 0, sizeof(PassStats) * B->nstats, B->stream), "clear statistics");
+    BATCH_TRY(cudaMemsetAsync(B->d_claim, 0, sizeof(unsigned long long) * std::max(1, B->rounds), B->stream),
+              "clear chunk counters");
     if (B->rounds > 0) {
         if (!B->exec) {
             sls_status st = build_graph(B);
@@ -167,8 +171,8 @@ sls_status reset(sls_batch *B)
 // Picks the launch shape by timing a whole batch smooth for each candidate,
 // restoring the starting coordinates after every trial: the block size (32-
 // node tasks a CTA runs at once, 4 per 128 threads) and the chunk of
-// consecutive tasks a warp takes in the grid stride (0: one contiguous share
-// of the task list per warp).  Every round of a call is one node of one
+// consecutive tasks a warp takes, in a grid stride (1, 4, 16), claimed from a
+// per-round counter (2, 8), or as one contiguous share of the list (0).  Every round of a call is one node of one
 // CUDA graph, so all passes of a call are one launch whatever the shape.
 sls_status autotune(sls_batch *B, bool tune_block)
 {
@@ -178,7 +182,7 @@ sls_status autotune(sls_batch *B, bool tune_block)
     };
     std::vector<Shape> cands;
     const int blocks[2] = {64, 128};  // the kernel is built for 6 blocks of <= 128
-    const int64_t chunks[4] = {0, 1, 4, 16};
+    const int64_t chunks[6] = {0, 1, 4, 16, -2, -8};  // < 0: claimed from a per-round counter
     for (int b : blocks) {
         if (!tune_block && b != B->block) continue;
         for (int64_t c : chunks) cands.push_back(Shape{b, c});
@@ -291,6 +295,7 @@ sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *i
     if (cudaMalloc(&B->d_jobs, sizeof(JobDesc) * k) != cudaSuccess ||
         cudaMalloc(&B->d_tasks, sizeof(WarpTask) * std::max<int64_t>(1, B->ntasks)) != cudaSuccess ||
         cudaMalloc(&B->d_stats, sizeof(PassStats) * B->nstats) != cudaSuccess ||
+        cudaMalloc(&B->d_claim, sizeof(unsigned long long) * std::max(1, B->rounds)) != cudaSuccess ||
         cudaMallocHost(&B->h_jobs, sizeof(JobDesc) * k) != cudaSuccess) {
         cudaGetLastError();
         return fail_free(fail(SLS_ERR_OOM, "batch allocation failed"));
@@ -342,6 +347,30 @@ sls_status sls_batch_reset(sls_batch *B)
 {
     if (!B) return fail(SLS_ERR_INVALID, "batch must not be NULL");
     return reset(B);
+}
+
+sls_status sls_batch_shape(const sls_batch *B, int32_t *block, int64_t *chunk)
+{
+    if (!B) return fail(SLS_ERR_INVALID, "batch must not be NULL");
+    if (block) *block = B->block;
+    if (chunk) *chunk = B->chunk;
+    return SLS_OK;
+}
+
+sls_status sls_batch_set_shape(sls_batch *B, int32_t block, int64_t chunk)
+{
+    if (!B) return fail(SLS_ERR_INVALID, "batch must not be NULL");
+    if (block != 32 && block != 64 && block != 96 && block != 128)
+        return fail(SLS_ERR_INVALID, "batch block size must be 32, 64, 96 or 128");
+    if (chunk < -(int64_t(1) << 20) || chunk > (int64_t(1) << 20)) return fail(SLS_ERR_INVALID, "chunk out of range");
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    B->block = block;
+    B->chunk = chunk;
+    B->grid = device_sm_count() * batch_pass_occupancy(B->layout, B->block);
+    return SLS_OK;
 }
 
 sls_status sls_batch_destroy(sls_batch *B)

@@ -21,10 +21,12 @@ cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int g
 int pass_screened_occupancy(int layout, int block);
 
 // One round of the batched / served form over all active jobs' tasks.
-// chunk: tasks per warp chunk, taken in a grid stride; 0 = one contiguous
-// share of the task list per warp.
+// chunk > 0: tasks per warp chunk, taken in a grid stride; chunk < 0: chunks
+// of -chunk tasks claimed in order from *claim (zero at the launch); 0 = one
+// contiguous share of the task list per warp.
 cudaError_t launch_batch_pass(const JobDesc *jobs, const WarpTask *tasks, int64_t ntasks, int round,
-                              int layout, int block, int grid, cudaStream_t s, int64_t chunk);
+                              int layout, int block, int grid, cudaStream_t s, int64_t chunk,
+                              unsigned long long *claim);
 int batch_pass_occupancy(int layout, int block);
 // Record of round `round` of each of the na jobs (pass round - base_round,
 // clamped to the job's last pass) into out[0 .. na).

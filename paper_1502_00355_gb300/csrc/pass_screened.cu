@@ -387,11 +387,14 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
 }
 
 // ---- batched / served form: many meshes, one launch per round -----------
-// Work is a list of warp tasks (32 consecutive nodes of one job).  The warps
-// take chunks of `chunk` consecutive tasks in a grid stride (warp w: chunks
-// w, w + W, w + 2W, ...), so that at any moment they work on a window of
-// neighbouring tasks and share its gathers in L1 and L2; chunk = 0 gives
-// each warp one contiguous share of the list instead.  A job takes part in
+// Work is a list of warp tasks (32 consecutive nodes of one job).  With
+// chunk > 0 the warps take chunks of `chunk` consecutive tasks in a grid
+// stride (warp w: chunks w, w + W, w + 2W, ...), so that at any moment they
+// work on a window of neighbouring tasks and share its gathers in L1 and L2;
+// with chunk < 0 they claim chunks of -chunk tasks in list order from the
+// round's counter (*claim, zero at the launch), which keeps that window and
+// lets a warp that drew cheap tasks take more; chunk = 0 gives each warp one
+// contiguous share of the list.  A job takes part in
 // round r as its pass q = r - base_round while q < max_iter and its
 // tolerance is not met.  The deferred queue is drained and the statistics
 // flushed whenever the warp moves to another job, so every record gets
@@ -399,7 +402,8 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
 template <int LAYOUT>
 __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__restrict__ jobs,
                                                           const WarpTask *__restrict__ tasks, int64_t ntasks,
-                                                          int round, int64_t chunk)
+                                                          int round, int64_t chunk,
+                                                          unsigned long long *claim)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;
@@ -411,9 +415,15 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
 
     const int64_t nwarps = (int64_t)gridDim.x * (nthr >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (nthr >> 5) + warp;
-    const int64_t per = chunk > 0 ? chunk : (ntasks + nwarps - 1) / nwarps;
+    const bool dynamic = chunk < 0;
+    const int64_t per = chunk > 0 ? chunk : (dynamic ? -chunk : (ntasks + nwarps - 1) / nwarps);
     const int64_t cstride = chunk > 0 ? nwarps * chunk : ntasks;  // one share per warp when chunk == 0
-    int64_t c0 = gw * per;                                       // first task of the current chunk
+    auto claim_next = [&]() -> int64_t {
+        unsigned long long v = 0ull;
+        if (lane == 0) v = atomicAdd(claim, (unsigned long long)per);
+        return (int64_t)__shfl_sync(0xffffffffu, v, 0);
+    };
+    int64_t c0 = dynamic ? claim_next() : gw * per;  // first task of the current chunk
     int64_t t = c0;
 
     int cur_job = -1;
@@ -423,7 +433,7 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
     int qn = 0;
     for (;;) {
         if (t >= c0 + per || t >= ntasks) {  // next chunk of this warp
-            c0 += cstride;
+            c0 = dynamic ? (c0 < ntasks ? claim_next() : c0) : c0 + cstride;
             t = c0;
         }
         const bool more = t < ntasks && c0 < ntasks;
@@ -540,14 +550,16 @@ cudaError_t launch_pass_screened(const PassArgs &a, int layout, int block, int g
 }
 
 cudaError_t launch_batch_pass(const JobDesc *jobs, const WarpTask *tasks, int64_t ntasks, int round,
-                              int layout, int block, int grid, cudaStream_t s, int64_t chunk)
+                              int layout, int block, int grid, cudaStream_t s, int64_t chunk,
+                              unsigned long long *claim)
 {
     cudaError_t e = ensure_constants();
     if (e != cudaSuccess) return e;
     if (ntasks <= 0) return cudaSuccess;
+    if (chunk < 0 && !claim) return cudaErrorInvalidValue;
     const size_t smem = screened_smem_bytes(block);
-    if (layout == 0) batch_pass_kernel<0><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round, chunk);
-    else batch_pass_kernel<1><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round, chunk);
+    if (layout == 0) batch_pass_kernel<0><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round, chunk, claim);
+    else batch_pass_kernel<1><<<grid, block, smem, s>>>(jobs, tasks, ntasks, round, chunk, claim);
     return cudaGetLastError();
 }
 

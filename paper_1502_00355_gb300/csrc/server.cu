@@ -450,7 +450,7 @@ void scheduler_loop(sls_server *S)
         }
         const auto t0 = Clock::now();
         cudaError_t e = launch_batch_pass(S->d_jobs, S->d_tasks, S->ntasks, S->round, S->opt.layout, S->block,
-                                          S->grid, S->stream, kServerChunk);
+                                          S->grid, S->stream, kServerChunk, nullptr);
         // every job's record of this round, gathered by one kernel, read back by one copy
         if (e == cudaSuccess) e = launch_gather_round(S->d_jobs, (int)na, S->round, S->d_round, S->stream);
         if (e == cudaSuccess)

@@ -120,3 +120,32 @@ def test_batch_edge_meshes(sls):
     batch.close()
     for h in handles:
         h.close()
+
+
+def test_every_launch_shape_gives_the_same_results(sls):
+    """The warp chunk and block size change only who computes what: every
+    shape (contiguous shares, grid-stride chunks, counter-claimed chunks)
+    gives results identical to smoothing each mesh alone."""
+    meshes = [meshgen.jittered_grid(nx, ny, 0.3, 600 + k, numbering="morton")
+              for k, (nx, ny) in enumerate([(40, 30), (7, 5), (120, 64), (33, 97), (3, 3), (64, 64)])]
+    iters = [12, 3, 25, 7, 1, 18]
+    alone = []
+    for m, it in zip(meshes, iters):
+        with sls.Mesh(m.xy, m.tri, m.boundary) as g:
+            g.smooth(it)
+            alone.append(g.coords())
+    handles = [sls.Mesh(m.xy, m.tri, m.boundary) for m in meshes]
+    b = sls.Batch(handles, iters)
+    assert b.shape[0] in (64, 128)
+    for block, chunk in [(128, 0), (64, 1), (128, 4), (96, 16), (128, -1), (64, -8), (32, -3)]:
+        b.set_shape(block, chunk)
+        assert b.shape == (block, chunk)
+        b.reset()
+        b.smooth()
+        for j, ref in enumerate(alone):
+            assert np.array_equal(b.coords(j), ref), (block, chunk, j)
+    with pytest.raises(sls.SlsError):
+        b.set_shape(100, 0)
+    b.close()
+    for h in handles:
+        h.close()
