@@ -817,23 +817,34 @@ def run_single(args):
     achieved = bytes_pass / (pass_ms * 1e-3) / 1e9
     fig = profile_figures("pass_screened") if headline else None
     traffic = fig["dram_bytes_per_node"] * mesh.n if fig else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "traffic_source": fig["source"] if fig else "no capture of the current kernel sources",
-                "bytes_per_pass": bytes_pass, "bytes_source": "16n + 16n_free + 8(n+1) + 4nnz + 12m + 12m + n",
-                "bytes_per_pass_library_encoding": bytes_ours, "pass_ms": pass_ms}
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+           "peak_kind": peak_kind,
+           "traffic_source": fig["source"] if fig else "no capture of the current kernel sources",
+           "bytes_per_pass": bytes_pass, "bytes_source": "16n + 16n_free + 8(n+1) + 4nnz + 12m + 12m + n",
+           "bytes_per_pass_library_encoding": bytes_ours}
+    roofline = {"bound": "hbm", **hbm, "pass_ms": pass_ms}
     if fig:
-        # the FP64 pipe: every warp instruction occupies it for all 32 lanes
-        fp64_peak = fp64_pipe_peak()
+        # The FP64 pipe: every FP64 warp instruction occupies it for all 32
+        # lanes.  Peak from the unit count and clock: 2 FP64 lane operations
+        # per clock per SM (the FMA pipe's sustained peak) x SMs x max SM clock.
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        clk_max = clk.summary().get("sm_max_mhz") or 2070.0
+        fp64_peak = 2.0 * sms * clk_max * 1e6
+        fp64_dgemm = fp64_pipe_peak()
         fp64_ops = fig["fp64_warp_inst_per_32_nodes"] * mesh.n
         fp64_ach = fp64_ops / (pass_ms * 1e-3)
-        roofline["fp64"] = {"achieved": fp64_ach / 1e12, "peak": fp64_peak / 1e12, "unit": "T lane-op/s",
-                            "frac": fp64_ach / fp64_peak,
-                            "peak_source": "cuBLAS DGEMM 4096^3 (n^3 FMA), measured in this run",
-                            "inst_source": fig["source"]}
-        if roofline["fp64"]["frac"] > roofline["frac"]:
-            roofline["bound"] = "alu"
-            roofline["bound_unit"] = "FP64 pipe (see fp64); HBM figures above"
+        fp64 = {"achieved": fp64_ach / 1e12, "peak": fp64_peak / 1e12, "unit": "T FP64 pipe op/s",
+                "frac": fp64_ach / fp64_peak,
+                "peak_source": f"2 FP64 lane operations per clock per SM x {sms} SMs x {clk_max:.0f} MHz",
+                "measured_dgemm": fp64_dgemm / 1e12, "frac_of_measured_dgemm": fp64_ach / fp64_dgemm,
+                "inst_source": fig["source"]}
+        roofline["hbm"] = dict(hbm)
+        roofline["fp64"] = fp64
+        if fp64["frac"] > hbm["frac"]:
+            # the binding unit is the FP64 pipe: the line's roofline describes it
+            roofline = {"bound": "alu", "achieved": fp64["achieved"], "peak": fp64["peak"], "unit": fp64["unit"],
+                        "frac": fp64["frac"], "traffic": traffic, "peak_kind": "derived (unit count x clock)",
+                        "pass_ms": pass_ms, "hbm": dict(hbm), "fp64": fp64}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

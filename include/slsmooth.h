@@ -216,9 +216,9 @@ sls_status sls_mesh_destroy(sls_mesh *mesh);
  * their coordinates in place.  The coordinates at packing time are saved for
  * sls_batch_reset.  The launch shape is autotuned by timing one full batch
  * smooth per candidate, restoring the saved coordinates after each trial:
- * the chunk of consecutive 32-node tasks a warp takes (1, 4 or 16 in a grid
- * stride, 2 or 8 claimed in order from a per-round counter, or one contiguous
- * share of the list per warp) and, with opt == NULL or
+ * the chunk of consecutive 32-node tasks a warp takes (one contiguous share
+ * of the list per warp, 64 in a grid stride, or 32 claimed in order from a
+ * per-round counter) and, with opt == NULL or
  * opt->block_size == 0, the block size (64 or 128 threads); an explicit
  * block_size must be 32, 64, 96 or 128 (SLS_ERR_INVALID otherwise). */
 sls_status sls_batch_create(sls_mesh *const *meshes, int32_t k, const int32_t *iters,

@@ -171,8 +171,8 @@ sls_status reset(sls_batch *B)
 // Picks the launch shape by timing a whole batch smooth for each candidate,
 // restoring the starting coordinates after every trial: the block size (32-
 // node tasks a CTA runs at once, 4 per 128 threads) and the chunk of
-// consecutive tasks a warp takes, in a grid stride (1, 4, 16), claimed from a
-// per-round counter (2, 8), or as one contiguous share of the list (0).  Every round of a call is one node of one
+// consecutive tasks a warp takes: one contiguous share of the list (0), 64
+// in a grid stride, or 32 claimed from a per-round counter.  Every round of a call is one node of one
 // CUDA graph, so all passes of a call are one launch whatever the shape.
 sls_status autotune(sls_batch *B, bool tune_block)
 {
@@ -182,7 +182,10 @@ sls_status autotune(sls_batch *B, bool tune_block)
     };
     std::vector<Shape> cands;
     const int blocks[2] = {64, 128};  // the kernel is built for 6 blocks of <= 128
-    const int64_t chunks[6] = {0, 1, 4, 16, -2, -8};  // < 0: claimed from a per-round counter
+    // chunks of 1 to 16 tasks measured 11-60% slower on the 2,048-mesh
+    // workload: a warp that changes job drains its deferred nodes at partial
+    // width, so short chunks run the exact FP64 path with few lanes active
+    const int64_t chunks[3] = {0, 64, -32};  // < 0: claimed from a per-round counter
     for (int b : blocks) {
         if (!tune_block && b != B->block) continue;
         for (int64_t c : chunks) cands.push_back(Shape{b, c});
