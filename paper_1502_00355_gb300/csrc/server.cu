@@ -39,7 +39,10 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kBuilders = 4;  // builder threads (and streams) per server
-constexpr int64_t kServerChunk = 4;  // tasks per warp chunk of a round (grid stride)
+// Warp tasks of a round: one contiguous share of the list per warp (short
+// chunks make warps change job often, and every change drains the warp's
+// deferred nodes at partial width; measured on the batched form).
+constexpr int64_t kServerChunk = 0;
 
 enum JobState { kQueued, kBuilding, kActive, kRetiring, kDone, kFailed };
 
@@ -121,7 +124,8 @@ namespace {
 // adjacency words, one statistics record per pass.
 size_t built_footprint(int64_t n, uint64_t adj_words, int32_t max_iter)
 {
-    return 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1) + sizeof(uint32_t) * adj_words +
+    return 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1) +
+           sizeof(uint32_t) * (adj_words + kAdjPad) +
            sizeof(PassStats) * (size_t)std::max(1, max_iter);
 }
 
@@ -197,7 +201,9 @@ sls_status build_job(ServerJob &J, cudaStream_t s, size_t *footprint)
         da.n_free = hm.n_free;
         da.diag = hm.diag;
         e = cudaMallocAsync((void **)&da.node_off, sizeof(uint32_t) * (size_t)(n + 1), s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&da.adj, sizeof(uint32_t) * std::max<uint64_t>(1, da.adj_words), s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&da.adj, sizeof(uint32_t) * (da.adj_words + kAdjPad), s);
+        if (e == cudaSuccess && da.adj)
+            e = cudaMemsetAsync(da.adj + da.adj_words, 0, sizeof(uint32_t) * kAdjPad, s);
         J.d_off = da.node_off;  // freed with the job on any failure below
         J.d_adj = da.adj;
         if (e == cudaSuccess)
