@@ -50,8 +50,8 @@ PROFILE_FIGURES = {
     },
     "batch_pass": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu"],
-        "sha256": None,
-        "dram_per_alg_byte": 1078639872 / 994046024,
+        "sha256": "096a6fdf2b7dedeb5d55317b668a5594a533c7e205d33258668833ae3697c5f3",
+        "dram_per_alg_byte": (908991488 + 169472768) / 994046024,
         "source": "profiles/batch_pass_batch256.md (round 0 of a 256-mesh batch, scaled by algorithmic bytes)",
     },
 }

@@ -73,12 +73,6 @@ struct WarpTask {
 
 constexpr uint32_t kMetaFixed = 0x80000000u;
 
-// Every adjacency array carries kAdjPad zero words past its last record: the
-// screened pass loads the first words of a node's record together, before it
-// knows the record's length, and a short record is followed by the next
-// node's words or by these.
-constexpr int kAdjPad = 8;
-
 __device__ __forceinline__ uint32_t meta_degree(uint32_t meta) { return meta & 0xffffu; }
 __device__ __forceinline__ uint32_t meta_ntri(uint32_t meta) { return (meta >> 16) & 0x7fffu; }
 __device__ __forceinline__ uint32_t code_slot(uint32_t c) { return c >> 30; }

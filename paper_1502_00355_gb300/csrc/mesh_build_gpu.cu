@@ -719,8 +719,7 @@ sls_status build_device_adjacency(int64_t n, int64_t m, const double *d_xy, cons
     unsigned long long wtotal = 0ull;
     if ((st = scan_u32(words, n, node_off, &wtotal, s, async)) != SLS_OK) return st;
     if (wtotal >= (1ull << 32)) return fail(SLS_ERR_INVALID, "adjacency exceeds 2^32 words");
-    if ((st = dalloc(b_adj, (size_t)wtotal + kAdjPad, &adj, "adjacency", al)) != SLS_OK) return st;
-    GB_TRY(cudaMemsetAsync(adj + wtotal, 0, sizeof(uint32_t) * kAdjPad, s), "adjacency padding");
+    if ((st = dalloc(b_adj, (size_t)wtotal, &adj, "adjacency", al)) != SLS_OK) return st;
     node_pass2_kernel<<<grid, block, 0, s>>>(n, d_tri, ptr, inc, nbtmp, deg, fixed, node_off, adj);
     GB_TRY(cudaGetLastError(), "node pass 2");
 

@@ -125,9 +125,8 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
     for (int b = 0; b < 2; ++b)
         if ((st = dev_alloc((void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
     if ((st = dev_alloc((void **)&M->node_off, sizeof(uint32_t) * (M->n + 1), "node offsets")) != SLS_OK) return st;
-    if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * (M->adj_words + kAdjPad), "adjacency")) != SLS_OK) return st;
+    if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
     if ((st = dev_alloc((void **)&M->tri, sizeof(int32_t) * 3 * (size_t)M->m, "triangles")) != SLS_OK) return st;
-    SLS_CUDA_TRY(cudaMemsetAsync(M->adj + M->adj_words, 0, sizeof(uint32_t) * kAdjPad, M->stream), "adjacency padding");
     if (o.layout == 0) {
         SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[0], xy, cbytes, cudaMemcpyHostToDevice, M->stream), "upload coordinates");
         SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload coordinates");
@@ -180,10 +179,7 @@ sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const
         M->diag = hm.diag;
         M->adj_words = hm.node_off[hm.n];
         if ((st = dev_alloc((void **)&M->node_off, sizeof(uint32_t) * (n + 1), "node offsets")) != SLS_OK) return st;
-        if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * (M->adj_words + kAdjPad), "adjacency")) != SLS_OK)
-            return st;
-        SLS_CUDA_TRY(cudaMemsetAsync(M->adj + M->adj_words, 0, sizeof(uint32_t) * kAdjPad, M->stream),
-                     "adjacency padding");
+        if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
         SLS_CUDA_TRY(cudaMemcpyAsync(M->node_off, hm.node_off.data(), sizeof(uint32_t) * (n + 1),
                                      cudaMemcpyHostToDevice, M->stream), "upload offsets");
         SLS_CUDA_TRY(cudaMemcpyAsync(M->adj, hm.adj.data(), sizeof(uint32_t) * M->adj_words,

@@ -83,18 +83,10 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     d.pad = 0u;
     d.cx = 0ull;
     d.cy = 0ull;
-    // The node's own coordinates and the first words of its record (meta,
-    // first neighbour, the next four; kAdjPad covers a short last record)
-    // are loaded together, before the record's length is known.
     uint32_t off = 0u, meta = kMetaFixed;
-    uint32_t w[5] = {0u, 0u, 0u, 0u, 0u};
-    ulonglong2 pb = make_ulonglong2(0ull, 0ull);
     if (have) {
-        pb = CoordBits<LAYOUT>::get(a.in, a.n, i);
         off = __ldg(a.node_off + i);
         meta = __ldg(a.adj + off);
-#pragma unroll
-        for (int u = 0; u < 5; ++u) w[u] = __ldg(a.adj + off + 1 + u);
     }
     const bool fixed = (meta & kMetaFixed) != 0u;
     if (have && fixed && a.accept) a.accept[i] = 0;
@@ -104,8 +96,11 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     const uint32_t *nb = a.adj + off + 1;
     const uint32_t dmax = __reduce_max_sync(0xffffffffu, act ? deg : 0u);
 
-    ulonglong2 v0 = make_ulonglong2(0ull, 0ull);
-    if (act) v0 = CoordBits<LAYOUT>::get(a.in, a.n, w[0]);
+    ulonglong2 pb = make_ulonglong2(0ull, 0ull), v0 = make_ulonglong2(0ull, 0ull);
+    if (act) {
+        pb = CoordBits<LAYOUT>::get(a.in, a.n, i);
+        v0 = CoordBits<LAYOUT>::get(a.in, a.n, __ldg(nb));
+    }
     float phx, plx, phy, ply;
     bool ok = head_tail(pb.x, phx, plx) & head_tail(pb.y, phy, ply);
     unsigned long long sxb = v0.x, syb = v0.y;
@@ -120,14 +115,10 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
         rn = rl;
         rmin = rl;
     }
-    uint32_t nxt[4] = {w[1], w[2], w[3], w[4]};  // the ids of the next group of four
     for (uint32_t k0 = 1; k0 < dmax; k0 += 4) {
         uint32_t id[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) id[u] = (act && k0 + u < deg) ? nxt[u] : 0u;
-        // the group after this one, loaded while this group's coordinates come in
-#pragma unroll
-        for (int u = 0; u < 4; ++u) nxt[u] = (act && k0 + 4 + u < deg) ? __ldg(nb + k0 + 4 + u) : 0u;
+        for (int u = 0; u < 4; ++u) id[u] = (act && k0 + u < deg) ? __ldg(nb + k0 + u) : 0u;
         ulonglong2 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)

@@ -124,8 +124,7 @@ namespace {
 // adjacency words, one statistics record per pass.
 size_t built_footprint(int64_t n, uint64_t adj_words, int32_t max_iter)
 {
-    return 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1) +
-           sizeof(uint32_t) * (adj_words + kAdjPad) +
+    return 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1) + sizeof(uint32_t) * adj_words +
            sizeof(PassStats) * (size_t)std::max(1, max_iter);
 }
 
@@ -149,11 +148,8 @@ void fail_job(sls_server *S, ServerJob &J, sls_status st, const std::string &msg
 
 void free_job_device(ServerJob &J, cudaStream_t s)
 {
-    cudaFreeAsync(J.d_xy[0], s);
-    cudaFreeAsync(J.d_xy[1], s);
-    cudaFreeAsync(J.d_off, s);
-    cudaFreeAsync(J.d_adj, s);
-    cudaFreeAsync(J.d_stats, s);
+    for (void *p : {(void *)J.d_xy[0], (void *)J.d_xy[1], (void *)J.d_off, (void *)J.d_adj, (void *)J.d_stats})
+        if (p) cudaFreeAsync(p, s);
     if (J.uploaded) cudaEventDestroy(J.uploaded);
     J.d_xy[0] = J.d_xy[1] = nullptr;
     J.d_off = J.d_adj = nullptr;
@@ -170,7 +166,7 @@ sls_status build_job(ServerJob &J, cudaStream_t s, size_t *footprint)
     const size_t cbytes = sizeof(double) * 2 * (size_t)n;
     int32_t *d_tri = nullptr;
     auto cleanup = [&](sls_status st) {
-        cudaFreeAsync(d_tri, s);
+        if (d_tri) cudaFreeAsync(d_tri, s);
         free_job_device(J, s);
         return st;
     };
@@ -201,9 +197,7 @@ sls_status build_job(ServerJob &J, cudaStream_t s, size_t *footprint)
         da.n_free = hm.n_free;
         da.diag = hm.diag;
         e = cudaMallocAsync((void **)&da.node_off, sizeof(uint32_t) * (size_t)(n + 1), s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&da.adj, sizeof(uint32_t) * (da.adj_words + kAdjPad), s);
-        if (e == cudaSuccess && da.adj)
-            e = cudaMemsetAsync(da.adj + da.adj_words, 0, sizeof(uint32_t) * kAdjPad, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&da.adj, sizeof(uint32_t) * std::max<uint64_t>(1, da.adj_words), s);
         J.d_off = da.node_off;  // freed with the job on any failure below
         J.d_adj = da.adj;
         if (e == cudaSuccess)
