@@ -28,6 +28,9 @@ cudaError_t launch_batch_pass(const JobDesc *jobs, const WarpTask *tasks, int64_
                               int layout, int block, int grid, cudaStream_t s, int64_t chunk,
                               unsigned long long *claim);
 int batch_pass_occupancy(int layout, int block);
+// The warp tasks of the na jobs of a table (job j's tasks from task_off[j]).
+cudaError_t launch_expand_tasks(const JobDesc *jobs, const int64_t *task_off, int na, WarpTask *tasks,
+                                cudaStream_t s);
 // Record of round `round` of each of the na jobs (pass round - base_round,
 // clamped to the job's last pass) into out[0 .. na).
 cudaError_t launch_gather_round(const JobDesc *jobs, int na, int round, PassStats *out, cudaStream_t s);

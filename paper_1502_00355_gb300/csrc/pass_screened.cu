@@ -576,7 +576,26 @@ __global__ void gather_round_kernel(const JobDesc *__restrict__ jobs, int na, in
     out[j] = J.stats[q];
 }
 
+// The warp tasks of na jobs: job j's 32-node tasks at task_off[j] onwards.
+__global__ void expand_tasks_kernel(const JobDesc *__restrict__ jobs, const int64_t *__restrict__ task_off, int na,
+                                    WarpTask *__restrict__ tasks)
+{
+    for (int j = blockIdx.x; j < na; j += gridDim.x) {
+        const int64_t n = jobs[j].n, t0 = task_off[j];
+        for (int64_t f = (int64_t)threadIdx.x * 32; f < n; f += (int64_t)blockDim.x * 32)
+            tasks[t0 + f / 32] = WarpTask{j, (int32_t)f};
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_expand_tasks(const JobDesc *jobs, const int64_t *task_off, int na, WarpTask *tasks,
+                                cudaStream_t s)
+{
+    if (na <= 0) return cudaSuccess;
+    expand_tasks_kernel<<<na < 4096 ? na : 4096, 256, 0, s>>>(jobs, task_off, na, tasks);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gather_round(const JobDesc *jobs, int na, int round, PassStats *out, cudaStream_t s)
 {

@@ -67,6 +67,8 @@ struct ServerJob {
     int upload_state = 0;  // 0 pending, 1 built (event recorded), 2 failed
     int base_round = 0;
     int iterations = 0;
+    bool finished = false;                // scheduler thread only: handed to the retire thread
+    cudaEvent_t free_after = nullptr;     // the retire thread waits for it before touching the job
     // result
     JobState state = kQueued;
     sls_status status = SLS_OK;
@@ -99,13 +101,17 @@ struct sls_server {
     std::vector<std::thread> builders;
     std::thread sched, retirer;
 
-    // job table and warp tasks of the active set
-    JobDesc *d_jobs = nullptr, *h_jobs = nullptr;
-    WarpTask *d_tasks = nullptr, *h_tasks = nullptr;
-    size_t jobs_cap = 0, tasks_cap = 0;
-    PassStats *h_round = nullptr;  // pinned: this round's record of each active job
-    PassStats *d_round = nullptr;  // the same records gathered on the device
-    size_t round_cap = 0;
+    // job table and warp tasks of the active set; the host staging and the
+    // round records are double-buffered by round parity, because round r+1
+    // is launched before the records of round r are read
+    JobDesc *d_jobs = nullptr, *h_jobs[2] = {nullptr, nullptr};
+    int64_t *d_toff = nullptr, *h_toff[2] = {nullptr, nullptr};  // first task of each job
+    WarpTask *d_tasks = nullptr;
+    size_t jobs_cap = 0, jobs_hcap[2] = {0, 0}, toff_cap = 0, toff_hcap[2] = {0, 0}, tasks_cap = 0;
+    PassStats *h_round[2] = {nullptr, nullptr};  // pinned: a round's record of each job it ran over
+    PassStats *d_round[2] = {nullptr, nullptr};  // the same records gathered on the device
+    size_t round_cap[2] = {0, 0}, dround_cap[2] = {0, 0};
+    cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
     int64_t ntasks = 0;
     int block = 256, grid = 0;
     int round = 0;
@@ -269,16 +275,14 @@ void builder_loop(sls_server *S, cudaStream_t s)
 }
 
 template <class T>
-bool grow_pair(T *&h, T *&d, size_t &cap, size_t need)
+bool grow_host(T *&h, size_t &cap, size_t need)
 {
     if (need <= cap) return true;
     const size_t c = std::max<size_t>(need, 2 * cap);
     cudaFreeHost(h);
-    cudaFree(d);
     h = nullptr;
-    d = nullptr;
     cap = 0;
-    if (cudaMallocHost((void **)&h, sizeof(T) * c) != cudaSuccess || cudaMalloc((void **)&d, sizeof(T) * c) != cudaSuccess) {
+    if (cudaMallocHost((void **)&h, sizeof(T) * c) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -286,19 +290,39 @@ bool grow_pair(T *&h, T *&d, size_t &cap, size_t need)
     return true;
 }
 
-// Rebuilds the job table and the warp-task list of the active set.
-bool rebuild_table(sls_server *S)
+// cudaFree waits for the device, so a round in flight finishes before its
+// buffers are replaced.
+template <class T>
+bool grow_dev(T *&d, size_t &cap, size_t need)
+{
+    if (need <= cap) return true;
+    const size_t c = std::max<size_t>(need, 2 * cap);
+    cudaFree(d);
+    d = nullptr;
+    cap = 0;
+    if (cudaMalloc((void **)&d, sizeof(T) * c) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cap = c;
+    return true;
+}
+
+// Rebuilds the job table and the warp-task list of the active set for the
+// round launched next, whose parity is `slot`: the table and each job's
+// first task are staged on the host, the task list is expanded on the device.
+bool rebuild_table(sls_server *S, int slot)
 {
     const size_t na = S->active.size();
-    size_t ntasks = 0;
-    for (auto &J : S->active) ntasks += (size_t)((J->n + 31) / 32);
-    if (!grow_pair(S->h_jobs, S->d_jobs, S->jobs_cap, na) ||
-        !grow_pair(S->h_tasks, S->d_tasks, S->tasks_cap, std::max<size_t>(1, ntasks)))
+    if (!grow_host(S->h_jobs[slot], S->jobs_hcap[slot], na) || !grow_dev(S->d_jobs, S->jobs_cap, na) ||
+        !grow_host(S->h_toff[slot], S->toff_hcap[slot], na + 1) || !grow_dev(S->d_toff, S->toff_cap, na + 1))
         return false;
-    size_t t = 0;
+    JobDesc *hj = S->h_jobs[slot];
+    int64_t *ht = S->h_toff[slot];
+    int64_t t = 0;
     for (size_t j = 0; j < na; ++j) {
         ServerJob &J = *S->active[j];
-        JobDesc &D = S->h_jobs[j];
+        JobDesc &D = hj[j];
         D.xy[0] = J.d_xy[0];
         D.xy[1] = J.d_xy[1];
         D.node_off = J.d_off;
@@ -314,11 +338,16 @@ bool rebuild_table(sls_server *S)
         D.cur0 = 0;
         D.pad = 0;
         D.accept = nullptr;
-        for (int64_t f = 0; f < J.n; f += 32) S->h_tasks[t++] = WarpTask{(int32_t)j, (int32_t)f};
+        ht[j] = t;
+        t += (J.n + 31) / 32;
     }
-    S->ntasks = (int64_t)t;
-    return cudaMemcpyAsync(S->d_jobs, S->h_jobs, sizeof(JobDesc) * na, cudaMemcpyHostToDevice, S->stream) == cudaSuccess &&
-           cudaMemcpyAsync(S->d_tasks, S->h_tasks, sizeof(WarpTask) * t, cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
+    ht[na] = t;
+    if (!grow_dev(S->d_tasks, S->tasks_cap, (size_t)std::max<int64_t>(1, t))) return false;
+    S->ntasks = t;
+    return cudaMemcpyAsync(S->d_jobs, hj, sizeof(JobDesc) * na, cudaMemcpyHostToDevice, S->stream) == cudaSuccess &&
+           cudaMemcpyAsync(S->d_toff, ht, sizeof(int64_t) * (na + 1), cudaMemcpyHostToDevice, S->stream) ==
+               cudaSuccess &&
+           launch_expand_tasks(S->d_jobs, S->d_toff, (int)na, S->d_tasks, S->stream) == cudaSuccess;
 }
 
 // Copies the results of finished jobs to the host and frees their device
@@ -336,6 +365,13 @@ void retire_loop(sls_server *S)
             S->to_retire.clear();
         }
         bool ok = true;
+        // the round launched after a job's last one still reads its records:
+        // wait for it before copying and freeing
+        std::vector<cudaEvent_t> evs;
+        for (auto &Jp : batch)
+            if (Jp->free_after && std::find(evs.begin(), evs.end(), Jp->free_after) == evs.end())
+                evs.push_back(Jp->free_after);
+        for (cudaEvent_t ev : evs) ok = ok && cudaStreamWaitEvent(S->retire_stream, ev, 0) == cudaSuccess;
         for (auto &Jp : batch) {
             ServerJob &J = *Jp;
             J.result.resize(2 * (size_t)J.n);
@@ -344,6 +380,8 @@ void retire_loop(sls_server *S)
         }
         ok = ok && cudaStreamSynchronize(S->retire_stream) == cudaSuccess;  // one wait for the batch
         if (!ok) cudaGetLastError();
+        for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+        for (auto &Jp : batch) Jp->free_after = nullptr;
         std::lock_guard<std::mutex> lk(S->mu);
         const auto now = Clock::now();
         for (auto &Jp : batch) {
@@ -376,15 +414,57 @@ bool can_admit(const sls_server *S)
     return S->used + need <= S->budget || S->used == 0;
 }
 
+// Processes the records of a completed round over `jobs` (the active set it
+// ran over): counts every job's executed pass and hands the jobs that reached
+// their cap or tolerance to the retire thread.  Jobs already handed over in
+// an earlier round are skipped (the round launched after their last pass
+// still lists them, and skips them).  Returns the jobs that finished.
+std::vector<std::shared_ptr<ServerJob>> process_round(sls_server *S, const std::vector<std::shared_ptr<ServerJob>> &jobs,
+                                                      const PassStats *rec)
+{
+    std::vector<std::shared_ptr<ServerJob>> finished;
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        ServerJob &J = *jobs[j];
+        if (J.finished) continue;
+        const PassStats &r = rec[j];
+        bool done = true;  // a job with max_iter == 0 runs no pass
+        if (J.max_iter > 0 && r.executed) {
+            J.iterations += 1;
+            J.info.iterations = J.iterations;
+            J.info.accepted_last = (int64_t)r.nacc;
+            std::memcpy(&J.info.max_d2_last, &r.maxd2_bits, sizeof(double));
+            J.info.fp64_fallbacks += (int64_t)r.fallbacks;
+            const double thr = tolerance_threshold(J.tol, J.diag);
+            unsigned long long tb;
+            std::memcpy(&tb, &thr, sizeof tb);
+            const bool conv = J.tol > 0.0 && r.maxd2_bits < tb;
+            J.info.converged = conv ? 1 : 0;
+            done = conv || J.iterations >= J.max_iter;
+        }
+        if (done) {
+            J.finished = true;
+            finished.push_back(jobs[j]);
+        }
+    }
+    return finished;
+}
+
 void scheduler_loop(sls_server *S)
 {
     cudaSetDevice(S->device);
     bool dirty = true;
+    // The round in flight (launched, records not yet read): its parity and
+    // the active set it runs over.  Round r+1 is launched before the records
+    // of round r are read, so the GPU never waits for the host between
+    // rounds; a job that finished in round r is still listed in round r+1,
+    // whose kernel skips it (its pass count or tolerance is reached).
+    int pending = -1;
+    std::vector<std::shared_ptr<ServerJob>> ran[2];
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_sched.wait(lk, [S] {
-                if (S->stop || !S->active.empty()) return true;
+            S->cv_sched.wait(lk, [S, pending] {
+                if (S->stop || !S->active.empty() || pending >= 0) return true;
                 for (auto &J : S->uploading)
                     if (J->upload_state != 0) return true;
                 return can_admit(S);
@@ -403,8 +483,8 @@ void scheduler_loop(sls_server *S)
             }
             if (handed) S->cv_build.notify_all();
         }
-        // built jobs join in this round (their builds overlap the previous
-        // rounds); with nothing running, wait for the first one to be built.
+        // built jobs join from the next round on (their builds overlap the
+        // running rounds); with nothing running, wait for the first built one
         for (size_t k = 0; k < S->uploading.size();) {
             auto J = S->uploading[k];
             int ust;
@@ -421,7 +501,7 @@ void scheduler_loop(sls_server *S)
                 ++k;
                 continue;
             }
-            if (S->active.empty()) cudaEventSynchronize(J->uploaded);
+            if (S->active.empty() && pending < 0) cudaEventSynchronize(J->uploaded);
             if (cudaEventQuery(J->uploaded) != cudaSuccess) {
                 ++k;
                 continue;
@@ -435,73 +515,83 @@ void scheduler_loop(sls_server *S)
             S->uploading.erase(S->uploading.begin() + k);
             dirty = true;
         }
-        if (S->active.empty()) continue;
-        const size_t na = S->active.size();
-        if (dirty) {
-            if (!rebuild_table(S)) {
-                S->sched_error = "job table upload failed";
+        // launch the next round over the active set
+        int launched = -1;
+        if (!S->active.empty()) {
+            const int slot = S->round & 1;
+            const size_t na = S->active.size();
+            if (dirty) {
+                if (!rebuild_table(S, slot)) {
+                    S->sched_error = "job table upload failed";
+                    break;
+                }
+                dirty = false;
+            }
+            if (!grow_host(S->h_round[slot], S->round_cap[slot], na) ||
+                !grow_dev(S->d_round[slot], S->dround_cap[slot], na)) {
+                S->sched_error = "out of pinned host memory";
                 break;
             }
-            dirty = false;
-        }
-        if (!grow_pair(S->h_round, S->d_round, S->round_cap, na)) {
-            S->sched_error = "out of pinned host memory";
-            break;
-        }
-        const auto t0 = Clock::now();
-        cudaError_t e = launch_batch_pass(S->d_jobs, S->d_tasks, S->ntasks, S->round, S->opt.layout, S->block,
-                                          S->grid, S->stream, kServerChunk, nullptr);
-        // every job's record of this round, gathered by one kernel, read back by one copy
-        if (e == cudaSuccess) e = launch_gather_round(S->d_jobs, (int)na, S->round, S->d_round, S->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(S->h_round, S->d_round, sizeof(PassStats) * na, cudaMemcpyDeviceToHost, S->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-        S->busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
-        if (e != cudaSuccess) {
-            S->sched_error = cudaGetErrorString(e);
-            cudaGetLastError();
-            break;
-        }
-        S->round += 1;
-        std::vector<std::shared_ptr<ServerJob>> keep, finished;
-        for (size_t j = 0; j < na; ++j) {
-            auto Jp = S->active[j];
-            ServerJob &J = *Jp;
-            const PassStats &r = S->h_round[j];
-            bool done = true;  // a job with max_iter == 0 runs no pass
-            if (J.max_iter > 0 && r.executed) {
-                J.iterations += 1;
-                J.info.iterations = J.iterations;
-                J.info.accepted_last = (int64_t)r.nacc;
-                std::memcpy(&J.info.max_d2_last, &r.maxd2_bits, sizeof(double));
-                J.info.fp64_fallbacks += (int64_t)r.fallbacks;
-                const double thr = tolerance_threshold(J.tol, J.diag);
-                unsigned long long tb;
-                std::memcpy(&tb, &thr, sizeof tb);
-                const bool conv = J.tol > 0.0 && r.maxd2_bits < tb;
-                J.info.converged = conv ? 1 : 0;
-                done = conv || J.iterations >= J.max_iter;
+            cudaError_t e = cudaEventRecord(S->ev_start[slot], S->stream);
+            if (e == cudaSuccess)
+                e = launch_batch_pass(S->d_jobs, S->d_tasks, S->ntasks, S->round, S->opt.layout, S->block, S->grid,
+                                      S->stream, kServerChunk, nullptr);
+            // every job's record of this round, gathered by one kernel, read back by one copy
+            if (e == cudaSuccess) e = launch_gather_round(S->d_jobs, (int)na, S->round, S->d_round[slot], S->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(S->h_round[slot], S->d_round[slot], sizeof(PassStats) * na,
+                                    cudaMemcpyDeviceToHost, S->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(S->ev_done[slot], S->stream);
+            if (e != cudaSuccess) {
+                S->sched_error = cudaGetErrorString(e);
+                cudaGetLastError();
+                break;
             }
-            if (!done) {
-                keep.push_back(Jp);
-                continue;
+            ran[slot] = S->active;
+            S->round += 1;
+            launched = slot;
+        }
+        // read the round launched before this one
+        if (pending >= 0) {
+            cudaError_t e = cudaEventSynchronize(S->ev_done[pending]);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, S->ev_start[pending], S->ev_done[pending]);
+            if (e != cudaSuccess) {
+                S->sched_error = cudaGetErrorString(e);
+                cudaGetLastError();
+                break;
             }
-            finished.push_back(Jp);
-        }
-        if (!finished.empty()) {
-            // the round's wait above leaves their final coordinates in place;
-            // no later round touches them (they leave the task list)
-            std::lock_guard<std::mutex> lk(S->mu);
-            for (auto &Jp : finished) {
-                Jp->state = kRetiring;
-                S->to_retire.push_back(Jp);
+            S->busy_s += 1e-3 * (double)ms;
+            auto finished = process_round(S, ran[pending], S->h_round[pending]);
+            ran[pending].clear();
+            if (!finished.empty()) {
+                // their memory is released once the round just launched (which
+                // still reads their records) is done
+                cudaEvent_t ev = nullptr;
+                if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventRecord(ev, S->stream) != cudaSuccess) {
+                    S->sched_error = "event for finished jobs";
+                    cudaGetLastError();
+                    break;
+                }
+                {
+                    std::lock_guard<std::mutex> lk(S->mu);
+                    for (auto &Jp : finished) {
+                        Jp->state = kRetiring;
+                        Jp->free_after = ev;
+                        S->to_retire.push_back(Jp);
+                    }
+                }
+                S->cv_retire.notify_one();
+                std::vector<std::shared_ptr<ServerJob>> keep;
+                keep.reserve(S->active.size());
+                for (auto &Jp : S->active)
+                    if (!Jp->finished) keep.push_back(Jp);
+                S->active.swap(keep);
+                dirty = true;
             }
-            S->cv_retire.notify_one();
         }
-        if (keep.size() != na) {
-            S->active.swap(keep);
-            dirty = true;
-        }
+        pending = launched;
     }
     // cancel what is left, once no builder touches a job any more
     std::unique_lock<std::mutex> lk(S->mu);
@@ -561,13 +651,20 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
                       cudaStreamCreateWithFlags(&S->retire_stream, cudaStreamNonBlocking) == cudaSuccess;
     for (auto &bs : S->build_streams)
         streams_ok = streams_ok && cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2; ++b)
+        streams_ok = streams_ok && cudaEventCreate(&S->ev_start[b]) == cudaSuccess &&
+                     cudaEventCreate(&S->ev_done[b]) == cudaSuccess;
     if (!streams_ok) {
         cudaGetLastError();
+        for (int b = 0; b < 2; ++b) {
+            if (S->ev_start[b]) cudaEventDestroy(S->ev_start[b]);
+            if (S->ev_done[b]) cudaEventDestroy(S->ev_done[b]);
+        }
         for (cudaStream_t x : S->build_streams)
             if (x) cudaStreamDestroy(x);
         if (S->stream) cudaStreamDestroy(S->stream);
         if (S->retire_stream) cudaStreamDestroy(S->retire_stream);
-        return fail(SLS_ERR_CUDA, "cudaStreamCreate failed");
+        return fail(SLS_ERR_CUDA, "stream or event creation failed");
     }
     if (cudaDeviceGetDefaultMemPool(&S->pool, S->device) == cudaSuccess) {
         uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
@@ -684,12 +781,18 @@ sls_status sls_server_destroy(sls_server *S)
     if (S->retirer.joinable()) S->retirer.join();
     for (cudaStream_t bs : S->build_streams) cudaStreamSynchronize(bs);
     cudaStreamSynchronize(S->retire_stream);
-    cudaFreeHost(S->h_jobs);
+    cudaStreamSynchronize(S->stream);
+    for (int b = 0; b < 2; ++b) {
+        cudaFreeHost(S->h_jobs[b]);
+        cudaFreeHost(S->h_toff[b]);
+        cudaFreeHost(S->h_round[b]);
+        cudaFree(S->d_round[b]);
+        if (S->ev_start[b]) cudaEventDestroy(S->ev_start[b]);
+        if (S->ev_done[b]) cudaEventDestroy(S->ev_done[b]);
+    }
     cudaFree(S->d_jobs);
-    cudaFreeHost(S->h_tasks);
+    cudaFree(S->d_toff);
     cudaFree(S->d_tasks);
-    cudaFreeHost(S->h_round);
-    cudaFree(S->d_round);
     cudaStreamDestroy(S->stream);
     cudaStreamDestroy(S->retire_stream);
     for (cudaStream_t bs : S->build_streams) cudaStreamDestroy(bs);
