@@ -330,7 +330,7 @@ def run_batch(args):
     world, rank = init_ranks()
     sls.lib()
     # weak scaling: every rank smooths its own batch of batch_meshes meshes
-    specs = shard(meshgen.batch_specs(args.batch_meshes * world), rank, world)
+    specs = shard(meshgen.batch_specs(args.batch_meshes * world, lo=args.batch_min_n, hi=args.batch_max_n), rank, world)
     meshes = [meshgen.batch_mesh(sp) for sp in specs]
     iters = [sp[2] for sp in specs]
     total_nodes = sum(m.n for m in meshes)
@@ -386,7 +386,9 @@ def run_batch(args):
     out = {"metric": "node-updates/s (batched)", "value": batched, "unit": "node-updates/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"batch{len(meshes)}_logu1K-256K_aspect1-4_iters10-100",
+           "config": {"workload": (f"batch{len(meshes) * world}_logu1K-256K_aspect1-4_iters10-100"
+                                   if (args.batch_min_n, args.batch_max_n) == (1024, 262144) else
+                                   f"batch{len(meshes) * world}_logu{args.batch_min_n}-{args.batch_max_n}_aspect1-4_iters10-100"),
                       "meshes_per_gpu": len(meshes), "meshes": len(meshes) * world,
                       "nodes_rank0": total_nodes, "launch_shape": {"block": batch.shape[0], "chunk": batch.shape[1]},
                       "parallelism": f"{world} ranks, independent meshes (no collective)" if world > 1 else "single"},
@@ -607,6 +609,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="large", choices=["large", "batch", "serve"])
     ap.add_argument("--batch-meshes", type=int, default=2048)
+    ap.add_argument("--batch-min-n", type=int, default=1024)
+    ap.add_argument("--batch-max-n", type=int, default=262144)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-max-n", type=int, default=4 * 1024 * 1024)
