@@ -16,7 +16,7 @@ struct Deferred {
     int32_t node;
     uint32_t flags;
     uint32_t masks;  // bits 0..15: candidates for q_old, bits 16..31: for q_new
-    uint32_t job;    // batched form: the job the node belongs to (0 for a single mesh)
+    uint32_t pad;
     unsigned long long cx, cy;  // the centre, as FP64 bit patterns
 };
 

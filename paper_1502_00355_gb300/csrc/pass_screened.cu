@@ -80,7 +80,7 @@ __device__ __forceinline__ bool screen_node(const PassArgs &a, bool have, int64_
     d.node = (int32_t)i;
     d.flags = 0u;
     d.masks = 0u;
-    d.job = 0u;
+    d.pad = 0u;
     d.cx = 0ull;
     d.cy = 0ull;
     uint32_t off = 0u, meta = kMetaFixed;
@@ -301,60 +301,6 @@ __device__ __forceinline__ void drain_queue(const PassArgs &a, Deferred *wq, int
     }
 }
 
-// The arguments of pass `round - base_round` of job J (batched form).
-__device__ __forceinline__ bool job_pass_args(const JobDesc *J, int round, PassArgs &a)
-{
-    const int q = round - J->base_round;
-    PassStats *st = J->stats;
-    const int tol_active = J->tol_active;
-    const unsigned long long thr_bits = J->thr_bits;
-    if (!(q >= 0 && q < J->max_iter && !pass_is_skipped(st, q, tol_active, thr_bits))) return false;
-    double *x0 = J->xy[0], *x1 = J->xy[1];
-    const bool odd = ((J->cur0 + q) & 1) != 0;
-    a.in = odd ? x1 : x0;
-    a.out = odd ? x0 : x1;
-    a.node_off = J->node_off;
-    a.adj = J->adj;
-    a.n = J->n;
-    a.order = nullptr;
-    a.norder = 0;
-    a.stats = st;
-    a.q = q;
-    a.strict = J->strict;
-    a.tol_active = tol_active;
-    a.thr_bits = thr_bits;
-    a.accept = J->accept;
-    return true;
-}
-
-// Batched form: finishes deferred nodes that may belong to different jobs,
-// each lane with its own job's arguments, and adds each result to its job's
-// record of this round with atomics, so a warp that moves on to another job
-// need not drain first (the queue fills to full width instead).
-template <int LAYOUT>
-__device__ __forceinline__ void drain_queue_jobs(const JobDesc *__restrict__ jobs, int round, Deferred *wq, int &qn,
-                                                 bool all)
-{
-    const int lane = threadIdx.x & 31;
-    while (qn >= 32 || (all && qn > 0)) {
-        if (lane < qn) {
-            const Deferred e = wq[lane];
-            PassArgs a{};
-            job_pass_args(jobs + e.job, round, a);  // the job was active when the node was deferred
-            unsigned long long b2;
-            bool acc, moved;
-            exact_update<LAYOUT>(a, e.node, e.flags, e.masks, e.cx, e.cy, b2, acc, moved);
-            if (b2) atomicMax(&a.stats[a.q].maxd2_bits, b2);
-            if (acc) atomicAdd(&a.stats[a.q].nacc, 1ull);
-        }
-        const int rest = qn > 32 ? qn - 32 : 0;
-        __syncwarp();
-        if (lane < rest) wq[lane] = wq[32 + lane];
-        __syncwarp();
-        qn = rest;
-    }
-}
-
 // Warp-wide reduction of the statistics into one record (lane 0 writes).
 __device__ __forceinline__ void warp_flush_stats(PassStats *st, unsigned long long best,
                                                  unsigned long long nacc, unsigned long long nfb)
@@ -493,13 +439,37 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
         const bool more = t < ntasks && c0 < ntasks;
         const int job = more ? tasks[t].job : -2;
         if (job != cur_job) {
-            // the decided nodes' counts go to the job being left; its deferred
-            // nodes stay queued and are finished with their own job's arguments
-            if (cur_job >= 0 && active) warp_flush_stats(a.stats + a.q, best, nacc, nfb);
+            if (cur_job >= 0 && active) {
+                __syncwarp();
+                drain_queue<LAYOUT>(a, wq, qn, true, best, nacc);
+                warp_flush_stats(a.stats + a.q, best, nacc, nfb);
+            }
             best = nacc = nfb = 0ull;
             cur_job = job;
             if (job < 0) break;
-            active = job_pass_args(jobs + job, round, a);
+            const JobDesc *J = jobs + job;
+            const int q = round - J->base_round;
+            PassStats *st = J->stats;
+            const int tol_active = J->tol_active;
+            const unsigned long long thr_bits = J->thr_bits;
+            active = q >= 0 && q < J->max_iter && !pass_is_skipped(st, q, tol_active, thr_bits);
+            if (active) {
+                double *x0 = J->xy[0], *x1 = J->xy[1];
+                const bool odd = ((J->cur0 + q) & 1) != 0;
+                a.in = odd ? x1 : x0;
+                a.out = odd ? x0 : x1;
+                a.node_off = J->node_off;
+                a.adj = J->adj;
+                a.n = J->n;
+                a.order = nullptr;
+                a.norder = 0;
+                a.stats = st;
+                a.q = q;
+                a.strict = J->strict;
+                a.tol_active = tol_active;
+                a.thr_bits = thr_bits;
+                a.accept = J->accept;
+            }
         }
         if (!active) {
             ++t;
@@ -512,18 +482,15 @@ __global__ void __launch_bounds__(128, 6) batch_pass_kernel(const JobDesc *__res
         Deferred d;
         uint32_t res;
         const bool defer = screen_node<LAYOUT>(a, i < a.n, i < a.n ? i : 0, loc, nthr, d, best, nacc, res);
-        d.job = (uint32_t)cur_job;
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (defer) wq[qn + __popc(m & ((1u << lane) - 1u))] = d;
         qn += __popc(m);
         nfb += defer ? 1ull : 0ull;
         if (qn >= 32) {
             __syncwarp();
-            drain_queue_jobs<LAYOUT>(jobs, round, wq, qn, false);
+            drain_queue<LAYOUT>(a, wq, qn, false, best, nacc);
         }
     }
-    __syncwarp();
-    drain_queue_jobs<LAYOUT>(jobs, round, wq, qn, true);
 }
 
 // Constant memory and function attributes belong to a context: they are set
