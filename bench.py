@@ -43,14 +43,14 @@ CSRC = os.path.join(ROOT, "paper_1502_00355_gb300", "csrc")
 PROFILE_FIGURES = {
     "pass_screened": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh"],
-        "sha256": "0c3d8c7e549e6613c97e08adddb98f3712b9aa1c046c25469679437f985dfb1c",
+        "sha256": "384a301409e6b085a6028b237862f2cc929b6302feee999f1e4ebccba2e05574",
         "dram_bytes_per_node": 361.5e6 / (2048 * 2048),
         "fp64_warp_inst_per_32_nodes": 19.0 + 5.9 + 1.2,
         "source": "profiles/pass_screened_grid2048.md (2048x2048 capture, per node)",
     },
     "batch_pass": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu"],
-        "sha256": "096a6fdf2b7dedeb5d55317b668a5594a533c7e205d33258668833ae3697c5f3",
+        "sha256": "e9cfa0127b9c51c4bf2a50834364281a4bedc6b4d08fe2e8cc319c95a0e02714",
         "dram_per_alg_byte": (908991488 + 169472768) / 994046024,
         "source": "profiles/batch_pass_batch256.md (round 0 of a 256-mesh batch, scaled by algorithmic bytes)",
     },
