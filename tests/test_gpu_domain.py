@@ -97,3 +97,22 @@ def test_gather_scatter_checks_ids(sls):
         assert e.value.code == 1
         empty = torch.empty(0, dtype=torch.int32, device="cuda")
         g.gather(empty, out[:0])
+
+
+def test_distributed_driver_at_one_rank(sls):
+    """domain.DistributedMesh with the library backend and no process group
+    (the path bench.py --decompose runs per rank): the stop rule with D from
+    the owned coordinates gives the whole mesh's run."""
+    mesh = meshgen.jittered_grid(120, 90, 0.35, 12, numbering="morton")
+    sub = domain.partition(mesh.n, mesh.tri, mesh.boundary, 1, 0)
+    be = domain.LibraryBackend(sub, mesh.xy[sub.nodes])
+    dm = domain.DistributedMesh(sub, be, mesh.xy[sub.lo:sub.hi], device="cuda")
+    info = dm.smooth(200, 1e-9)
+    xy = dm.owned_coords()
+    be.close()
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary) as g:
+        ref = g.smooth(200, 1e-9)
+        assert np.array_equal(xy, g.coords())
+    for key in ("iterations", "converged", "accepted_last", "maxd2_last"):
+        assert info[key] == ref[key], key
+    assert dm.diag == g.diag
