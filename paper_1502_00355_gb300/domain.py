@@ -61,9 +61,12 @@ def ranges(n: int, world: int) -> np.ndarray:
 
 
 def partition(n: int, tri: np.ndarray, boundary: np.ndarray, world: int, rank: int) -> Subdomain:
-    """The subdomain of `rank` out of `world` for a mesh of n nodes."""
+    """The subdomain of `rank` out of `world` for a mesh of n nodes (every
+    rank must own at least one node: world <= n)."""
     if boundary is None:
         raise ValueError("the decomposed path needs the boundary flags of the whole mesh")
+    if not 1 <= world <= n or not 0 <= rank < world:
+        raise ValueError("need 1 <= world <= n and 0 <= rank < world")
     tri = np.ascontiguousarray(tri, dtype=np.int64).reshape(-1, 3)
     b = ranges(n, world)
     lo, hi = int(b[rank]), int(b[rank + 1])
@@ -177,6 +180,11 @@ class DistributedMesh:
                 reqs.append(self.dist.isend(self.sendbuf[p], dst=p, group=self.group))
         for r in reqs:
             r.wait()
+        if reqs and str(self.dev).startswith("cuda"):
+            # with NCCL, wait() orders only the current CUDA stream after the
+            # transfer; the scatter runs on the mesh's own stream, so wait here
+            torch = self.torch
+            torch.cuda.synchronize()
         for p, buf in self.recvbuf.items():
             self.backend.scatter(p, buf)
 
