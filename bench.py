@@ -600,6 +600,9 @@ def run_serve(args):
                     "node_updates_per_s_busy": fifo_busy, "busy_s": busy_ms * 1e-3},
            "speedup_vs_fifo": served / fifo,
            "speedup_vs_fifo_busy": served / fifo_busy,
+           # work rate against work rate: the server's node-updates over the
+           # device time of its rounds, FIFO's over the time its calls took
+           "speedup_busy_vs_busy": st["node_updates_per_s"] / fifo_busy if world == 1 else None,
            "identical_results": bool(same),
            "latency": "scheduled arrival to result on the host"}
     print(json.dumps(out), flush=True)
