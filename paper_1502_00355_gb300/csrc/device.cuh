@@ -25,6 +25,8 @@ struct PassArgs {
     int64_t n;
     const uint32_t *order;     // nullptr: every node in index order; else the nodes to update
     int64_t norder;            // (one colour class of Form B) and their number
+    int ranged;                // 1 (order null): only the nodes first .. first + count - 1
+    int64_t first, count;      // (a contiguous colour class of a renumbered Form-B mesh)
     PassStats *stats;          // stats[q] receives this pass
     int q;                     // pass index within the call
     int strict;                // 1: accept iff q_new > q_old

@@ -65,6 +65,22 @@ cudaError_t launch_gather_nodes(const double *xy, int layout, int64_t n, const i
 cudaError_t launch_scatter_nodes(double *xy0, double *xy1, int layout, int64_t n, const int32_t *idx, int64_t k,
                                  const double *in, unsigned *bad, int grid, cudaStream_t s);
 
+// A renumbered mesh (Form B: colour classes contiguous).  Coordinates are
+// doubles or, with f32, floats, in the layout; perm maps a new id to the
+// caller's.
+// dst[k] = src[perm[k]]
+cudaError_t launch_permute_coords(const double *src, double *dst, int layout, bool f32, int64_t n,
+                                  const uint32_t *perm, int grid, cudaStream_t s);
+// dst_aos (interleaved doubles, the caller's numbering)[perm[k]] = src[k]
+cudaError_t launch_unpermute_to_aos(const double *src, int layout, bool f32, int64_t n, const uint32_t *perm,
+                                    double *dst_aos, int grid, cudaStream_t s);
+// dst[k] = src_aos (interleaved doubles, the caller's numbering)[perm[k]], rounded to floats with f32
+cudaError_t launch_permute_from_aos(const double *src_aos, int layout, bool f32, int64_t n, const uint32_t *perm,
+                                    double *dst, int grid, cudaStream_t s);
+// dst[perm[k]] = src[k]
+cudaError_t launch_unpermute_u8(const uint8_t *src, int64_t n, const uint32_t *perm, uint8_t *dst, int grid,
+                                cudaStream_t s);
+
 // Layout conversions on the device (SoA <-> interleaved).
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int64_t n, int grid, cudaStream_t s);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int64_t n, int grid, cudaStream_t s);

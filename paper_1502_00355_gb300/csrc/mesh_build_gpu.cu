@@ -589,6 +589,128 @@ sls_status order_segment(sls_mesh *M, const int32_t *colour, int32_t c, uint32_t
 
 }  // namespace
 
+namespace {
+
+// ---- renumbering of a Form-B mesh: every colour class a contiguous id range
+
+__global__ void fixed_flag_kernel(const uint32_t *__restrict__ node_off, const uint32_t *__restrict__ adj, int64_t n,
+                                  unsigned *flag)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        flag[i] = (__ldg(adj + __ldg(node_off + i)) & kMetaFixed) ? 1u : 0u;
+}
+
+// perm[base + scan[i]] = i for the flagged nodes, in id order.
+__global__ void compact_kernel(const unsigned *__restrict__ flag, const uint32_t *__restrict__ scan, int64_t n,
+                               int64_t base, uint32_t *perm)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        if (flag[i]) perm[base + scan[i]] = (uint32_t)i;
+}
+
+__global__ void inverse_kernel(const uint32_t *__restrict__ perm, int64_t n, uint32_t *inv)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) inv[perm[k]] = (uint32_t)k;
+}
+
+__global__ void record_len_kernel(const uint32_t *__restrict__ node_off, const uint32_t *__restrict__ perm, int64_t n,
+                                  unsigned *len)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const uint32_t i = perm[k];
+        len[k] = node_off[i + 1] - node_off[i];
+    }
+}
+
+// The record of new node k is the record of old node perm[k] with its
+// neighbour ids renumbered; the meta word and the triangle codes (positions
+// in the neighbour list, whose order is kept) are copied as they are.
+__global__ void remap_adj_kernel(const uint32_t *__restrict__ off_old, const uint32_t *__restrict__ adj_old,
+                                 const uint32_t *__restrict__ perm, const uint32_t *__restrict__ inv,
+                                 const uint32_t *__restrict__ off_new, int64_t n, uint32_t *__restrict__ adj_new)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const uint32_t *src = adj_old + off_old[perm[k]];
+        uint32_t *dst = adj_new + off_new[k];
+        const uint32_t meta = src[0];
+        dst[0] = meta;
+        if (meta & kMetaFixed) continue;
+        const uint32_t deg = meta & 0xffffu, ntri = (meta >> 16) & 0x7fffu;
+        for (uint32_t w = 1; w <= deg; ++w) dst[w] = inv[src[w]];
+        for (uint32_t w = deg + 1; w <= deg + ntri; ++w) dst[w] = src[w];
+    }
+}
+
+__global__ void remap_ids_kernel(int32_t *ids, int64_t count, const uint32_t *__restrict__ inv)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride)
+        ids[t] = (int32_t)inv[ids[t]];
+}
+
+}  // namespace
+
+// Form B: renumbers the mesh so that every colour class is a contiguous id
+// range (the classes in order, each in its old id order, then the fixed
+// nodes in id order): a sweep then reads and writes each class's nodes
+// contiguously.  The colouring was computed on the caller's numbering, and
+// the neighbour lists keep their order (only the ids change), so every pass
+// computes what it computed before.  Fills M->perm (new -> caller's id) and
+// M->inv; replaces the adjacency, the triangles and both coordinate arrays.
+sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
+{
+    const int64_t n = M->n;
+    const int grid = device_sm_count() * 8, block = 256;
+    GB_TRY(cudaMalloc(&M->perm, sizeof(uint32_t) * (size_t)n), "renumbering");
+    GB_TRY(cudaMalloc(&M->inv, sizeof(uint32_t) * (size_t)n), "renumbering");
+    // the free nodes by class: the processing order already lists them so
+    if (M->n_free > 0)
+        GB_TRY(cudaMemcpyAsync(M->perm, M->node_order, sizeof(uint32_t) * (size_t)M->n_free,
+                               cudaMemcpyDeviceToDevice, s), "renumbering");
+    DevBuf b_flag, b_scan, b_off, b_adj;
+    unsigned *flag = nullptr;
+    uint32_t *scan = nullptr, *off_new = nullptr, *adj_new = nullptr;
+    sls_status st;
+    if ((st = dalloc(b_flag, (size_t)n + 1, &flag, "renumbering")) != SLS_OK) return st;
+    if ((st = dalloc(b_scan, (size_t)n + 1, &scan, "renumbering")) != SLS_OK) return st;
+    fixed_flag_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, n, flag);
+    GB_TRY(cudaGetLastError(), "renumbering");
+    unsigned long long nfixed = 0ull;
+    if ((st = scan_u32(flag, n, scan, &nfixed, s)) != SLS_OK) return st;
+    if ((int64_t)nfixed + M->n_free != n) return fail(SLS_ERR_INVALID, "node count mismatch in the renumbering");
+    compact_kernel<<<grid, block, 0, s>>>(flag, scan, n, M->n_free, M->perm);
+    inverse_kernel<<<grid, block, 0, s>>>(M->perm, n, M->inv);
+    record_len_kernel<<<grid, block, 0, s>>>(M->node_off, M->perm, n, flag);
+    GB_TRY(cudaGetLastError(), "renumbering");
+    if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering")) != SLS_OK) return st;
+    unsigned long long words = 0ull;
+    if ((st = scan_u32(flag, n, off_new, &words, s)) != SLS_OK) return st;
+    if (words != M->adj_words) return fail(SLS_ERR_INVALID, "adjacency size mismatch in the renumbering");
+    if ((st = dalloc(b_adj, (size_t)words, &adj_new, "renumbering")) != SLS_OK) return st;
+    remap_adj_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, M->perm, M->inv, off_new, n, adj_new);
+    remap_ids_kernel<<<grid, block, 0, s>>>(M->tri, 3 * M->m, M->inv);
+    GB_TRY(cudaGetLastError(), "renumbering");
+    // coordinates: both arrays hold the creation coordinates
+    GB_TRY(launch_permute_coords(M->xy[0], M->xy[1], M->opt.layout, M->f32, n, M->perm, grid, s), "renumbering");
+    GB_TRY(cudaMemcpyAsync(M->xy[0], M->xy[1], (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)n,
+                           cudaMemcpyDeviceToDevice, s), "renumbering");
+    GB_TRY(cudaStreamSynchronize(s), "renumbering");
+    cudaFree(M->node_off);
+    cudaFree(M->adj);
+    M->node_off = off_new;
+    M->adj = adj_new;
+    b_off.p = nullptr;  // now the mesh's
+    b_adj.p = nullptr;
+    cudaFree(M->node_order);
+    M->node_order = nullptr;
+    return SLS_OK;
+}
+
 sls_status build_node_order(sls_mesh *M, cudaStream_t s)
 {
     // Form A visits every node in index order: no list needed
@@ -639,7 +761,7 @@ sls_status build_node_order(sls_mesh *M, cudaStream_t s)
         M->colour_off[(size_t)c + 1] = at;
     }
     if (at != M->n_free) return fail(SLS_ERR_INVALID, "free-node count mismatch in the colouring");
-    return SLS_OK;
+    return renumber_classes(M, s);
 }
 
 // Builds the adjacency of a mesh whose coordinates (AoS) and triangles are

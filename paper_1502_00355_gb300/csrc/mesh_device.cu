@@ -204,6 +204,8 @@ void mesh_release(sls_mesh *M)
     cudaFree(M->node_off);
     cudaFree(M->adj);
     cudaFree(M->node_order);
+    cudaFree(M->perm);
+    cudaFree(M->inv);
     cudaFree(M->tri);
     cudaFree(M->stats);
     cudaFree(M->accept);
@@ -288,10 +290,13 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
                 // Form B: the colour classes in turn, in place (Eq. 3).  A
                 // mesh without free nodes has no class; one launch over an
                 // empty list still records the sweep, as Form A does.
+                // the mesh is renumbered: class c is the id range colour_off[c] ..
                 a.in = a.out = M->xy[M->cur];
                 for (int c = 0; c < std::max(nseg, 1); ++c) {
-                    a.order = M->node_order + (nseg > 0 ? M->colour_off[c] : 0);
-                    a.norder = nseg > 0 ? M->colour_off[c + 1] - M->colour_off[c] : 0;
+                    a.order = nullptr;
+                    a.ranged = 1;
+                    a.first = nseg > 0 ? M->colour_off[c] : 0;
+                    a.count = nseg > 0 ? M->colour_off[c + 1] - M->colour_off[c] : 0;
                     SLS_CUDA_TRY(launch_pass(M, a), "pass kernel");
                     ++kernels;
                 }
@@ -362,6 +367,20 @@ sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device)
 {
     const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
     const double *src = M->xy[M->cur];
+    if (M->perm) {
+        // renumbered mesh: back to the caller's numbering (and to interleaved doubles) on the device
+        double *d = xy_out;
+        sls_status st;
+        if (!dst_is_device && (st = dev_alloc((void **)&d, cbytes, "download")) != SLS_OK) return st;
+        cudaError_t e = launch_unpermute_to_aos(src, M->opt.layout, M->f32, M->n, M->perm, d,
+                                                device_sm_count() * 4, M->stream);
+        if (e == cudaSuccess && !dst_is_device)
+            e = cudaMemcpyAsync(xy_out, d, cbytes, cudaMemcpyDeviceToHost, M->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+        if (!dst_is_device) cudaFree(d);
+        if (e != cudaSuccess) return cuda_fail(e, "download coordinates");
+        return SLS_OK;
+    }
     if (M->f32) {
         const float *f = reinterpret_cast<const float *>(src);
         if (dst_is_device) {
@@ -398,6 +417,25 @@ sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device)
 
 sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
 {
+    if (M->perm) {
+        // renumbered mesh: into the mesh's numbering (and layout, and type) on the device
+        const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
+        const size_t ebytes = (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)M->n;
+        double *d = const_cast<double *>(xy);
+        sls_status st;
+        if (!src_is_device && (st = dev_alloc((void **)&d, cbytes, "upload")) != SLS_OK) return st;
+        cudaError_t e = cudaSuccess;
+        if (!src_is_device) e = cudaMemcpyAsync(d, xy, cbytes, cudaMemcpyHostToDevice, M->stream);
+        if (e == cudaSuccess)
+            e = launch_permute_from_aos(d, M->opt.layout, M->f32, M->n, M->perm, M->xy[M->cur],
+                                        device_sm_count() * 4, M->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(M->xy[M->cur ^ 1], M->xy[M->cur], ebytes, cudaMemcpyDeviceToDevice, M->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+        if (!src_is_device) cudaFree(d);
+        if (e != cudaSuccess) return cuda_fail(e, "set coordinates");
+        return SLS_OK;
+    }
     if (M->f32) {
         const size_t fbytes = sizeof(float) * 2 * (size_t)M->n;
         float *f = reinterpret_cast<float *>(M->xy[M->cur]);
@@ -442,6 +480,7 @@ sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
 sls_status mesh_transfer_nodes(sls_mesh *M, const int32_t *idx, int64_t k, double *buf, bool scatter)
 {
     if (M->f32) return fail(SLS_ERR_INVALID, "node gather/scatter needs an FP64 mesh");
+    if (M->perm) return fail(SLS_ERR_INVALID, "node gather/scatter needs a Form-A mesh");
     if (k == 0) return SLS_OK;
     if (!M->xfer_bad) {
         sls_status st = dev_alloc((void **)&M->xfer_bad, sizeof(unsigned), "transfer flag");

@@ -117,10 +117,10 @@ __global__ void __launch_bounds__(256) pass_f32_kernel(PassArgs a)
 
     unsigned best = 0u;  // bits of the largest squared move (non-negative floats order as integers)
     unsigned long long nacc = 0ull;
-    const int64_t cnt = a.order ? a.norder : a.n;
+    const int64_t cnt = a.order ? a.norder : (a.ranged ? a.count : a.n);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
-        const int64_t i = a.order ? (int64_t)__ldg(a.order + j) : j;
+        const int64_t i = a.order ? (int64_t)__ldg(a.order + j) : a.first + j;
         const uint32_t off = __ldg(a.node_off + i);
         const uint32_t meta = __ldg(a.adj + off);
         if (meta & kMetaFixed) {

@@ -27,9 +27,9 @@ __global__ void __launch_bounds__(1024) pass_fp64_kernel(PassArgs a)
     unsigned long long best = 0ull, nacc = 0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // every node, or (a colour class of Form B) the listed free nodes
-    const int64_t cnt = a.order ? a.norder : a.n;
+    const int64_t cnt = a.order ? a.norder : (a.ranged ? a.count : a.n);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
-        const int64_t i = a.order ? (int64_t)__ldg(a.order + j) : j;
+        const int64_t i = a.order ? (int64_t)__ldg(a.order + j) : a.first + j;
         const uint32_t meta = __ldg(a.adj + __ldg(a.node_off + i));
         if (meta & kMetaFixed) {
             if (a.accept) a.accept[i] = 0;
@@ -214,6 +214,141 @@ cudaError_t launch_scatter_nodes(double *xy0, double *xy1, int layout, int64_t n
         scatter_nodes_kernel<0><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, v, bad);
     else
         scatter_nodes_kernel<1><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, v, bad);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Coordinates in a layout and an element type (double or float).
+template <class T, int LAYOUT>
+struct Pair;
+template <class T>
+struct Pair<T, 0> {
+    static __device__ __forceinline__ void get(const T *p, int64_t, int64_t i, T &x, T &y)
+    {
+        x = p[2 * i];
+        y = p[2 * i + 1];
+    }
+    static __device__ __forceinline__ void put(T *p, int64_t, int64_t i, T x, T y)
+    {
+        p[2 * i] = x;
+        p[2 * i + 1] = y;
+    }
+};
+template <class T>
+struct Pair<T, 1> {
+    static __device__ __forceinline__ void get(const T *p, int64_t n, int64_t i, T &x, T &y)
+    {
+        x = p[i];
+        y = p[n + i];
+    }
+    static __device__ __forceinline__ void put(T *p, int64_t n, int64_t i, T x, T y)
+    {
+        p[i] = x;
+        p[n + i] = y;
+    }
+};
+
+// dst[k] = src[perm[k]] (same layout and type)
+template <class T, int LAYOUT>
+__global__ void permute_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t n,
+                               const uint32_t *__restrict__ perm)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        T x, y;
+        Pair<T, LAYOUT>::get(src, n, perm[k], x, y);
+        Pair<T, LAYOUT>::put(dst, n, k, x, y);
+    }
+}
+
+// dst (interleaved doubles, the caller's numbering)[perm[k]] = src[k] (exact widening of floats)
+template <class T, int LAYOUT>
+__global__ void unpermute_to_aos_kernel(const T *__restrict__ src, int64_t n, const uint32_t *__restrict__ perm,
+                                        double2 *__restrict__ dst)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        T x, y;
+        Pair<T, LAYOUT>::get(src, n, k, x, y);
+        dst[perm[k]] = make_double2((double)x, (double)y);
+    }
+}
+
+// dst[k] = src (interleaved doubles, the caller's numbering)[perm[k]], rounded to T
+template <class T, int LAYOUT>
+__global__ void permute_from_aos_kernel(const double2 *__restrict__ src, int64_t n, const uint32_t *__restrict__ perm,
+                                        T *__restrict__ dst)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const double2 v = src[perm[k]];
+        Pair<T, LAYOUT>::put(dst, n, k, (T)v.x, (T)v.y);
+    }
+}
+
+__global__ void unpermute_u8_kernel(const uint8_t *__restrict__ src, int64_t n, const uint32_t *__restrict__ perm,
+                                    uint8_t *__restrict__ dst)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) dst[perm[k]] = src[k];
+}
+
+}  // namespace
+
+cudaError_t launch_permute_coords(const double *src, double *dst, int layout, bool f32, int64_t n,
+                                  const uint32_t *perm, int grid, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (f32) {
+        const float *fs = reinterpret_cast<const float *>(src);
+        float *fd = reinterpret_cast<float *>(dst);
+        if (layout == 0) permute_kernel<float, 0><<<grid, 256, 0, s>>>(fs, fd, n, perm);
+        else permute_kernel<float, 1><<<grid, 256, 0, s>>>(fs, fd, n, perm);
+    } else {
+        if (layout == 0) permute_kernel<double, 0><<<grid, 256, 0, s>>>(src, dst, n, perm);
+        else permute_kernel<double, 1><<<grid, 256, 0, s>>>(src, dst, n, perm);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute_to_aos(const double *src, int layout, bool f32, int64_t n, const uint32_t *perm,
+                                    double *dst_aos, int grid, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    double2 *d = reinterpret_cast<double2 *>(dst_aos);
+    if (f32) {
+        const float *f = reinterpret_cast<const float *>(src);
+        if (layout == 0) unpermute_to_aos_kernel<float, 0><<<grid, 256, 0, s>>>(f, n, perm, d);
+        else unpermute_to_aos_kernel<float, 1><<<grid, 256, 0, s>>>(f, n, perm, d);
+    } else {
+        if (layout == 0) unpermute_to_aos_kernel<double, 0><<<grid, 256, 0, s>>>(src, n, perm, d);
+        else unpermute_to_aos_kernel<double, 1><<<grid, 256, 0, s>>>(src, n, perm, d);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_from_aos(const double *src_aos, int layout, bool f32, int64_t n, const uint32_t *perm,
+                                    double *dst, int grid, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const double2 *v = reinterpret_cast<const double2 *>(src_aos);
+    if (f32) {
+        float *f = reinterpret_cast<float *>(dst);
+        if (layout == 0) permute_from_aos_kernel<float, 0><<<grid, 256, 0, s>>>(v, n, perm, f);
+        else permute_from_aos_kernel<float, 1><<<grid, 256, 0, s>>>(v, n, perm, f);
+    } else {
+        if (layout == 0) permute_from_aos_kernel<double, 0><<<grid, 256, 0, s>>>(v, n, perm, dst);
+        else permute_from_aos_kernel<double, 1><<<grid, 256, 0, s>>>(v, n, perm, dst);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute_u8(const uint8_t *src, int64_t n, const uint32_t *perm, uint8_t *dst, int grid,
+                                cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    unpermute_u8_kernel<<<grid, 256, 0, s>>>(src, n, perm, dst);
     return cudaGetLastError();
 }
 

@@ -336,8 +336,9 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
     float2 *loc = s_loc + tid;
     Deferred *wq = s_q + 64 * warp;
     int qn = 0;  // warp-uniform queue length
-    // every node in index order, or (a colour class of Form B) the listed nodes
-    const int64_t cnt = a.order ? a.norder : a.n;
+    // every node in index order, or (a colour class of Form B) the listed
+    // nodes or a range of ids
+    const int64_t cnt = a.order ? a.norder : (a.ranged ? a.count : a.n);
     const int64_t nwtiles = (cnt + 31) / 32;
     const int64_t wstride = (int64_t)gridDim.x * (nthr >> 5);
     for (int64_t wt = (int64_t)blockIdx.x * (nthr >> 5) + warp; wt < nwtiles; wt += wstride) {
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(128, 7) pass_screened_kernel(PassArgs a)
         Deferred d;
         const bool have = j < cnt;
         uint32_t res;
-        const bool defer = screen_node<LAYOUT>(a, have, have ? (a.order ? (int64_t)__ldg(a.order + j) : j) : 0,
+        const bool defer = screen_node<LAYOUT>(a, have, have ? (a.order ? (int64_t)__ldg(a.order + j) : a.first + j) : 0,
                                                loc, nthr, d, best, nacc, res);
         const unsigned m = __ballot_sync(0xffffffffu, defer);
         if (a.halo) {  // before any drain: deferred nodes add their bits there
