@@ -93,9 +93,13 @@ typedef struct sls_options {
                               Gauss-Seidel: the free nodes are coloured at creation so that
                               no two neighbours share a colour (Jones-Plassmann rounds,
                               priority splitmix64(150200355 + node id)), and every sweep
-                              updates the colour classes in turn, in place.  copy_back is
-                              ignored.  Single meshes only: the batched, served and
-                              allocation-free forms reject it.                               */
+                              updates the colour classes in turn, in place.  Inside the
+                              library the mesh is renumbered so that each class is a
+                              contiguous id range (8 bytes per node for the maps); every
+                              call still reads and writes coordinates and decisions in the
+                              caller's numbering.  copy_back is ignored.  Single meshes
+                              only: the batched, served, allocation-free and gather /
+                              scatter entry points reject it.                                */
     int32_t precision;     /* 64 (default; 0 means 64): FP64 coordinates and arithmetic,
                               results bit-identical to the FP64 definition.  32: binary32
                               coordinates (the given doubles rounded to nearest) and every
