@@ -482,22 +482,28 @@ def run_serve(args):
     srv.close()
 
     # ---- served: continuous batching ----
+    # several clients: request k is submitted by client k % clients at its
+    # arrival time (each client makes its own meshes ahead of their turn), and
+    # two pollers collect the results (request k by poller k % 2)
     srv = sls.Server(max_queue=args.serve_queue)
-    pre = Prefetch(reqs, args.gen_threads, args.gen_depth)
+    clients, pollers = max(1, args.serve_clients), 2
+    pres = [Prefetch([reqs[k] for k in range(c, len(reqs), clients)], max(1, args.gen_threads // clients),
+                     args.gen_depth) for c in range(clients)]
     done_t = [None] * len(reqs)
     prints = [None] * len(reqs)
     iters = [0] * len(reqs)
-    pending = {}  # job id -> (request index, output buffer)
-    lock = threading.Lock()
-    submitted = threading.Event()
-    busy_retries = [0]
+    pending = [dict() for _ in range(pollers)]  # job id -> (request index, output buffer)
+    locks = [threading.Lock() for _ in range(pollers)]
+    left = [clients]
+    left_lock = threading.Lock()
+    busy_retries = [0] * clients
     if world > 1:
         dist.barrier()
     t_start = time.perf_counter()
 
-    def submitter():
-        for k in range(len(reqs)):
-            m = pre.get(k)
+    def submitter(c):
+        for local, k in enumerate(range(c, len(reqs), clients)):
+            m = pres[c].get(local)
             delay = arrivals[k] - (time.perf_counter() - t_start)
             if delay > 0:
                 time.sleep(delay)
@@ -508,20 +514,25 @@ def run_serve(args):
                 except sls.SlsError as e:
                     if e.code != 6:  # SLS_ERR_BUSY: the queue is full, try again shortly
                         raise
-                    busy_retries[0] += 1
+                    busy_retries[c] += 1
                     time.sleep(0.0005)
-            with lock:
-                pending[jid] = (k, np.empty((sizes[k], 2), np.float64))
-        submitted.set()
+            p = k % pollers
+            with locks[p]:
+                pending[p][jid] = (k, np.empty((sizes[k], 2), np.float64))
+        with left_lock:
+            left[0] -= 1
 
-    def poller():
+    def poller(p):
         while True:
-            with lock:
-                items = list(pending.items())
-            if not items and submitted.is_set():
-                with lock:
-                    if not pending:
-                        return
+            with locks[p]:
+                items = list(pending[p].items())
+            if not items:
+                with left_lock:
+                    finished = left[0] == 0
+                if finished:
+                    with locks[p]:
+                        if not pending[p]:
+                            return
             for jid, (k, buf) in items:
                 info = srv.try_wait(jid, buf)
                 if info is None:
@@ -529,21 +540,24 @@ def run_serve(args):
                 done_t[k] = time.perf_counter() - t_start
                 prints[k] = fp(buf)
                 iters[k] = info["iterations"]
-                with lock:
-                    del pending[jid]
+                with locks[p]:
+                    del pending[p][jid]
             time.sleep(0.0005)
 
-    ths = [threading.Thread(target=submitter), threading.Thread(target=poller)]
+    ths = [threading.Thread(target=submitter, args=(c,)) for c in range(clients)] + \
+          [threading.Thread(target=poller, args=(p,)) for p in range(pollers)]
     for t in ths:
         t.start()
     for t in ths:
         t.join()
     wall = time.perf_counter() - t_start
-    pre.close()
+    for pr in pres:
+        pr.close()
     st = srv.stats()
     srv.close()
     lat = [1e3 * (d - a) for d, a in zip(done_t, arrivals)]
     updates = float(sum(n * it for n, it in zip(sizes, iters)))
+    busy_retries = [sum(busy_retries)]
 
     # ---- FIFO: one request at a time, same arrivals, same kernels ----
     pre = Prefetch(reqs, args.gen_threads, args.gen_depth)
@@ -589,7 +603,7 @@ def run_serve(args):
                       "requests_per_gpu": len(reqs), "requests": len(reqs) * world,
                       "offered_req_per_s_per_gpu": args.serve_rate, "nodes_rank0": int(sum(sizes)),
                       "mesh_generator": "meshgen.fast_grid (jittered grid, J = 0.3, Morton)",
-                      "server_queue_limit": args.serve_queue,
+                      "server_queue_limit": args.serve_queue, "clients": args.serve_clients,
                       "parallelism": f"{world} ranks, one server each (no collective)" if world > 1 else "single"},
            "served": {"p50_ms": p50, "p99_ms": p99, "wall_s": wall_ms * 1e-3,
                       "req_per_s": len(reqs) * world / (wall_ms * 1e-3),
@@ -619,7 +633,9 @@ def main():
     ap.add_argument("--serve-max-n", type=int, default=4 * 1024 * 1024)
     ap.add_argument("--serve-queue", type=int, default=64,
                     help="jobs the server queues before a client must wait (host memory of queued inputs)")
-    ap.add_argument("--gen-threads", type=int, default=6)
+    ap.add_argument("--serve-clients", type=int, default=4,
+                    help="client threads submitting the stream (request k by client k %% clients)")
+    ap.add_argument("--gen-threads", type=int, default=8)
     ap.add_argument("--gen-depth", type=int, default=24)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)

@@ -731,13 +731,13 @@ sls_status sls_wait(sls_server *S, uint64_t job, double timeout_s, double *xy_ou
         return fail(SLS_ERR_TIMEOUT, "job not finished within the timeout");
     }
     // an oversized job is only known after its adjacency is built
-    if (J->state == kFailed) {
-        S->jobs.erase(job);
-        return fail(J->status, J->error);
-    }
+    S->jobs.erase(job);
+    if (J->state == kFailed) return fail(J->status, J->error);
+    // the copy of a large result must not hold up the scheduler and the
+    // builders: the job is ours alone once it left the table
+    lk.unlock();
     if (xy_out) std::memcpy(xy_out, J->result.data(), sizeof(double) * J->result.size());
     if (info) *info = J->info;
-    S->jobs.erase(job);
     return SLS_OK;
 }
 
