@@ -115,6 +115,16 @@ typedef struct sls_options {
                               and the screened kernel (SLS_KERNEL_AUTO or _FILTERED); costs
                               140 bytes of device memory per 32 nodes.  The batched and
                               allocation-free forms compute every tile; the server rejects it. */
+    int32_t keep_numbering;/* 0 (default): a Form-A mesh is renumbered inside the library: in
+                              every window of 128 consecutive ids the nodes are listed by
+                              incident-triangle count, then degree (fixed nodes last, ties by
+                              id), so that the 32 lanes of a warp run loops of similar length
+                              (the pass's loops run to the warp's longest).  The windows stay
+                              where they are, so the gathers keep their locality.  Not done
+                              with skip_unchanged (its 32-node tiles would lose theirs).
+                              Every call still reads and writes coordinates, decisions and
+                              node ids in the caller's numbering; 8 bytes per node for the
+                              maps; results are identical.  1: keep the caller's numbering.  */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle    */
 } sls_options;
 
@@ -184,9 +194,11 @@ sls_status sls_set_coords(sls_mesh *mesh, const double *xy, int32_t src_is_devic
  *                      float64 interleaved);
  *   sls_scatter_coords writes in (device, 2k float64) into both coordinate
  *                      arrays of the k listed nodes (distinct ids).
- * Both run on the handle's stream and return when done.  FP64 meshes only.
+ * Ids are in the caller's numbering (mapped inside the library when it
+ * renumbered the mesh).  Both run on the handle's stream and return when
+ * done.  FP64 Form-A meshes only.
  * Errors: SLS_ERR_INVALID for an id outside [0, n) (nothing is written for
- * it) or a binary32 mesh. */
+ * it), a binary32 or a Form-B mesh. */
 sls_status sls_gather_coords(sls_mesh *mesh, const int32_t *idx, int64_t k, double *out);
 sls_status sls_scatter_coords(sls_mesh *mesh, const int32_t *idx, int64_t k, const double *in);
 
@@ -317,7 +329,10 @@ sls_status sls_server_destroy(sls_server *srv);
  *            FP64; its own coordinates, accept mask and statistics are not
  *            used or changed, and its copy_back, skip_unchanged, l2_window and
  *            record_accept options are not applied (the results are the
- *            same: those options never change them)
+ *            same: those options never change them).  When the library
+ *            renumbered the mesh (keep_numbering = 0) two more kernels map
+ *            the coordinates into its numbering and back; both buffers are
+ *            in the caller's numbering
  *   xy_in    device, 2n float64 interleaved: the starting coordinates; also
  *            serves as the second buffer of the ping-pong, so its contents
  *            are unspecified on return

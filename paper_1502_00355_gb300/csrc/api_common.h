@@ -24,8 +24,9 @@ struct sls_mesh {
     uint32_t *adj = nullptr;      // node_off[n] words
     uint64_t adj_words = 0;
     uint32_t *node_order = nullptr;  // n_free: processing order of the free nodes (Form A: none)
-    uint32_t *perm = nullptr;     // Form B: new id -> the caller's id (colour classes contiguous)
-    uint32_t *inv = nullptr;      //         the caller's id -> new id
+    uint32_t *perm = nullptr;     // renumbered mesh: internal id -> the caller's id (Form B: colour
+                                  // classes contiguous; Form A: grouped by loop length in windows)
+    uint32_t *inv = nullptr;      // the caller's id -> internal id
     std::vector<int64_t> colour_off; // segments of node_order: one per colour (Form B), else one
     int32_t *tri = nullptr;       // 3m, for the histogram
     sls::PassStats *stats = nullptr;  // one record per pass of a call

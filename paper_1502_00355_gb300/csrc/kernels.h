@@ -59,13 +59,15 @@ cudaError_t launch_widen(const float *src, double *aos, int64_t n, int layout, i
 
 // Ghost exchange of a domain-decomposed mesh: the listed nodes' coordinates
 // (interleaved out / in, 2k doubles) from the current array, or into both
-// arrays; an id outside [0, n) sets *bad and is skipped.
+// arrays; an id outside [0, n) sets *bad and is skipped.  inv (caller's id ->
+// internal id) maps the ids of a renumbered mesh; NULL when it is not.
 cudaError_t launch_gather_nodes(const double *xy, int layout, int64_t n, const int32_t *idx, int64_t k,
-                                double *out, unsigned *bad, int grid, cudaStream_t s);
+                                const uint32_t *inv, double *out, unsigned *bad, int grid, cudaStream_t s);
 cudaError_t launch_scatter_nodes(double *xy0, double *xy1, int layout, int64_t n, const int32_t *idx, int64_t k,
-                                 const double *in, unsigned *bad, int grid, cudaStream_t s);
+                                 const uint32_t *inv, const double *in, unsigned *bad, int grid, cudaStream_t s);
 
-// A renumbered mesh (Form B: colour classes contiguous).  Coordinates are
+// A renumbered mesh (Form B: colour classes contiguous; Form A: nodes grouped
+// by loop length inside windows of ids).  Coordinates are
 // doubles or, with f32, floats, in the layout; perm maps a new id to the
 // caller's.
 // dst[k] = src[perm[k]]

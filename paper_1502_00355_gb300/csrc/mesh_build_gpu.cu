@@ -591,7 +591,8 @@ sls_status order_segment(sls_mesh *M, const int32_t *colour, int32_t c, uint32_t
 
 namespace {
 
-// ---- renumbering of a Form-B mesh: every colour class a contiguous id range
+// ---- renumbering: Form B lists every colour class as a contiguous id range,
+// Form A groups nodes by loop length inside windows of ids
 
 __global__ void fixed_flag_kernel(const uint32_t *__restrict__ node_off, const uint32_t *__restrict__ adj, int64_t n,
                                   unsigned *flag)
@@ -653,7 +654,146 @@ __global__ void remap_ids_kernel(int32_t *ids, int64_t count, const uint32_t *__
         ids[t] = (int32_t)inv[ids[t]];
 }
 
+// ---- Form A: nodes grouped by loop length inside fixed windows of ids
+
+constexpr int kGroupWindow = 128;  // the ids one block of the pass covers per grid-stride step
+
+// perm[new] = old inside each window of kGroupWindow consecutive ids: the
+// window's nodes by (incident triangles, degree), fixed nodes last, ties by
+// id (a stable counting rank over the window's keys in shared memory).
+__global__ void __launch_bounds__(kGroupWindow) window_order_kernel(const uint32_t *__restrict__ node_off,
+                                                                    const uint32_t *__restrict__ adj, int64_t n,
+                                                                    uint32_t *__restrict__ perm)
+{
+    __shared__ uint32_t key[kGroupWindow];
+    const int t = threadIdx.x;
+    const int64_t nwin = (n + kGroupWindow - 1) / kGroupWindow;
+    for (int64_t w = blockIdx.x; w < nwin; w += gridDim.x) {
+        const int64_t base = w * kGroupWindow;
+        const int len = n - base < kGroupWindow ? (int)(n - base) : kGroupWindow;
+        uint32_t k = 0xffffffffu;
+        if (t < len) {
+            const uint32_t meta = __ldg(adj + __ldg(node_off + base + t));
+            k = (meta & kMetaFixed) ? 0xfffffffeu : (meta_ntri(meta) << 16) | meta_degree(meta);
+        }
+        key[t] = k;
+        __syncthreads();
+        if (t < len) {
+            int r = 0;
+            for (int u = 0; u < len; ++u) {
+                const uint32_t ku = key[u];
+                r += (ku < k || (ku == k && u < t)) ? 1 : 0;
+            }
+            perm[base + r] = (uint32_t)(base + t);
+        }
+        __syncthreads();
+    }
+}
+
+// Neighbour ids of every record renumbered where the record lies (Form A
+// keeps its records in place; the list order, hence the summation order, is
+// unchanged).
+__global__ void remap_in_place_kernel(const uint32_t *__restrict__ node_off, uint32_t *__restrict__ adj, int64_t n,
+                                      const uint32_t *__restrict__ inv)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t *rec = adj + node_off[i];
+        const uint32_t meta = rec[0];
+        if (meta & kMetaFixed) continue;
+        const uint32_t deg = meta_degree(meta);
+        for (uint32_t w = 1; w <= deg; ++w) rec[w] = inv[rec[w]];
+    }
+}
+
+// off_new[k] = off_old[perm[k]]: new node k keeps old node perm[k]'s record;
+// off_new[n] = off_old[n] (the word count).
+__global__ void permute_offsets_kernel(const uint32_t *__restrict__ off_old, const uint32_t *__restrict__ perm,
+                                       int64_t n, uint32_t *__restrict__ off_new)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += stride)
+        off_new[k] = k < n ? off_old[perm[k]] : off_old[n];
+}
+
 }  // namespace
+
+// Renumbers the mesh by M->perm (new id -> caller's id, a permutation of
+// [0, n) already on the device): fills M->inv and replaces the adjacency (the
+// records in the new order, neighbour ids renumbered, each list's order
+// kept, so every pass sums and tests exactly as before), the triangles and
+// both coordinate arrays (which hold the creation coordinates).
+static sls_status apply_renumbering(sls_mesh *M, cudaStream_t s)
+{
+    const int64_t n = M->n;
+    const int grid = device_sm_count() * 8, block = 256;
+    GB_TRY(cudaMalloc(&M->inv, sizeof(uint32_t) * (size_t)n), "renumbering");
+    DevBuf b_len, b_off, b_adj;
+    unsigned *len = nullptr;
+    uint32_t *off_new = nullptr, *adj_new = nullptr;
+    sls_status st;
+    if ((st = dalloc(b_len, (size_t)n + 1, &len, "renumbering")) != SLS_OK) return st;
+    inverse_kernel<<<grid, block, 0, s>>>(M->perm, n, M->inv);
+    record_len_kernel<<<grid, block, 0, s>>>(M->node_off, M->perm, n, len);
+    GB_TRY(cudaGetLastError(), "renumbering");
+    if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering")) != SLS_OK) return st;
+    unsigned long long words = 0ull;
+    if ((st = scan_u32(len, n, off_new, &words, s)) != SLS_OK) return st;
+    if (words != M->adj_words) return fail(SLS_ERR_INVALID, "adjacency size mismatch in the renumbering");
+    if ((st = dalloc(b_adj, (size_t)words, &adj_new, "renumbering")) != SLS_OK) return st;
+    remap_adj_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, M->perm, M->inv, off_new, n, adj_new);
+    remap_ids_kernel<<<grid, block, 0, s>>>(M->tri, 3 * M->m, M->inv);
+    GB_TRY(cudaGetLastError(), "renumbering");
+    GB_TRY(launch_permute_coords(M->xy[0], M->xy[1], M->opt.layout, M->f32, n, M->perm, grid, s), "renumbering");
+    GB_TRY(cudaMemcpyAsync(M->xy[0], M->xy[1], (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)n,
+                           cudaMemcpyDeviceToDevice, s), "renumbering");
+    GB_TRY(cudaStreamSynchronize(s), "renumbering");
+    cudaFree(M->node_off);
+    cudaFree(M->adj);
+    M->node_off = off_new;
+    M->adj = adj_new;
+    b_off.p = nullptr;  // now the mesh's
+    b_adj.p = nullptr;
+    return SLS_OK;
+}
+
+// Form A: groups the nodes of every window of kGroupWindow consecutive ids
+// by incident-triangle count and degree.  The pass's neighbour loop runs to
+// the largest degree in a warp and its triangle loop to the largest count
+// (the lanes run in step), so 32 nodes of similar counts spend fewer idle
+// trips; the windows are the id ranges a block covers together, so their
+// gathers share the block's L1 as before.
+//
+// The records stay where they are (a window's records are contiguous either
+// way): only their neighbour ids are renumbered, and the offsets permuted.
+static sls_status group_by_degree(sls_mesh *M, cudaStream_t s)
+{
+    const int64_t n = M->n;
+    const int grid = device_sm_count() * 8, block = 256;
+    GB_TRY(cudaMalloc(&M->perm, sizeof(uint32_t) * (size_t)n), "renumbering");
+    GB_TRY(cudaMalloc(&M->inv, sizeof(uint32_t) * (size_t)n), "renumbering");
+    DevBuf b_off;
+    uint32_t *off_new = nullptr;
+    sls_status st;
+    if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering")) != SLS_OK) return st;
+    const int64_t nwin = (n + kGroupWindow - 1) / kGroupWindow;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    window_order_kernel<<<(unsigned)(nwin < cap ? nwin : cap), kGroupWindow, 0, s>>>(M->node_off, M->adj, n,
+                                                                                    M->perm);
+    inverse_kernel<<<grid, block, 0, s>>>(M->perm, n, M->inv);
+    remap_in_place_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, n, M->inv);
+    permute_offsets_kernel<<<grid, block, 0, s>>>(M->node_off, M->perm, n, off_new);
+    remap_ids_kernel<<<grid, block, 0, s>>>(M->tri, 3 * M->m, M->inv);
+    GB_TRY(cudaGetLastError(), "renumbering");
+    GB_TRY(launch_permute_coords(M->xy[0], M->xy[1], M->opt.layout, M->f32, n, M->perm, grid, s), "renumbering");
+    GB_TRY(cudaMemcpyAsync(M->xy[0], M->xy[1], (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)n,
+                           cudaMemcpyDeviceToDevice, s), "renumbering");
+    GB_TRY(cudaStreamSynchronize(s), "renumbering");
+    cudaFree(M->node_off);
+    M->node_off = off_new;
+    b_off.p = nullptr;  // now the mesh's
+    return SLS_OK;
+}
 
 // Form B: renumbers the mesh so that every colour class is a contiguous id
 // range (the classes in order, each in its old id order, then the fixed
@@ -667,14 +807,13 @@ sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
     const int64_t n = M->n;
     const int grid = device_sm_count() * 8, block = 256;
     GB_TRY(cudaMalloc(&M->perm, sizeof(uint32_t) * (size_t)n), "renumbering");
-    GB_TRY(cudaMalloc(&M->inv, sizeof(uint32_t) * (size_t)n), "renumbering");
     // the free nodes by class: the processing order already lists them so
     if (M->n_free > 0)
         GB_TRY(cudaMemcpyAsync(M->perm, M->node_order, sizeof(uint32_t) * (size_t)M->n_free,
                                cudaMemcpyDeviceToDevice, s), "renumbering");
-    DevBuf b_flag, b_scan, b_off, b_adj;
+    DevBuf b_flag, b_scan;
     unsigned *flag = nullptr;
-    uint32_t *scan = nullptr, *off_new = nullptr, *adj_new = nullptr;
+    uint32_t *scan = nullptr;
     sls_status st;
     if ((st = dalloc(b_flag, (size_t)n + 1, &flag, "renumbering")) != SLS_OK) return st;
     if ((st = dalloc(b_scan, (size_t)n + 1, &scan, "renumbering")) != SLS_OK) return st;
@@ -684,28 +823,8 @@ sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
     if ((st = scan_u32(flag, n, scan, &nfixed, s)) != SLS_OK) return st;
     if ((int64_t)nfixed + M->n_free != n) return fail(SLS_ERR_INVALID, "node count mismatch in the renumbering");
     compact_kernel<<<grid, block, 0, s>>>(flag, scan, n, M->n_free, M->perm);
-    inverse_kernel<<<grid, block, 0, s>>>(M->perm, n, M->inv);
-    record_len_kernel<<<grid, block, 0, s>>>(M->node_off, M->perm, n, flag);
     GB_TRY(cudaGetLastError(), "renumbering");
-    if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering")) != SLS_OK) return st;
-    unsigned long long words = 0ull;
-    if ((st = scan_u32(flag, n, off_new, &words, s)) != SLS_OK) return st;
-    if (words != M->adj_words) return fail(SLS_ERR_INVALID, "adjacency size mismatch in the renumbering");
-    if ((st = dalloc(b_adj, (size_t)words, &adj_new, "renumbering")) != SLS_OK) return st;
-    remap_adj_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, M->perm, M->inv, off_new, n, adj_new);
-    remap_ids_kernel<<<grid, block, 0, s>>>(M->tri, 3 * M->m, M->inv);
-    GB_TRY(cudaGetLastError(), "renumbering");
-    // coordinates: both arrays hold the creation coordinates
-    GB_TRY(launch_permute_coords(M->xy[0], M->xy[1], M->opt.layout, M->f32, n, M->perm, grid, s), "renumbering");
-    GB_TRY(cudaMemcpyAsync(M->xy[0], M->xy[1], (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)n,
-                           cudaMemcpyDeviceToDevice, s), "renumbering");
-    GB_TRY(cudaStreamSynchronize(s), "renumbering");
-    cudaFree(M->node_off);
-    cudaFree(M->adj);
-    M->node_off = off_new;
-    M->adj = adj_new;
-    b_off.p = nullptr;  // now the mesh's
-    b_adj.p = nullptr;
+    if ((st = apply_renumbering(M, s)) != SLS_OK) return st;
     cudaFree(M->node_order);
     M->node_order = nullptr;
     return SLS_OK;
@@ -714,7 +833,10 @@ sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
 sls_status build_node_order(sls_mesh *M, cudaStream_t s)
 {
     // Form A visits every node in index order: no list needed
-    if (M->opt.form != 1) return SLS_OK;
+    if (M->opt.form != 1) {
+        if (M->opt.keep_numbering || M->opt.skip_unchanged) return SLS_OK;
+        return group_by_degree(M, s);
+    }
     GB_TRY(cudaMalloc(&M->node_order, sizeof(uint32_t) * (size_t)(M->n_free > 0 ? M->n_free : 1)),
            "processing order");
     // Form B: Jones-Plassmann colouring, then one order segment per colour

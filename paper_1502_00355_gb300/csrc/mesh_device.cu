@@ -368,16 +368,22 @@ sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device)
     const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
     const double *src = M->xy[M->cur];
     if (M->perm) {
-        // renumbered mesh: back to the caller's numbering (and to interleaved doubles) on the device
-        double *d = xy_out;
+        // renumbered mesh: back to the caller's numbering (and to interleaved
+        // doubles) on the device.  For a host destination an FP64 mesh stages
+        // it in its other coordinate array (nothing reads that array before a
+        // pass rewrites its free nodes) and then copies the current one back
+        // over it, so that its fixed nodes hold their values again
+        const bool stage = !dst_is_device && !M->f32;
+        double *d = dst_is_device ? xy_out : (stage ? M->xy[M->cur ^ 1] : nullptr);
         sls_status st;
-        if (!dst_is_device && (st = dev_alloc((void **)&d, cbytes, "download")) != SLS_OK) return st;
+        if (!d && (st = dev_alloc((void **)&d, cbytes, "download")) != SLS_OK) return st;
         cudaError_t e = launch_unpermute_to_aos(src, M->opt.layout, M->f32, M->n, M->perm, d,
                                                 device_sm_count() * 4, M->stream);
         if (e == cudaSuccess && !dst_is_device)
             e = cudaMemcpyAsync(xy_out, d, cbytes, cudaMemcpyDeviceToHost, M->stream);
+        if (e == cudaSuccess && stage) e = cudaMemcpyAsync(d, src, cbytes, cudaMemcpyDeviceToDevice, M->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
-        if (!dst_is_device) cudaFree(d);
+        if (!dst_is_device && !stage) cudaFree(d);
         if (e != cudaSuccess) return cuda_fail(e, "download coordinates");
         return SLS_OK;
     }
@@ -480,7 +486,7 @@ sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
 sls_status mesh_transfer_nodes(sls_mesh *M, const int32_t *idx, int64_t k, double *buf, bool scatter)
 {
     if (M->f32) return fail(SLS_ERR_INVALID, "node gather/scatter needs an FP64 mesh");
-    if (M->perm) return fail(SLS_ERR_INVALID, "node gather/scatter needs a Form-A mesh");
+    if (M->opt.form != 0) return fail(SLS_ERR_INVALID, "node gather/scatter needs a Form-A mesh");
     if (k == 0) return SLS_OK;
     if (!M->xfer_bad) {
         sls_status st = dev_alloc((void **)&M->xfer_bad, sizeof(unsigned), "transfer flag");
@@ -489,11 +495,11 @@ sls_status mesh_transfer_nodes(sls_mesh *M, const int32_t *idx, int64_t k, doubl
     const int grid = device_sm_count() * 4;
     SLS_CUDA_TRY(cudaMemsetAsync(M->xfer_bad, 0, sizeof(unsigned), M->stream), "transfer");
     if (scatter)
-        SLS_CUDA_TRY(launch_scatter_nodes(M->xy[0], M->xy[1], M->opt.layout, M->n, idx, k, buf, M->xfer_bad,
-                                          grid, M->stream), "scatter");
+        SLS_CUDA_TRY(launch_scatter_nodes(M->xy[0], M->xy[1], M->opt.layout, M->n, idx, k, M->inv, buf,
+                                          M->xfer_bad, grid, M->stream), "scatter");
     else
-        SLS_CUDA_TRY(launch_gather_nodes(M->xy[M->cur], M->opt.layout, M->n, idx, k, buf, M->xfer_bad, grid,
-                                         M->stream), "gather");
+        SLS_CUDA_TRY(launch_gather_nodes(M->xy[M->cur], M->opt.layout, M->n, idx, k, M->inv, buf, M->xfer_bad,
+                                         grid, M->stream), "gather");
     SLS_CUDA_TRY(cudaMemcpyAsync(M->h_stats, M->xfer_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, M->stream),
                  "transfer");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "transfer");

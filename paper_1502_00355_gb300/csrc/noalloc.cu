@@ -97,8 +97,14 @@ extern "C" sls_status sls_smooth_noalloc(const sls_mesh *M, double *xy_in, doubl
     if (max_iter > 0) {
         e = cudaMemsetAsync(stats, 0, sizeof(PassStats) * (size_t)max_iter, s);
         if (e != cudaSuccess) return cuda_fail(e, "clear the pass statistics");
-        // passes never write fixed nodes, so both buffers must start equal
-        e = cudaMemcpyAsync(xy_out, xy_in, cbytes, cudaMemcpyDeviceToDevice, s);
+        if (M->perm) {
+            // a mesh renumbered inside the library: the start into its numbering
+            e = launch_permute_coords(xy_in, xy_out, 0, false, M->n, M->perm, device_sm_count() * 4, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(xy_in, xy_out, cbytes, cudaMemcpyDeviceToDevice, s);
+        } else {
+            // passes never write fixed nodes, so both buffers must start equal
+            e = cudaMemcpyAsync(xy_out, xy_in, cbytes, cudaMemcpyDeviceToDevice, s);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "copy the starting coordinates");
     }
     const bool tol_active = tol_rel > 0.0;
@@ -154,8 +160,15 @@ extern "C" sls_status sls_smooth_noalloc(const sls_mesh *M, double *xy_in, doubl
             ++it;
         }
     }
-    // the result of pass it-1 is in buf[it & 1]; make xy_out hold it
-    if ((it & 1) == 0) {
+    // the result of pass it-1 is in buf[it & 1]; make xy_out hold it (in the
+    // caller's numbering: a renumbered mesh's result goes back through xy_in)
+    if (M->perm && max_iter > 0) {
+        e = (it & 1) ? cudaMemcpyAsync(xy_in, xy_out, cbytes, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
+        if (e == cudaSuccess)
+            e = launch_unpermute_to_aos(xy_in, 0, false, M->n, M->perm, xy_out, device_sm_count() * 4, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy the result");
+    } else if ((it & 1) == 0) {
         e = cudaMemcpyAsync(xy_out, xy_in, cbytes, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "copy the result");

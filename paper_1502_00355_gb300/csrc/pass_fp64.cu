@@ -161,7 +161,8 @@ namespace {
 // of a domain-decomposed mesh); an id outside [0, n) sets *bad and is skipped.
 template <int LAYOUT>
 __global__ void gather_nodes_kernel(const double *__restrict__ xy, int64_t n, const int32_t *__restrict__ idx,
-                                    int64_t k, double2 *__restrict__ out, unsigned *bad)
+                                    int64_t k, const uint32_t *__restrict__ inv, double2 *__restrict__ out,
+                                    unsigned *bad)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += stride) {
@@ -170,14 +171,15 @@ __global__ void gather_nodes_kernel(const double *__restrict__ xy, int64_t n, co
             atomicOr(bad, 1u);
             continue;
         }
-        out[t] = Coords<LAYOUT>::get(xy, n, i);
+        out[t] = Coords<LAYOUT>::get(xy, n, inv ? (int64_t)__ldg(inv + i) : (int64_t)i);
     }
 }
 
 // The listed nodes' coordinates written into both arrays of the ping-pong.
 template <int LAYOUT>
 __global__ void scatter_nodes_kernel(double *xy0, double *xy1, int64_t n, const int32_t *__restrict__ idx,
-                                     int64_t k, const double2 *__restrict__ in, unsigned *bad)
+                                     int64_t k, const uint32_t *__restrict__ inv, const double2 *__restrict__ in,
+                                     unsigned *bad)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += stride) {
@@ -187,33 +189,34 @@ __global__ void scatter_nodes_kernel(double *xy0, double *xy1, int64_t n, const 
             continue;
         }
         const double2 v = __ldg(in + t);
-        Coords<LAYOUT>::put(xy0, n, i, v);
-        Coords<LAYOUT>::put(xy1, n, i, v);
+        const int64_t j = inv ? (int64_t)__ldg(inv + i) : (int64_t)i;
+        Coords<LAYOUT>::put(xy0, n, j, v);
+        Coords<LAYOUT>::put(xy1, n, j, v);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_gather_nodes(const double *xy, int layout, int64_t n, const int32_t *idx, int64_t k,
-                                double *out, unsigned *bad, int grid, cudaStream_t s)
+                                const uint32_t *inv, double *out, unsigned *bad, int grid, cudaStream_t s)
 {
     if (k <= 0) return cudaSuccess;
     if (layout == 0)
-        gather_nodes_kernel<0><<<grid, 256, 0, s>>>(xy, n, idx, k, reinterpret_cast<double2 *>(out), bad);
+        gather_nodes_kernel<0><<<grid, 256, 0, s>>>(xy, n, idx, k, inv, reinterpret_cast<double2 *>(out), bad);
     else
-        gather_nodes_kernel<1><<<grid, 256, 0, s>>>(xy, n, idx, k, reinterpret_cast<double2 *>(out), bad);
+        gather_nodes_kernel<1><<<grid, 256, 0, s>>>(xy, n, idx, k, inv, reinterpret_cast<double2 *>(out), bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_nodes(double *xy0, double *xy1, int layout, int64_t n, const int32_t *idx, int64_t k,
-                                 const double *in, unsigned *bad, int grid, cudaStream_t s)
+                                 const uint32_t *inv, const double *in, unsigned *bad, int grid, cudaStream_t s)
 {
     if (k <= 0) return cudaSuccess;
     const double2 *v = reinterpret_cast<const double2 *>(in);
     if (layout == 0)
-        scatter_nodes_kernel<0><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, v, bad);
+        scatter_nodes_kernel<0><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, inv, v, bad);
     else
-        scatter_nodes_kernel<1><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, v, bad);
+        scatter_nodes_kernel<1><<<grid, 256, 0, s>>>(xy0, xy1, n, idx, k, inv, v, bad);
     return cudaGetLastError();
 }
 

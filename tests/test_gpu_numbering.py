@@ -1,0 +1,126 @@
+"""The library's internal numbering of Form-A meshes (nodes grouped by
+incident-triangle count inside windows of 128 ids, keep_numbering = 0, the
+default) against the caller's numbering (keep_numbering = 1) and the oracle:
+coordinates, decisions, statistics, the histogram and every entry point that
+takes node ids or coordinates in the caller's numbering must be unchanged."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1502_00355_gb300 as mod
+    mod.build()
+    mod.lib()
+    return mod
+
+
+MESHES = {
+    # ragged last window (n not a multiple of 128), random diagonals: degrees 4-8
+    "grid_ragged": lambda: meshgen.jittered_grid(97, 61, 0.35, 21, pull_fraction=0.05, pull_centres=32),
+    # the paper's family: degrees 3 to about 12, random numbering
+    "delaunay_random": lambda: meshgen.delaunay_random(5000, 4, numbering="random"),
+    # fewer nodes than one window
+    "tiny": lambda: meshgen.jittered_grid(9, 7, 0.3, 2),
+}
+
+
+def _run(sls, mesh, iters, tol, **opts):
+    with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, record_accept=True, **opts) as g:
+        info = g.smooth(iters, tol)
+        return g.coords(), info, g.accept_mask(), g.histogram(16)
+
+
+@pytest.mark.parametrize("name", sorted(MESHES))
+@pytest.mark.parametrize("opts", [dict(), dict(layout="soa"), dict(copy_back=True), dict(kernel="fp64"),
+                                  dict(strict=True)], ids=["aos", "soa", "copy_back", "fp64", "strict"])
+def test_grouped_equals_given_and_oracle(sls, name, opts):
+    mesh = MESHES[name]()
+    xy, info, acc, hist = _run(sls, mesh, 40, 1e-9, **opts)
+    kxy, kinfo, kacc, khist = _run(sls, mesh, 40, 1e-9, keep_numbering=True, **opts)
+    assert np.array_equal(xy, kxy)
+    assert np.array_equal(acc, kacc)
+    for key in ("iterations", "converged", "accepted_last", "maxd2_last", "fp64_fallbacks"):
+        assert info[key] == kinfo[key], key
+    # counts and minimum exact; the mean is a sum of atomic additions, whose
+    # order varies from run to run
+    assert np.array_equal(hist[0], khist[0]) and hist[1] == khist[1]
+    assert abs(hist[2] - khist[2]) <= 1e-12 * abs(khist[2])
+    rxy, rinfo, racc = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary).smooth(
+        mesh.xy, 40, tol=1e-9, strict=opts.get("strict", False))
+    assert np.array_equal(xy, rxy)
+    assert info["iterations"] == rinfo["iterations"]
+    assert np.array_equal(acc, racc)
+
+
+def test_binary32_grouped(sls):
+    mesh = MESHES["grid_ragged"]()
+    a = _run(sls, mesh, 25, 0.0, precision=32)
+    b = _run(sls, mesh, 25, 0.0, precision=32, keep_numbering=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+
+
+def test_set_coords_and_device_transfers(sls):
+    import torch
+    mesh = MESHES["delaunay_random"]()
+    rng = np.random.default_rng(5)
+    start = mesh.xy + np.where(mesh.boundary[:, None] == 0, rng.uniform(-1e-3, 1e-3, mesh.xy.shape), 0.0)
+    outs = []
+    for keep in (False, True):
+        with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, keep_numbering=keep) as g:
+            g.set_coords(start)
+            assert np.array_equal(g.coords(), start)
+            g.smooth(7)
+            dev = g.coords_device()
+            g.set_coords(dev * 1.0)                      # device round trip in the caller's numbering
+            g.smooth(5)
+            idx = torch.tensor([0, 17, mesh.n - 1, 4321], dtype=torch.int32, device="cuda")
+            got = torch.empty((4, 2), dtype=torch.float64, device="cuda")
+            g.gather(idx, got)
+            assert np.array_equal(got.cpu().numpy(), g.coords()[[0, 17, mesh.n - 1, 4321]])
+            g.scatter(idx[:2], got[:2] + 0.25)
+            xy = g.coords()
+            assert np.array_equal(xy[[0, 17]], got[:2].cpu().numpy() + 0.25)
+            outs.append(xy)
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_noalloc_and_batch_on_grouped_meshes(sls):
+    import torch
+    mesh = MESHES["grid_ragged"]()
+    ref_xy, ref_info, _ = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary).smooth(mesh.xy, 31, tol=1e-12)
+    for passes in (30, 31):  # the result ends in either buffer
+        with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary) as g:
+            xin = torch.from_numpy(mesh.xy.copy()).cuda()
+            xout = torch.empty_like(xin)
+            info = g.smooth_noalloc(xin, xout, passes)
+            want, _, _ = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary).smooth(mesh.xy, passes)
+            assert info["iterations"] == passes
+            assert np.array_equal(xout.cpu().numpy(), want)
+    meshes = [sls.Mesh(m.xy, m.tri, m.boundary) for m in (mesh, MESHES["delaunay_random"](), MESHES["tiny"]())]
+    try:
+        with sls.Batch(meshes, [31, 12, 9], [1e-12, 0.0, 0.0]) as b:
+            b.smooth()
+            assert np.array_equal(b.coords(0), ref_xy)
+            m1 = MESHES["delaunay_random"]()
+            want, _, _ = oracle.OracleMesh(m1.xy, m1.tri, m1.boundary).smooth(m1.xy, 12)
+            assert np.array_equal(b.coords(1), want)
+    finally:
+        for g in meshes:
+            g.close()
+
+
+def test_skip_unchanged_keeps_the_callers_numbering(sls):
+    # grouping is not applied with skip_unchanged; results equal either way
+    mesh = MESHES["grid_ragged"]()
+    a = _run(sls, mesh, 60, 1e-9, skip_unchanged=True)
+    b = _run(sls, mesh, 60, 1e-9)
+    assert np.array_equal(a[0], b[0]) and a[1]["iterations"] == b[1]["iterations"]
