@@ -42,16 +42,18 @@ CSRC = os.path.join(ROOT, "paper_1502_00355_gb300", "csrc")
 # figures no longer describe the kernel and the bench line reports null.
 PROFILE_FIGURES = {
     "pass_screened": {
-        "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh"],
-        "sha256": "384a301409e6b085a6028b237862f2cc929b6302feee999f1e4ebccba2e05574",
-        "dram_bytes_per_node": 361.5e6 / (2048 * 2048),
-        "fp64_warp_inst_per_32_nodes": 19.0 + 5.9 + 1.2,
+        "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh",
+                  "mesh_build_gpu.cu"],
+        "sha256": "1b435e1ad0c450bbee7454199b2beca18cb7ee273ed919ef1b1dc63a8bdc0674",
+        "dram_bytes_per_node": (309189376 + 54080512) / (2048 * 2048),
+        "fp64_warp_inst_per_32_nodes": (2132648 + 795086 + 157073) / (2048 * 2048 / 32),
         "source": "profiles/pass_screened_grid2048.md (2048x2048 capture, per node)",
     },
     "batch_pass": {
-        "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu"],
-        "sha256": "e9cfa0127b9c51c4bf2a50834364281a4bedc6b4d08fe2e8cc319c95a0e02714",
-        "dram_per_alg_byte": (908991488 + 169472768) / 994046024,
+        "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu",
+                  "mesh_build_gpu.cu"],
+        "sha256": "33ee460188345b7951690d62ea18054644f335d25da7bfc5bec7610a9ebf0b3f",
+        "dram_per_alg_byte": (1007816192 + 171327488) / 994046024,
         "source": "profiles/batch_pass_batch256.md (round 0 of a 256-mesh batch, scaled by algorithmic bytes)",
     },
 }
