@@ -281,8 +281,11 @@ sls_status sls_batch_destroy(sls_batch *batch);
  * built on the device (the jobs whose inputs the server still holds in host
  * memory) that sls_submit accepts (0 = unlimited); beyond it sls_submit
  * returns SLS_ERR_BUSY.  opt: FP64 Form A with the AoS layout only
- * (SLS_ERR_INVALID otherwise).  The default memory pool of the device is set
- * to keep freed memory (release threshold: unlimited). */
+ * (SLS_ERR_INVALID otherwise); with keep_numbering = 0 (the default) every
+ * job is renumbered inside the server as a single mesh is (results in the
+ * caller's numbering; 4 bytes per node more while the job is held).  The
+ * default memory pool of the device is set to keep freed memory (release
+ * threshold: unlimited). */
 sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_options *opt,
                              sls_server **out);
 

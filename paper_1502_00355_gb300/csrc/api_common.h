@@ -79,6 +79,13 @@ struct DeviceAdjacency {
 // SLS_ERR_NOT_FOUND = a node is in too many triangles: use the host build.
 sls_status build_device_adjacency(int64_t n, int64_t m, const double *d_xy, const int32_t *d_tri,
                                   const uint8_t *h_boundary, bool async, cudaStream_t s, DeviceAdjacency &out);
+// Form A's grouped numbering of a built adjacency (mesh_build_gpu.cu): nodes
+// listed by incident-triangle count and degree inside windows of 128 ids;
+// neighbour ids renumbered in place, *node_off replaced by the permuted
+// offsets; *perm_out (new -> old id) and, if inv_out is not NULL, *inv_out
+// (old -> new) allocated as `async` says, the caller's to free.
+sls_status group_adjacency(int64_t n, uint32_t **node_off, uint32_t *adj, bool async, cudaStream_t s,
+                           uint32_t **perm_out, uint32_t **inv_out);
 // Device adjacency build of a mesh handle; SLS_ERR_NOT_FOUND = use the host build.
 sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
                              cudaStream_t s);

@@ -757,41 +757,69 @@ static sls_status apply_renumbering(sls_mesh *M, cudaStream_t s)
     return SLS_OK;
 }
 
-// Form A: groups the nodes of every window of kGroupWindow consecutive ids
-// by incident-triangle count and degree.  The pass's neighbour loop runs to
-// the largest degree in a warp and its triangle loop to the largest count
-// (the lanes run in step), so 32 nodes of similar counts spend fewer idle
-// trips; the windows are the id ranges a block covers together, so their
-// gathers share the block's L1 as before.
-//
-// The records stay where they are (a window's records are contiguous either
-// way): only their neighbour ids are renumbered, and the offsets permuted.
+// Form A's grouped numbering of a built adjacency (n nodes; *node_off and
+// adj on the device): inside every window of kGroupWindow consecutive ids
+// the nodes are listed by incident-triangle count and degree.  The pass's
+// neighbour loop runs to the largest degree in a warp and its triangle loop
+// to the largest count (the lanes run in step), so 32 nodes of similar
+// counts spend fewer idle trips; the windows are the id ranges a block covers
+// together, so their gathers share the block's L1 as before.  The records
+// stay where they are (a window's records are contiguous either way): their
+// neighbour ids are renumbered in place and *node_off is replaced by the
+// permuted offsets (the old array freed).  *perm_out (new id -> old id) and,
+// when inv_out is not NULL, *inv_out (old -> new) are allocated as `a` says
+// and owned by the caller; coordinates and triangles are the caller's to
+// move.  Stream-ordered on s; with a non-async `a` it synchronises s.
+sls_status group_adjacency(int64_t n, uint32_t **node_off, uint32_t *adj, bool async, cudaStream_t s,
+                           uint32_t **perm_out, uint32_t **inv_out)
+{
+    const Alloc al{async, s};
+    const int grid = device_sm_count() * 8, block = 256;
+    DevBuf b_perm, b_inv, b_off;
+    uint32_t *perm = nullptr, *inv = nullptr, *off_new = nullptr;
+    sls_status st;
+    if ((st = dalloc(b_perm, (size_t)n, &perm, "renumbering", al)) != SLS_OK) return st;
+    if ((st = dalloc(b_inv, (size_t)n, &inv, "renumbering", al)) != SLS_OK) return st;
+    if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering", al)) != SLS_OK) return st;
+    const int64_t nwin = (n + kGroupWindow - 1) / kGroupWindow;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    window_order_kernel<<<(unsigned)(nwin < cap ? nwin : cap), kGroupWindow, 0, s>>>(*node_off, adj, n, perm);
+    inverse_kernel<<<grid, block, 0, s>>>(perm, n, inv);
+    remap_in_place_kernel<<<grid, block, 0, s>>>(*node_off, adj, n, inv);
+    permute_offsets_kernel<<<grid, block, 0, s>>>(*node_off, perm, n, off_new);
+    GB_TRY(cudaGetLastError(), "renumbering");
+    if (async) {
+        GB_TRY(cudaFreeAsync(*node_off, s), "renumbering");
+    } else {
+        GB_TRY(cudaStreamSynchronize(s), "renumbering");
+        cudaFree(*node_off);
+    }
+    *node_off = off_new;
+    b_off.p = nullptr;
+    *perm_out = perm;
+    b_perm.p = nullptr;
+    if (inv_out) {
+        *inv_out = inv;
+        b_inv.p = nullptr;
+    }
+    return SLS_OK;
+}
+
+// A single mesh's grouped numbering (group_adjacency), with its triangles
+// and both coordinate arrays (which hold the creation coordinates) moved to
+// the new ids; fills M->perm and M->inv.
 static sls_status group_by_degree(sls_mesh *M, cudaStream_t s)
 {
     const int64_t n = M->n;
     const int grid = device_sm_count() * 8, block = 256;
-    GB_TRY(cudaMalloc(&M->perm, sizeof(uint32_t) * (size_t)n), "renumbering");
-    GB_TRY(cudaMalloc(&M->inv, sizeof(uint32_t) * (size_t)n), "renumbering");
-    DevBuf b_off;
-    uint32_t *off_new = nullptr;
-    sls_status st;
-    if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering")) != SLS_OK) return st;
-    const int64_t nwin = (n + kGroupWindow - 1) / kGroupWindow;
-    const int64_t cap = (int64_t)device_sm_count() * 16;
-    window_order_kernel<<<(unsigned)(nwin < cap ? nwin : cap), kGroupWindow, 0, s>>>(M->node_off, M->adj, n,
-                                                                                    M->perm);
-    inverse_kernel<<<grid, block, 0, s>>>(M->perm, n, M->inv);
-    remap_in_place_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, n, M->inv);
-    permute_offsets_kernel<<<grid, block, 0, s>>>(M->node_off, M->perm, n, off_new);
+    sls_status st = group_adjacency(n, &M->node_off, M->adj, false, s, &M->perm, &M->inv);
+    if (st != SLS_OK) return st;
     remap_ids_kernel<<<grid, block, 0, s>>>(M->tri, 3 * M->m, M->inv);
     GB_TRY(cudaGetLastError(), "renumbering");
     GB_TRY(launch_permute_coords(M->xy[0], M->xy[1], M->opt.layout, M->f32, n, M->perm, grid, s), "renumbering");
     GB_TRY(cudaMemcpyAsync(M->xy[0], M->xy[1], (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)n,
                            cudaMemcpyDeviceToDevice, s), "renumbering");
     GB_TRY(cudaStreamSynchronize(s), "renumbering");
-    cudaFree(M->node_off);
-    M->node_off = off_new;
-    b_off.p = nullptr;  // now the mesh's
     return SLS_OK;
 }
 

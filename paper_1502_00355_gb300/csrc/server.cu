@@ -61,6 +61,7 @@ struct ServerJob {
     // device state (stream-ordered allocations)
     double *d_xy[2] = {nullptr, nullptr};
     uint32_t *d_off = nullptr, *d_adj = nullptr;
+    uint32_t *d_perm = nullptr;  // grouped numbering: internal id -> the caller's id (NULL: none)
     PassStats *d_stats = nullptr;
     cudaStream_t build_stream = nullptr;  // the builder stream the memory was allocated on
     cudaEvent_t uploaded = nullptr;
@@ -127,20 +128,21 @@ struct sls_server {
 namespace {
 
 // Device bytes a job holds once built: two coordinate arrays, node offsets,
-// adjacency words, one statistics record per pass.
+// adjacency words, the numbering map, one statistics record per pass.
 size_t built_footprint(int64_t n, uint64_t adj_words, int32_t max_iter)
 {
     return 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1) + sizeof(uint32_t) * adj_words +
-           sizeof(PassStats) * (size_t)std::max(1, max_iter);
+           sizeof(uint32_t) * (size_t)n + sizeof(PassStats) * (size_t)std::max(1, max_iter);
 }
 
 // A bound on what a job holds while it is built: the built footprint with
 // at most n + 9m adjacency words (a meta word per node; per corner of a
 // triangle at most two neighbours and one triangle code), plus the build's
-// scratch (triangles, incidences, neighbour candidates, counts and flags).
+// scratch (triangles, incidences, neighbour candidates, counts and flags;
+// the numbering's inverse map and new offsets).
 size_t admission_bound(int64_t n, int64_t m, int32_t max_iter)
 {
-    return built_footprint(n, (uint64_t)(n + 9 * m), max_iter) + 18 * (size_t)n + 48 * (size_t)m + 65536;
+    return built_footprint(n, (uint64_t)(n + 9 * m), max_iter) + 26 * (size_t)n + 48 * (size_t)m + 65536;
 }
 
 void fail_job(sls_server *S, ServerJob &J, sls_status st, const std::string &msg)
@@ -154,11 +156,12 @@ void fail_job(sls_server *S, ServerJob &J, sls_status st, const std::string &msg
 
 void free_job_device(ServerJob &J, cudaStream_t s)
 {
-    for (void *p : {(void *)J.d_xy[0], (void *)J.d_xy[1], (void *)J.d_off, (void *)J.d_adj, (void *)J.d_stats})
+    for (void *p : {(void *)J.d_xy[0], (void *)J.d_xy[1], (void *)J.d_off, (void *)J.d_adj, (void *)J.d_perm,
+                    (void *)J.d_stats})
         if (p) cudaFreeAsync(p, s);
     if (J.uploaded) cudaEventDestroy(J.uploaded);
     J.d_xy[0] = J.d_xy[1] = nullptr;
-    J.d_off = J.d_adj = nullptr;
+    J.d_off = J.d_adj = J.d_perm = nullptr;
     J.d_stats = nullptr;
     J.uploaded = nullptr;
 }
@@ -166,7 +169,7 @@ void free_job_device(ServerJob &J, cudaStream_t s)
 // Uploads job J on stream s and builds its adjacency there.  On success the
 // job's device state is complete once J.uploaded has fired; *footprint is
 // what it holds.  On failure everything is freed behind the stream's work.
-sls_status build_job(ServerJob &J, cudaStream_t s, size_t *footprint)
+sls_status build_job(ServerJob &J, bool group, cudaStream_t s, size_t *footprint)
 {
     const int64_t n = J.n, m = J.m;
     const size_t cbytes = sizeof(double) * 2 * (size_t)n;
@@ -221,7 +224,17 @@ sls_status build_job(ServerJob &J, cudaStream_t s, size_t *footprint)
     J.diag = da.diag;
     e = cudaFreeAsync(d_tri, s);
     d_tri = nullptr;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(J.d_xy[1], J.d_xy[0], cbytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_err(e, "build");
+    if (group) {
+        // Form A's grouped numbering (as for a single mesh): the coordinates
+        // move to the new ids; the result goes back at retirement
+        st = group_adjacency(n, &J.d_off, J.d_adj, true, s, &J.d_perm, nullptr);
+        if (st != SLS_OK) return cleanup(st);
+        e = launch_permute_coords(J.d_xy[0], J.d_xy[1], 0, false, n, J.d_perm, device_sm_count() * 4, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(J.d_xy[0], J.d_xy[1], cbytes, cudaMemcpyDeviceToDevice, s);
+    } else {
+        e = cudaMemcpyAsync(J.d_xy[1], J.d_xy[0], cbytes, cudaMemcpyDeviceToDevice, s);
+    }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(J.d_stats, 0, sizeof(PassStats) * (size_t)std::max(1, J.max_iter), s);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&J.uploaded, cudaEventDisableTiming);
@@ -246,7 +259,7 @@ void builder_loop(sls_server *S, cudaStream_t s)
         }
         size_t fp = 0;
         J->build_stream = s;
-        const sls_status st = build_job(*J, s, &fp);
+        const sls_status st = build_job(*J, !S->opt.keep_numbering, s, &fp);
         const std::string err = st == SLS_OK ? std::string() : std::string(sls_last_error());
         std::lock_guard<std::mutex> lk(S->mu);
         J->xy.clear();
@@ -375,7 +388,15 @@ void retire_loop(sls_server *S)
         for (auto &Jp : batch) {
             ServerJob &J = *Jp;
             J.result.resize(2 * (size_t)J.n);
-            ok = ok && cudaMemcpyAsync(J.result.data(), J.d_xy[J.iterations & 1], sizeof(double) * J.result.size(),
+            const double *res = J.d_xy[J.iterations & 1];
+            if (J.d_perm) {
+                // back to the caller's numbering, through the idle array
+                double *d = J.d_xy[(J.iterations & 1) ^ 1];
+                ok = ok && launch_unpermute_to_aos(res, 0, false, J.n, J.d_perm, d, device_sm_count() * 4,
+                                                   S->retire_stream) == cudaSuccess;
+                res = d;
+            }
+            ok = ok && cudaMemcpyAsync(J.result.data(), res, sizeof(double) * J.result.size(),
                                        cudaMemcpyDeviceToHost, S->retire_stream) == cudaSuccess;
         }
         ok = ok && cudaStreamSynchronize(S->retire_stream) == cudaSuccess;  // one wait for the batch

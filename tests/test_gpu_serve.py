@@ -51,6 +51,20 @@ def test_served_jobs_equal_oracle_in_the_mix(sls):
     srv.close()
 
 
+def test_served_jobs_in_the_callers_numbering(sls):
+    # jobs built without the internal grouped numbering give the same bits
+    jobs = _jobs(12, 7)
+    out = []
+    for keep in (False, True):
+        srv = sls.Server(keep_numbering=keep)
+        ids = [srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=tol) for m, cap, tol in jobs]
+        out.append([srv.wait(jid, timeout=120.0) for jid in ids])
+        srv.close()
+    for (xa, ia), (xb, ib) in zip(*out):
+        assert np.array_equal(xa, xb)
+        assert ia["iterations"] == ib["iterations"] and ia["maxd2_last"] == ib["maxd2_last"]
+
+
 def test_served_concurrent_clients_and_budget(sls):
     # a small memory budget forces jobs to wait for each other; four client
     # threads submit and wait concurrently
