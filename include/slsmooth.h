@@ -115,16 +115,18 @@ typedef struct sls_options {
                               and the screened kernel (SLS_KERNEL_AUTO or _FILTERED); costs
                               140 bytes of device memory per 32 nodes.  The batched and
                               allocation-free forms compute every tile; the server rejects it. */
-    int32_t keep_numbering;/* 0 (default): a Form-A mesh is renumbered inside the library: in
-                              every window of 128 consecutive ids the nodes are listed by
-                              incident-triangle count, then degree (fixed nodes last, ties by
-                              id), so that the 32 lanes of a warp run loops of similar length
-                              (the pass's loops run to the warp's longest).  The windows stay
-                              where they are, so the gathers keep their locality.  Not done
-                              with skip_unchanged (its 32-node tiles would lose theirs).
-                              Every call still reads and writes coordinates, decisions and
-                              node ids in the caller's numbering; 8 bytes per node for the
-                              maps; results are identical.  1: keep the caller's numbering.  */
+    int32_t numbering;     /* Form A: 0 (default) lets the library renumber a mesh of at least
+                              2^20 nodes, 1 keeps the caller's numbering, 2 renumbers at any
+                              size.  Renumbered, every window of 128 consecutive ids lists its
+                              nodes by incident-triangle count, then degree (fixed nodes last,
+                              ties by id), so that the 32 lanes of a warp run loops of similar
+                              length (the pass's loops run to the warp's longest).  The windows
+                              stay where they are, so the gathers keep their locality.  Costs
+                              two kernels and 8 bytes per node at creation, which only larger
+                              meshes repay.  Not done with skip_unchanged (its 32-node tiles
+                              would lose their locality).  Every call still reads and writes
+                              coordinates, decisions and node ids in the caller's numbering;
+                              results are identical.                                         */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle    */
 } sls_options;
 
@@ -281,9 +283,9 @@ sls_status sls_batch_destroy(sls_batch *batch);
  * built on the device (the jobs whose inputs the server still holds in host
  * memory) that sls_submit accepts (0 = unlimited); beyond it sls_submit
  * returns SLS_ERR_BUSY.  opt: FP64 Form A with the AoS layout only
- * (SLS_ERR_INVALID otherwise); with keep_numbering = 0 (the default) every
- * job is renumbered inside the server as a single mesh is (results in the
- * caller's numbering; 4 bytes per node more while the job is held).  The
+ * (SLS_ERR_INVALID otherwise).  opt's numbering applies to every job as to a
+ * single mesh (results in the caller's numbering; a renumbered job holds 4
+ * bytes per node more).  The
  * default memory pool of the device is set to keep freed memory (release
  * threshold: unlimited). */
 sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_options *opt,
@@ -333,7 +335,7 @@ sls_status sls_server_destroy(sls_server *srv);
  *            used or changed, and its copy_back, skip_unchanged, l2_window and
  *            record_accept options are not applied (the results are the
  *            same: those options never change them).  When the library
- *            renumbered the mesh (keep_numbering = 0) two more kernels map
+ *            renumbered the mesh (see numbering) two more kernels map
  *            the coordinates into its numbering and back; both buffers are
  *            in the caller's numbering
  *   xy_in    device, 2n float64 interleaved: the starting coordinates; also

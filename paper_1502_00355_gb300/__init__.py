@@ -35,7 +35,7 @@ class Options(C.Structure):
                 ("kernel", C.c_int32), ("record_accept", C.c_int32), ("block_size", C.c_int32),
                 ("l2_window", C.c_int32), ("passes_per_check", C.c_int32), ("host_build", C.c_int32),
                 ("form", C.c_int32), ("precision", C.c_int32), ("skip_unchanged", C.c_int32),
-                ("keep_numbering", C.c_int32), ("stream", C.c_void_p)]
+                ("numbering", C.c_int32), ("stream", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -119,7 +119,7 @@ def _p(a: np.ndarray | None):
 
 def make_options(*, strict=False, copy_back=False, layout="aos", kernel="auto", record_accept=False,
                  block_size=0, l2_window=False, passes_per_check=0, host_build=False, form="A",
-                 precision=64, skip_unchanged=False, keep_numbering=False, stream=None) -> Options:
+                 precision=64, skip_unchanged=False, numbering="auto", stream=None) -> Options:
     o = Options()
     lib().sls_default_options(C.byref(o))
     o.accept_strict = int(bool(strict))
@@ -134,7 +134,7 @@ def make_options(*, strict=False, copy_back=False, layout="aos", kernel="auto", 
     o.form = {"A": 0, "B": 1}[form]
     o.precision = int(precision)
     o.skip_unchanged = int(bool(skip_unchanged))
-    o.keep_numbering = int(bool(keep_numbering))
+    o.numbering = {"auto": 0, "given": 1, "grouped": 2}[numbering] if isinstance(numbering, str) else int(numbering)
     o.stream = None if stream is None else C.c_void_p(int(stream))
     return o
 

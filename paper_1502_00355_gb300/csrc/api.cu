@@ -85,7 +85,7 @@ sls_status check_options(const sls_options &o)
     if (o.form != 0 && o.form != 1) return fail(SLS_ERR_INVALID, "form must be 0 (Form A) or 1 (Form B)");
     if (o.precision != 32 && o.precision != 64) return fail(SLS_ERR_INVALID, "precision must be 32 or 64");
     if (o.skip_unchanged != 0 && o.skip_unchanged != 1) return fail(SLS_ERR_INVALID, "skip_unchanged must be 0 or 1");
-    if (o.keep_numbering != 0 && o.keep_numbering != 1) return fail(SLS_ERR_INVALID, "keep_numbering must be 0 or 1");
+    if (o.numbering < 0 || o.numbering > 2) return fail(SLS_ERR_INVALID, "numbering must be 0, 1 or 2");
     if (o.skip_unchanged && (o.form != 0 || o.precision != 64 || o.kernel == SLS_KERNEL_FP64))
         return fail(SLS_ERR_INVALID, "skip_unchanged needs Form A, FP64 and the screened kernel");
     return SLS_OK;

@@ -86,6 +86,11 @@ sls_status build_device_adjacency(int64_t n, int64_t m, const double *d_xy, cons
 // (old -> new) allocated as `async` says, the caller's to free.
 sls_status group_adjacency(int64_t n, uint32_t **node_off, uint32_t *adj, bool async, cudaStream_t s,
                            uint32_t **perm_out, uint32_t **inv_out);
+// Whether options o renumber a Form-A mesh of n nodes (grouped numbering).
+inline bool groups_nodes(const sls_options &o, int64_t n)
+{
+    return o.form == 0 && !o.skip_unchanged && (o.numbering == 2 || (o.numbering == 0 && n >= (int64_t(1) << 20)));
+}
 // Device adjacency build of a mesh handle; SLS_ERR_NOT_FOUND = use the host build.
 sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
                              cudaStream_t s);

@@ -658,22 +658,27 @@ __global__ void remap_ids_kernel(int32_t *ids, int64_t count, const uint32_t *__
 
 constexpr int kGroupWindow = 128;  // the ids one block of the pass covers per grid-stride step
 
-// perm[new] = old inside each window of kGroupWindow consecutive ids: the
-// window's nodes by (incident triangles, degree), fixed nodes last, ties by
-// id (a stable counting rank over the window's keys in shared memory).
-__global__ void __launch_bounds__(kGroupWindow) window_order_kernel(const uint32_t *__restrict__ node_off,
+// Inside each window of kGroupWindow consecutive ids, the window's nodes by
+// (incident triangles, degree), fixed nodes last, ties by id (a stable
+// counting rank over the window's keys in shared memory): perm[new] = old,
+// inv[old] = new and off_new[new] = off_old[old], off_new[n] = off_old[n].
+__global__ void __launch_bounds__(kGroupWindow) window_group_kernel(const uint32_t *__restrict__ node_off,
                                                                     const uint32_t *__restrict__ adj, int64_t n,
-                                                                    uint32_t *__restrict__ perm)
+                                                                    uint32_t *__restrict__ perm,
+                                                                    uint32_t *__restrict__ inv,
+                                                                    uint32_t *__restrict__ off_new)
 {
     __shared__ uint32_t key[kGroupWindow];
     const int t = threadIdx.x;
     const int64_t nwin = (n + kGroupWindow - 1) / kGroupWindow;
+    if (blockIdx.x == 0 && t == 0) off_new[n] = node_off[n];
     for (int64_t w = blockIdx.x; w < nwin; w += gridDim.x) {
         const int64_t base = w * kGroupWindow;
         const int len = n - base < kGroupWindow ? (int)(n - base) : kGroupWindow;
-        uint32_t k = 0xffffffffu;
+        uint32_t k = 0xffffffffu, off = 0u;
         if (t < len) {
-            const uint32_t meta = __ldg(adj + __ldg(node_off + base + t));
+            off = __ldg(node_off + base + t);
+            const uint32_t meta = __ldg(adj + off);
             k = (meta & kMetaFixed) ? 0xfffffffeu : (meta_ntri(meta) << 16) | meta_degree(meta);
         }
         key[t] = k;
@@ -685,6 +690,8 @@ __global__ void __launch_bounds__(kGroupWindow) window_order_kernel(const uint32
                 r += (ku < k || (ku == k && u < t)) ? 1 : 0;
             }
             perm[base + r] = (uint32_t)(base + t);
+            inv[base + t] = (uint32_t)(base + r);
+            off_new[base + r] = off;
         }
         __syncthreads();
     }
@@ -704,16 +711,6 @@ __global__ void remap_in_place_kernel(const uint32_t *__restrict__ node_off, uin
         const uint32_t deg = meta_degree(meta);
         for (uint32_t w = 1; w <= deg; ++w) rec[w] = inv[rec[w]];
     }
-}
-
-// off_new[k] = off_old[perm[k]]: new node k keeps old node perm[k]'s record;
-// off_new[n] = off_old[n] (the word count).
-__global__ void permute_offsets_kernel(const uint32_t *__restrict__ off_old, const uint32_t *__restrict__ perm,
-                                       int64_t n, uint32_t *__restrict__ off_new)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += stride)
-        off_new[k] = k < n ? off_old[perm[k]] : off_old[n];
 }
 
 }  // namespace
@@ -783,10 +780,9 @@ sls_status group_adjacency(int64_t n, uint32_t **node_off, uint32_t *adj, bool a
     if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering", al)) != SLS_OK) return st;
     const int64_t nwin = (n + kGroupWindow - 1) / kGroupWindow;
     const int64_t cap = (int64_t)device_sm_count() * 16;
-    window_order_kernel<<<(unsigned)(nwin < cap ? nwin : cap), kGroupWindow, 0, s>>>(*node_off, adj, n, perm);
-    inverse_kernel<<<grid, block, 0, s>>>(perm, n, inv);
+    window_group_kernel<<<(unsigned)(nwin < cap ? nwin : cap), kGroupWindow, 0, s>>>(*node_off, adj, n, perm,
+                                                                                    inv, off_new);
     remap_in_place_kernel<<<grid, block, 0, s>>>(*node_off, adj, n, inv);
-    permute_offsets_kernel<<<grid, block, 0, s>>>(*node_off, perm, n, off_new);
     GB_TRY(cudaGetLastError(), "renumbering");
     if (async) {
         GB_TRY(cudaFreeAsync(*node_off, s), "renumbering");
@@ -862,8 +858,7 @@ sls_status build_node_order(sls_mesh *M, cudaStream_t s)
 {
     // Form A visits every node in index order: no list needed
     if (M->opt.form != 1) {
-        if (M->opt.keep_numbering || M->opt.skip_unchanged) return SLS_OK;
-        return group_by_degree(M, s);
+        return groups_nodes(M->opt, M->n) ? group_by_degree(M, s) : SLS_OK;
     }
     GB_TRY(cudaMalloc(&M->node_order, sizeof(uint32_t) * (size_t)(M->n_free > 0 ? M->n_free : 1)),
            "processing order");

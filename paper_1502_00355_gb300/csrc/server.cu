@@ -231,10 +231,9 @@ sls_status build_job(ServerJob &J, bool group, cudaStream_t s, size_t *footprint
         st = group_adjacency(n, &J.d_off, J.d_adj, true, s, &J.d_perm, nullptr);
         if (st != SLS_OK) return cleanup(st);
         e = launch_permute_coords(J.d_xy[0], J.d_xy[1], 0, false, n, J.d_perm, device_sm_count() * 4, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(J.d_xy[0], J.d_xy[1], cbytes, cudaMemcpyDeviceToDevice, s);
-    } else {
-        e = cudaMemcpyAsync(J.d_xy[1], J.d_xy[0], cbytes, cudaMemcpyDeviceToDevice, s);
+        std::swap(J.d_xy[0], J.d_xy[1]);
     }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(J.d_xy[1], J.d_xy[0], cbytes, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(J.d_stats, 0, sizeof(PassStats) * (size_t)std::max(1, J.max_iter), s);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&J.uploaded, cudaEventDisableTiming);
@@ -259,7 +258,7 @@ void builder_loop(sls_server *S, cudaStream_t s)
         }
         size_t fp = 0;
         J->build_stream = s;
-        const sls_status st = build_job(*J, !S->opt.keep_numbering, s, &fp);
+        const sls_status st = build_job(*J, groups_nodes(S->opt, J->n), s, &fp);
         const std::string err = st == SLS_OK ? std::string() : std::string(sls_last_error());
         std::lock_guard<std::mutex> lk(S->mu);
         J->xy.clear();

@@ -1,6 +1,7 @@
 """The library's internal numbering of Form-A meshes (nodes grouped by
-incident-triangle count inside windows of 128 ids, keep_numbering = 0, the
-default) against the caller's numbering (keep_numbering = 1) and the oracle:
+incident-triangle count inside windows of 128 ids: numbering = 2, and by
+default for meshes of 2^20 nodes or more) against the caller's numbering
+(numbering = 1) and the oracle:
 coordinates, decisions, statistics, the histogram and every entry point that
 takes node ids or coordinates in the caller's numbering must be unchanged."""
 import numpy as np
@@ -44,8 +45,8 @@ def _run(sls, mesh, iters, tol, **opts):
                                   dict(strict=True)], ids=["aos", "soa", "copy_back", "fp64", "strict"])
 def test_grouped_equals_given_and_oracle(sls, name, opts):
     mesh = MESHES[name]()
-    xy, info, acc, hist = _run(sls, mesh, 40, 1e-9, **opts)
-    kxy, kinfo, kacc, khist = _run(sls, mesh, 40, 1e-9, keep_numbering=True, **opts)
+    xy, info, acc, hist = _run(sls, mesh, 40, 1e-9, numbering="grouped", **opts)
+    kxy, kinfo, kacc, khist = _run(sls, mesh, 40, 1e-9, numbering="given", **opts)
     assert np.array_equal(xy, kxy)
     assert np.array_equal(acc, kacc)
     for key in ("iterations", "converged", "accepted_last", "maxd2_last", "fp64_fallbacks"):
@@ -63,8 +64,8 @@ def test_grouped_equals_given_and_oracle(sls, name, opts):
 
 def test_binary32_grouped(sls):
     mesh = MESHES["grid_ragged"]()
-    a = _run(sls, mesh, 25, 0.0, precision=32)
-    b = _run(sls, mesh, 25, 0.0, precision=32, keep_numbering=True)
+    a = _run(sls, mesh, 25, 0.0, precision=32, numbering="grouped")
+    b = _run(sls, mesh, 25, 0.0, precision=32, numbering="given")
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
 
 
@@ -74,8 +75,8 @@ def test_set_coords_and_device_transfers(sls):
     rng = np.random.default_rng(5)
     start = mesh.xy + np.where(mesh.boundary[:, None] == 0, rng.uniform(-1e-3, 1e-3, mesh.xy.shape), 0.0)
     outs = []
-    for keep in (False, True):
-        with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, keep_numbering=keep) as g:
+    for numbering in ("grouped", "given"):
+        with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, numbering=numbering) as g:
             g.set_coords(start)
             assert np.array_equal(g.coords(), start)
             g.smooth(7)
@@ -98,14 +99,14 @@ def test_noalloc_and_batch_on_grouped_meshes(sls):
     mesh = MESHES["grid_ragged"]()
     ref_xy, ref_info, _ = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary).smooth(mesh.xy, 31, tol=1e-12)
     for passes in (30, 31):  # the result ends in either buffer
-        with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary) as g:
+        with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, numbering="grouped") as g:
             xin = torch.from_numpy(mesh.xy.copy()).cuda()
             xout = torch.empty_like(xin)
             info = g.smooth_noalloc(xin, xout, passes)
             want, _, _ = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary).smooth(mesh.xy, passes)
             assert info["iterations"] == passes
             assert np.array_equal(xout.cpu().numpy(), want)
-    meshes = [sls.Mesh(m.xy, m.tri, m.boundary) for m in (mesh, MESHES["delaunay_random"](), MESHES["tiny"]())]
+    meshes = [sls.Mesh(m.xy, m.tri, m.boundary, numbering="grouped") for m in (mesh, MESHES["delaunay_random"](), MESHES["tiny"]())]
     try:
         with sls.Batch(meshes, [31, 12, 9], [1e-12, 0.0, 0.0]) as b:
             b.smooth()
@@ -119,8 +120,16 @@ def test_noalloc_and_batch_on_grouped_meshes(sls):
 
 
 def test_skip_unchanged_keeps_the_callers_numbering(sls):
-    # grouping is not applied with skip_unchanged; results equal either way
+    # grouping is not applied with skip_unchanged (even when asked for);
+    # results equal either way
     mesh = MESHES["grid_ragged"]()
-    a = _run(sls, mesh, 60, 1e-9, skip_unchanged=True)
-    b = _run(sls, mesh, 60, 1e-9)
+    a = _run(sls, mesh, 60, 1e-9, skip_unchanged=True, numbering="grouped")
+    b = _run(sls, mesh, 60, 1e-9, numbering="grouped")
     assert np.array_equal(a[0], b[0]) and a[1]["iterations"] == b[1]["iterations"]
+
+
+def test_numbering_option_checked(sls):
+    mesh = MESHES["tiny"]()
+    with pytest.raises(sls.SlsError) as e:
+        sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, numbering=3)
+    assert e.value.code == 1

@@ -55,8 +55,8 @@ def test_served_jobs_in_the_callers_numbering(sls):
     # jobs built without the internal grouped numbering give the same bits
     jobs = _jobs(12, 7)
     out = []
-    for keep in (False, True):
-        srv = sls.Server(keep_numbering=keep)
+    for numbering in ("grouped", "given"):
+        srv = sls.Server(numbering=numbering)
         ids = [srv.submit(m.xy, m.tri, m.boundary, max_iter=cap, tol=tol) for m, cap, tol in jobs]
         out.append([srv.wait(jid, timeout=120.0) for jid in ids])
         srv.close()
