@@ -294,7 +294,8 @@ def large_config(args, mesh, workload: str, world: int) -> dict:
             "l2": "inputs larger than L2 (no flush)" if mesh.n >= 4 * 1024 * 1024
             else "inputs fit L2 (no flush; see l2_hit_rate)",
             "parallelism": "replicas" if world > 1 else "single",
-            "skip_unchanged": bool(args.skip_unchanged), "l2_window": bool(args.l2_window)}
+            "skip_unchanged": bool(args.skip_unchanged), "l2_window": bool(args.l2_window),
+            "library_numbering": getattr(args, "lib_numbering", "auto")}
 
 
 def run_reference(args, mesh, workload):
@@ -395,7 +396,7 @@ def run_batch(args):
                                    f"batch{len(meshes) * world}_logu{args.batch_min_n}-{args.batch_max_n}_aspect1-4_iters10-100"),
                       "meshes_per_gpu": len(meshes), "meshes": len(meshes) * world,
                       "nodes_rank0": total_nodes, "launch_shape": {"block": batch.shape[0], "chunk": batch.shape[1]},
-                      "numbering": args.batch_numbering,
+                      "library_numbering": args.batch_numbering,
                       "parallelism": f"{world} ranks, independent meshes (no collective)" if world > 1 else "single"},
            "per_request": {"value": per_request, "unit": "node-updates/s", "seconds": per_req_s},
            "speedup_vs_per_request": batched / per_request, "identical_results": bool(same),
@@ -490,7 +491,7 @@ def run_serve(args):
     # several clients: request k is submitted by client k % clients at its
     # arrival time (each client makes its own meshes ahead of their turn), and
     # two pollers collect the results (request k by poller k % 2)
-    srv = sls.Server(max_queue=args.serve_queue)
+    srv = sls.Server(max_queue=args.serve_queue, numbering=args.lib_numbering)
     clients, pollers = max(1, args.serve_clients), 2
     pres = [Prefetch([reqs[k] for k in range(c, len(reqs), clients)], max(1, args.gen_threads // clients),
                      args.gen_depth) for c in range(clients)]
@@ -576,7 +577,7 @@ def run_serve(args):
         if now < arrivals[k]:
             time.sleep(arrivals[k] - now)
         t0 = time.perf_counter()
-        with sls.Mesh(m.xy, m.tri, m.boundary) as g:
+        with sls.Mesh(m.xy, m.tri, m.boundary, numbering=args.lib_numbering) as g:
             inf = g.smooth(caps[k], TOL)
             xy = g.coords()
         busy += time.perf_counter() - t0
@@ -609,6 +610,7 @@ def run_serve(args):
                       "offered_req_per_s_per_gpu": args.serve_rate, "nodes_rank0": int(sum(sizes)),
                       "mesh_generator": "meshgen.fast_grid (jittered grid, J = 0.3, Morton)",
                       "server_queue_limit": args.serve_queue, "clients": args.serve_clients,
+                      "library_numbering": args.lib_numbering,
                       "parallelism": f"{world} ranks, one server each (no collective)" if world > 1 else "single"},
            "served": {"p50_ms": p50, "p99_ms": p99, "wall_s": wall_ms * 1e-3,
                       "req_per_s": len(reqs) * world / (wall_ms * 1e-3),
@@ -646,6 +648,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lib-numbering", default="auto", choices=["auto", "given", "grouped"],
+                    help="node numbering inside the library (single mesh, served jobs and their FIFO baseline)")
     ap.add_argument("--batch-numbering", default="grouped", choices=["auto", "given", "grouped"],
                     help="node numbering of the batch's meshes (created once, smoothed every step)")
     ap.add_argument("--kernel", default="auto")
@@ -778,6 +782,7 @@ def run_single(args):
 
     stream = torch.cuda.Stream()
     variant = dict(kernel=args.kernel, precision=args.precision, form=args.form, layout=args.layout,
+                   numbering=args.lib_numbering,
                    copy_back=args.copy_back, skip_unchanged=args.skip_unchanged, l2_window=args.l2_window)
     g = sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, stream=stream.cuda_stream, **variant)
     xy0 = torch.from_numpy(mesh.xy).to("cuda")
