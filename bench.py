@@ -44,7 +44,7 @@ PROFILE_FIGURES = {
     "pass_screened": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh",
                   "mesh_build_gpu.cu"],
-        "sha256": "1b435e1ad0c450bbee7454199b2beca18cb7ee273ed919ef1b1dc63a8bdc0674",
+        "sha256": "f76ef0d18df380e9bf954a7820437e56e57ab0fec84c1cced71b4fe23c0a6a0f",
         "dram_bytes_per_node": (309189376 + 54080512) / (2048 * 2048),
         "fp64_warp_inst_per_32_nodes": (2132648 + 795086 + 157073) / (2048 * 2048 / 32),
         "source": "profiles/pass_screened_grid2048.md (2048x2048 capture, per node)",
@@ -52,7 +52,7 @@ PROFILE_FIGURES = {
     "batch_pass": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu",
                   "mesh_build_gpu.cu"],
-        "sha256": "33ee460188345b7951690d62ea18054644f335d25da7bfc5bec7610a9ebf0b3f",
+        "sha256": "c1e451ee9557dc81957df52d4afab0759f314275d9106164982c60a77744858a",
         "dram_per_alg_byte": (1007816192 + 171327488) / 994046024,
         "source": "profiles/batch_pass_batch256.md (round 0 of a 256-mesh batch, scaled by algorithmic bytes)",
     },
