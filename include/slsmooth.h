@@ -219,7 +219,20 @@ sls_status sls_quality_histogram(const sls_mesh *mesh, int32_t nbins, double lo,
 sls_status sls_mesh_stats(const sls_mesh *mesh, int64_t *n, int64_t *m, int64_t *n_free,
                           double *diag);
 
+/* Frees the handle.  Its device memory goes back to the library's memory
+ * pool on the device (see sls_trim_memory); returns without waiting for the
+ * device. */
 sls_status sls_mesh_destroy(sls_mesh *mesh);
+
+/* Device memory of meshes, their builds and served jobs comes from one
+ * stream-ordered memory pool per device that the library owns (the device's
+ * default pool is left alone).  Memory that destroyed handles return stays
+ * in the pool for later handles, so creating a mesh of a size seen before
+ * maps no new memory.  sls_trim_memory waits for the current device and then
+ * hands the pool's unused memory back to the driver, keeping at most
+ * keep_bytes.  Not a counterpart of anything in the paper: a memory policy of
+ * this library. */
+sls_status sls_trim_memory(size_t keep_bytes);
 
 /* ---- batched form: many meshes of uneven size, one graph launch --------
  * Each mesh keeps its own device buffers, iteration count and tolerance; the
@@ -288,9 +301,8 @@ sls_status sls_batch_destroy(sls_batch *batch);
  * per node more while held); 0 and 1 keep the caller's numbering, because the
  * server's throughput is held by its builds, which the renumbering lengthens
  * (measured: 2.5% more node-updates per second of round time, fewer
- * requests per second).  The
- * default memory pool of the device is set to keep freed memory (release
- * threshold: unlimited). */
+ * requests per second).  Jobs take their device memory from the library's
+ * pool (see sls_trim_memory). */
 sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_options *opt,
                              sls_server **out);
 

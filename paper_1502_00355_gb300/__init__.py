@@ -96,6 +96,7 @@ def lib() -> C.CDLL:
                 "sls_server_stats": (S, [P, P, P, P, P]),
                 "sls_server_destroy": (S, [P]),
                 "sls_smooth_noalloc": (S, [P, P, P, I32, D, P, P]),
+                "sls_trim_memory": (S, [C.c_size_t]),
                 "sls_status_str": (C.c_char_p, [S]),
                 "sls_last_error": (C.c_char_p, []),
             }
@@ -105,6 +106,12 @@ def lib() -> C.CDLL:
                 f.argtypes = args
             _lib = L
         return _lib
+
+
+def trim_memory(keep_bytes: int = 0):
+    """Hand the library pool's unused device memory (current device) back to
+    the driver, keeping at most keep_bytes (``sls_trim_memory``)."""
+    _check(lib().sls_trim_memory(int(keep_bytes)), "sls_trim_memory")
 
 
 def _check(code: int, where: str):

@@ -217,11 +217,11 @@ sls_status sls_get_accept(const sls_mesh *M, uint8_t *accept_out)
     if (!M->accept) return fail(SLS_ERR_INVALID, "the mesh was created without record_accept");
     if (M->perm) {  // renumbered mesh: back to the caller's numbering
         uint8_t *d = nullptr;
-        cudaError_t e = cudaMalloc((void **)&d, (size_t)M->n);
+        cudaError_t e = pool_alloc((void **)&d, (size_t)M->n, M->stream);
         if (e == cudaSuccess) e = launch_unpermute_u8(M->accept, M->n, M->perm, d, device_sm_count() * 4, M->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(accept_out, d, (size_t)M->n, cudaMemcpyDeviceToHost, M->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
-        cudaFree(d);
+        pool_free(d, M->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sls_get_accept");
         return SLS_OK;
     }

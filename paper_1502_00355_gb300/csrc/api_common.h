@@ -79,6 +79,12 @@ struct DeviceAdjacency {
 // SLS_ERR_NOT_FOUND = a node is in too many triangles: use the host build.
 sls_status build_device_adjacency(int64_t n, int64_t m, const double *d_xy, const int32_t *d_tri,
                                   const uint8_t *h_boundary, bool async, cudaStream_t s, DeviceAdjacency &out);
+// Device memory of the handles (memory.cu): stream-ordered allocations from
+// the library's pool on the current device, which keeps freed memory for
+// later handles (sls_trim_memory returns it).  Allocate and free on the
+// stream that uses the buffer; pool_free ignores NULL.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
 // Form A's grouped numbering of a built adjacency (mesh_build_gpu.cu): nodes
 // listed by incident-triangle count and degree inside windows of 128 ids;
 // neighbour ids renumbered in place, *node_off replaced by the permuted

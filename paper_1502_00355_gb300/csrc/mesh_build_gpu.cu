@@ -308,20 +308,14 @@ __global__ void scan_final_kernel(const unsigned *__restrict__ in, int64_t len,
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[len] = (uint32_t)offs[gridDim.x];
 }
 
-// A scratch buffer of the build.  With `async` it comes from the device's
-// stream-ordered pool on `s` and returns there (the served form builds jobs
-// while other streams run, and cudaFree would wait for the whole device);
-// otherwise plain cudaMalloc / cudaFree.
+// A device buffer of the build, from the library's pool on stream s (memory
+// comes and goes in stream order, so no call waits for the whole device).
+// `async` tells the build whether it may synchronise s (a single mesh's
+// build does; the served form builds jobs while rounds run).
 struct DevBuf {
     void *p = nullptr;
-    bool async = false;
     cudaStream_t s = nullptr;
-    ~DevBuf()
-    {
-        if (!p) return;
-        if (async) cudaFreeAsync(p, s);
-        else cudaFree(p);
-    }
+    ~DevBuf() { pool_free(p, s); }
 };
 
 struct Alloc {
@@ -329,10 +323,7 @@ struct Alloc {
     cudaStream_t s;
 };
 
-cudaError_t raw_alloc(const Alloc &a, void **p, size_t bytes)
-{
-    return a.async ? cudaMallocAsync(p, bytes, a.s) : cudaMalloc(p, bytes);
-}
+cudaError_t raw_alloc(const Alloc &a, void **p, size_t bytes) { return pool_alloc(p, bytes, a.s); }
 
 #define GB_TRY(expr, what)                                  \
     do {                                                    \
@@ -341,9 +332,8 @@ cudaError_t raw_alloc(const Alloc &a, void **p, size_t bytes)
     } while (0)
 
 template <class T>
-sls_status dalloc(DevBuf &b, size_t count, T **out, const char *what, const Alloc &a = Alloc{false, nullptr})
+sls_status dalloc(DevBuf &b, size_t count, T **out, const char *what, const Alloc &a)
 {
-    b.async = a.async;
     b.s = a.s;
     cudaError_t e = raw_alloc(a, &b.p, sizeof(T) * (count > 0 ? count : 1));
     if (e == cudaErrorMemoryAllocation) {
@@ -547,9 +537,9 @@ sls_status build_tile_halo(sls_mesh *M, cudaStream_t s)
 {
     if (!M->opt.skip_unchanged) return SLS_OK;
     const int64_t nt = (M->n + 31) / 32;
-    GB_TRY(cudaMalloc(&M->halo, sizeof(uint2) * (size_t)kHaloEntries * (size_t)nt), "tile halo");
-    for (int k = 0; k < 2; ++k) GB_TRY(cudaMalloc(&M->chg[k], sizeof(uint32_t) * (size_t)nt), "tile masks");
-    GB_TRY(cudaMalloc(&M->accm, sizeof(uint32_t) * (size_t)nt), "tile masks");
+    GB_TRY(pool_alloc((void **)&M->halo, sizeof(uint2) * (size_t)kHaloEntries * (size_t)nt, s), "tile halo");
+    for (int k = 0; k < 2; ++k) GB_TRY(pool_alloc((void **)&M->chg[k], sizeof(uint32_t) * (size_t)nt, s), "tile masks");
+    GB_TRY(pool_alloc((void **)&M->accm, sizeof(uint32_t) * (size_t)nt, s), "tile masks");
     for (int k = 0; k < 2; ++k) GB_TRY(cudaMemsetAsync(M->chg[k], 0xff, sizeof(uint32_t) * (size_t)nt, s), "tile masks");
     GB_TRY(cudaMemsetAsync(M->accm, 0, sizeof(uint32_t) * (size_t)nt, s), "tile masks");
     tile_halo_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(M->node_off, M->adj, M->n, nt, M->halo);
@@ -571,8 +561,8 @@ sls_status order_segment(sls_mesh *M, const int32_t *colour, int32_t c, uint32_t
     unsigned *cnt = nullptr;
     uint32_t *off = nullptr;
     sls_status st;
-    if ((st = dalloc(b_cnt, (size_t)tiles, &cnt, "order counts")) != SLS_OK) return st;
-    if ((st = dalloc(b_off, (size_t)tiles + 1, &off, "order offsets")) != SLS_OK) return st;
+    if ((st = dalloc(b_cnt, (size_t)tiles, &cnt, "order counts", Alloc{false, s})) != SLS_OK) return st;
+    if ((st = dalloc(b_off, (size_t)tiles + 1, &off, "order offsets", Alloc{false, s})) != SLS_OK) return st;
     order_count_kernel<<<(unsigned)tiles, kOrderTile, 0, s>>>(M->node_off, M->adj, n, colour, c, cnt);
     GB_TRY(cudaGetLastError(), "order count");
     unsigned long long total = 0ull;
@@ -724,20 +714,20 @@ static sls_status apply_renumbering(sls_mesh *M, cudaStream_t s)
 {
     const int64_t n = M->n;
     const int grid = device_sm_count() * 8, block = 256;
-    GB_TRY(cudaMalloc(&M->inv, sizeof(uint32_t) * (size_t)n), "renumbering");
+    GB_TRY(pool_alloc((void **)&M->inv, sizeof(uint32_t) * (size_t)n, s), "renumbering");
     DevBuf b_len, b_off, b_adj;
     unsigned *len = nullptr;
     uint32_t *off_new = nullptr, *adj_new = nullptr;
     sls_status st;
-    if ((st = dalloc(b_len, (size_t)n + 1, &len, "renumbering")) != SLS_OK) return st;
+    if ((st = dalloc(b_len, (size_t)n + 1, &len, "renumbering", Alloc{false, s})) != SLS_OK) return st;
     inverse_kernel<<<grid, block, 0, s>>>(M->perm, n, M->inv);
     record_len_kernel<<<grid, block, 0, s>>>(M->node_off, M->perm, n, len);
     GB_TRY(cudaGetLastError(), "renumbering");
-    if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering")) != SLS_OK) return st;
+    if ((st = dalloc(b_off, (size_t)n + 1, &off_new, "renumbering", Alloc{false, s})) != SLS_OK) return st;
     unsigned long long words = 0ull;
     if ((st = scan_u32(len, n, off_new, &words, s)) != SLS_OK) return st;
     if (words != M->adj_words) return fail(SLS_ERR_INVALID, "adjacency size mismatch in the renumbering");
-    if ((st = dalloc(b_adj, (size_t)words, &adj_new, "renumbering")) != SLS_OK) return st;
+    if ((st = dalloc(b_adj, (size_t)words, &adj_new, "renumbering", Alloc{false, s})) != SLS_OK) return st;
     remap_adj_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, M->perm, M->inv, off_new, n, adj_new);
     remap_ids_kernel<<<grid, block, 0, s>>>(M->tri, 3 * M->m, M->inv);
     GB_TRY(cudaGetLastError(), "renumbering");
@@ -745,8 +735,8 @@ static sls_status apply_renumbering(sls_mesh *M, cudaStream_t s)
     GB_TRY(cudaMemcpyAsync(M->xy[0], M->xy[1], (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)n,
                            cudaMemcpyDeviceToDevice, s), "renumbering");
     GB_TRY(cudaStreamSynchronize(s), "renumbering");
-    cudaFree(M->node_off);
-    cudaFree(M->adj);
+    pool_free(M->node_off, s);
+    pool_free(M->adj, s);
     M->node_off = off_new;
     M->adj = adj_new;
     b_off.p = nullptr;  // now the mesh's
@@ -784,12 +774,8 @@ sls_status group_adjacency(int64_t n, uint32_t **node_off, uint32_t *adj, bool a
                                                                                     inv, off_new);
     remap_in_place_kernel<<<grid, block, 0, s>>>(*node_off, adj, n, inv);
     GB_TRY(cudaGetLastError(), "renumbering");
-    if (async) {
-        GB_TRY(cudaFreeAsync(*node_off, s), "renumbering");
-    } else {
-        GB_TRY(cudaStreamSynchronize(s), "renumbering");
-        cudaFree(*node_off);
-    }
+    pool_free(*node_off, s);
+    if (!async) GB_TRY(cudaStreamSynchronize(s), "renumbering");
     *node_off = off_new;
     b_off.p = nullptr;
     *perm_out = perm;
@@ -830,7 +816,7 @@ sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
 {
     const int64_t n = M->n;
     const int grid = device_sm_count() * 8, block = 256;
-    GB_TRY(cudaMalloc(&M->perm, sizeof(uint32_t) * (size_t)n), "renumbering");
+    GB_TRY(pool_alloc((void **)&M->perm, sizeof(uint32_t) * (size_t)n, s), "renumbering");
     // the free nodes by class: the processing order already lists them so
     if (M->n_free > 0)
         GB_TRY(cudaMemcpyAsync(M->perm, M->node_order, sizeof(uint32_t) * (size_t)M->n_free,
@@ -839,8 +825,8 @@ sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
     unsigned *flag = nullptr;
     uint32_t *scan = nullptr;
     sls_status st;
-    if ((st = dalloc(b_flag, (size_t)n + 1, &flag, "renumbering")) != SLS_OK) return st;
-    if ((st = dalloc(b_scan, (size_t)n + 1, &scan, "renumbering")) != SLS_OK) return st;
+    if ((st = dalloc(b_flag, (size_t)n + 1, &flag, "renumbering", Alloc{false, s})) != SLS_OK) return st;
+    if ((st = dalloc(b_scan, (size_t)n + 1, &scan, "renumbering", Alloc{false, s})) != SLS_OK) return st;
     fixed_flag_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, n, flag);
     GB_TRY(cudaGetLastError(), "renumbering");
     unsigned long long nfixed = 0ull;
@@ -849,7 +835,7 @@ sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
     compact_kernel<<<grid, block, 0, s>>>(flag, scan, n, M->n_free, M->perm);
     GB_TRY(cudaGetLastError(), "renumbering");
     if ((st = apply_renumbering(M, s)) != SLS_OK) return st;
-    cudaFree(M->node_order);
+    pool_free(M->node_order, s);
     M->node_order = nullptr;
     return SLS_OK;
 }
@@ -860,7 +846,7 @@ sls_status build_node_order(sls_mesh *M, cudaStream_t s)
     if (M->opt.form != 1) {
         return groups_nodes(M->opt, M->n) ? group_by_degree(M, s) : SLS_OK;
     }
-    GB_TRY(cudaMalloc(&M->node_order, sizeof(uint32_t) * (size_t)(M->n_free > 0 ? M->n_free : 1)),
+    GB_TRY(pool_alloc((void **)&M->node_order, sizeof(uint32_t) * (size_t)(M->n_free > 0 ? M->n_free : 1), s),
            "processing order");
     // Form B: Jones-Plassmann colouring, then one order segment per colour
     const int64_t n = M->n;
@@ -869,8 +855,8 @@ sls_status build_node_order(sls_mesh *M, cudaStream_t s)
     unsigned long long *cnt = nullptr;
     sls_status st;
     for (int k = 0; k < 2; ++k)
-        if ((st = dalloc(b_col[k], (size_t)n, &col[k], "colours")) != SLS_OK) return st;
-    if ((st = dalloc(b_cnt, 2, &cnt, "colouring counters")) != SLS_OK) return st;
+        if ((st = dalloc(b_col[k], (size_t)n, &col[k], "colours", Alloc{false, s})) != SLS_OK) return st;
+    if ((st = dalloc(b_cnt, 2, &cnt, "colouring counters", Alloc{false, s})) != SLS_OK) return st;
     const int grid = device_sm_count() * 8, block = 256;
     colour_init_kernel<<<grid, block, 0, s>>>(M->node_off, M->adj, n, col[0]);
     GB_TRY(cudaGetLastError(), "colouring");

@@ -14,9 +14,10 @@ namespace sls {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-static sls_status dev_alloc(void **p, size_t bytes, const char *what)
+// A buffer of mesh M from the library's pool, on the mesh's stream.
+static sls_status dev_alloc(const sls_mesh *M, void **p, size_t bytes, const char *what)
 {
-    cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 1);
+    cudaError_t e = pool_alloc(p, bytes, M->stream);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return fail(SLS_ERR_OOM, std::string("device allocation failed: ") + what);
@@ -48,10 +49,10 @@ static sls_status mesh_setup(sls_mesh *M, const sls_options &o)
     }
     sls_status st;
     M->stats_cap = 256;
-    if ((st = dev_alloc((void **)&M->stats, sizeof(PassStats) * M->stats_cap, "pass statistics")) != SLS_OK) return st;
+    if ((st = dev_alloc(M, (void **)&M->stats, sizeof(PassStats) * M->stats_cap, "pass statistics")) != SLS_OK) return st;
     SLS_CUDA_TRY(cudaMallocHost((void **)&M->h_stats, sizeof(PassStats)), "cudaMallocHost");
     if (o.record_accept) {
-        if ((st = dev_alloc((void **)&M->accept, (size_t)M->n, "accept mask")) != SLS_OK) return st;
+        if ((st = dev_alloc(M, (void **)&M->accept, (size_t)M->n, "accept mask")) != SLS_OK) return st;
         SLS_CUDA_TRY(cudaMemsetAsync(M->accept, 0, (size_t)M->n, M->stream), "cudaMemset");
     }
     M->cur = 0;
@@ -91,8 +92,8 @@ static sls_status narrow_coordinates(sls_mesh *M)
     float *f[2] = {nullptr, nullptr};
     sls_status st;
     for (int b = 0; b < 2; ++b)
-        if ((st = dev_alloc((void **)&f[b], fbytes, "coordinates")) != SLS_OK) {
-            cudaFree(f[0]);
+        if ((st = dev_alloc(M, (void **)&f[b], fbytes, "coordinates")) != SLS_OK) {
+            pool_free(f[0], M->stream);
             return st;
         }
     const int grid = device_sm_count() * 4;
@@ -105,7 +106,7 @@ static sls_status narrow_coordinates(sls_mesh *M)
     SLS_CUDA_TRY(cudaMemcpyAsync(f[1], f[0], fbytes, cudaMemcpyDeviceToDevice, M->stream), "copy coordinates");
     SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "narrow");
     for (int b = 0; b < 2; ++b) {
-        cudaFree(M->xy[b]);
+        pool_free(M->xy[b], M->stream);
         M->xy[b] = reinterpret_cast<double *>(f[b]);
     }
     return SLS_OK;
@@ -123,10 +124,10 @@ sls_status mesh_upload(sls_mesh *M, const HostMesh &hm, const double *xy, const 
     if (st != SLS_OK) return st;
     const size_t cbytes = sizeof(double) * 2 * (size_t)M->n;
     for (int b = 0; b < 2; ++b)
-        if ((st = dev_alloc((void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
-    if ((st = dev_alloc((void **)&M->node_off, sizeof(uint32_t) * (M->n + 1), "node offsets")) != SLS_OK) return st;
-    if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
-    if ((st = dev_alloc((void **)&M->tri, sizeof(int32_t) * 3 * (size_t)M->m, "triangles")) != SLS_OK) return st;
+        if ((st = dev_alloc(M, (void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
+    if ((st = dev_alloc(M, (void **)&M->node_off, sizeof(uint32_t) * (M->n + 1), "node offsets")) != SLS_OK) return st;
+    if ((st = dev_alloc(M, (void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
+    if ((st = dev_alloc(M, (void **)&M->tri, sizeof(int32_t) * 3 * (size_t)M->m, "triangles")) != SLS_OK) return st;
     if (o.layout == 0) {
         SLS_CUDA_TRY(cudaMemcpyAsync(M->xy[0], xy, cbytes, cudaMemcpyHostToDevice, M->stream), "upload coordinates");
         SLS_CUDA_TRY(cudaStreamSynchronize(M->stream), "upload coordinates");
@@ -158,8 +159,8 @@ sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const
     if (st != SLS_OK) return st;
     const size_t cbytes = sizeof(double) * 2 * (size_t)n;
     for (int b = 0; b < 2; ++b)
-        if ((st = dev_alloc((void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
-    if ((st = dev_alloc((void **)&M->tri, sizeof(int32_t) * 3 * (size_t)m, "triangles")) != SLS_OK) return st;
+        if ((st = dev_alloc(M, (void **)&M->xy[b], cbytes, "coordinates")) != SLS_OK) return st;
+    if ((st = dev_alloc(M, (void **)&M->tri, sizeof(int32_t) * 3 * (size_t)m, "triangles")) != SLS_OK) return st;
     // interleaved coordinates go to xy[0] (AoS) or xy[1] (staging for SoA)
     double *aos = o.layout == 0 ? M->xy[0] : M->xy[1];
     SLS_CUDA_TRY(cudaMemcpyAsync(aos, xy, cbytes, cudaMemcpyHostToDevice, M->stream), "upload coordinates");
@@ -171,15 +172,15 @@ sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const
         HostMesh hm;
         st = build_host_mesh(xy, n, tri, m, boundary, hm);
         if (st != SLS_OK) return st;
-        cudaFree(M->node_off);
-        cudaFree(M->adj);
+        pool_free(M->node_off, M->stream);
+        pool_free(M->adj, M->stream);
         M->node_off = nullptr;
         M->adj = nullptr;
         M->n_free = hm.n_free;
         M->diag = hm.diag;
         M->adj_words = hm.node_off[hm.n];
-        if ((st = dev_alloc((void **)&M->node_off, sizeof(uint32_t) * (n + 1), "node offsets")) != SLS_OK) return st;
-        if ((st = dev_alloc((void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
+        if ((st = dev_alloc(M, (void **)&M->node_off, sizeof(uint32_t) * (n + 1), "node offsets")) != SLS_OK) return st;
+        if ((st = dev_alloc(M, (void **)&M->adj, sizeof(uint32_t) * M->adj_words, "adjacency")) != SLS_OK) return st;
         SLS_CUDA_TRY(cudaMemcpyAsync(M->node_off, hm.node_off.data(), sizeof(uint32_t) * (n + 1),
                                      cudaMemcpyHostToDevice, M->stream), "upload offsets");
         SLS_CUDA_TRY(cudaMemcpyAsync(M->adj, hm.adj.data(), sizeof(uint32_t) * M->adj_words,
@@ -199,21 +200,21 @@ sls_status mesh_create_on_device(sls_mesh *M, const double *xy, int64_t n, const
 void mesh_release(sls_mesh *M)
 {
     if (M->stream) cudaStreamSynchronize(M->stream);
-    cudaFree(M->xy[0]);
-    cudaFree(M->xy[1]);
-    cudaFree(M->node_off);
-    cudaFree(M->adj);
-    cudaFree(M->node_order);
-    cudaFree(M->perm);
-    cudaFree(M->inv);
-    cudaFree(M->tri);
-    cudaFree(M->stats);
-    cudaFree(M->accept);
-    cudaFree(M->halo);
-    cudaFree(M->chg[0]);
-    cudaFree(M->chg[1]);
-    cudaFree(M->accm);
-    cudaFree(M->xfer_bad);
+    pool_free(M->xy[0], M->stream);
+    pool_free(M->xy[1], M->stream);
+    pool_free(M->node_off, M->stream);
+    pool_free(M->adj, M->stream);
+    pool_free(M->node_order, M->stream);
+    pool_free(M->perm, M->stream);
+    pool_free(M->inv, M->stream);
+    pool_free(M->tri, M->stream);
+    pool_free(M->stats, M->stream);
+    pool_free(M->accept, M->stream);
+    pool_free(M->halo, M->stream);
+    pool_free(M->chg[0], M->stream);
+    pool_free(M->chg[1], M->stream);
+    pool_free(M->accm, M->stream);
+    pool_free(M->xfer_bad, M->stream);
     if (M->h_stats) cudaFreeHost(M->h_stats);
     if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
     M->stream = nullptr;
@@ -249,10 +250,10 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
     if (max_iter == 0) return SLS_OK;
     if (M->stats_cap < max_iter) {
         cudaStreamSynchronize(M->stream);
-        cudaFree(M->stats);
+        pool_free(M->stats, M->stream);
         M->stats = nullptr;
         int cap = std::max(max_iter, 2 * M->stats_cap);
-        sls_status st = dev_alloc((void **)&M->stats, sizeof(PassStats) * cap, "pass statistics");
+        sls_status st = dev_alloc(M, (void **)&M->stats, sizeof(PassStats) * cap, "pass statistics");
         if (st != SLS_OK) {
             M->stats_cap = 0;
             return st;
@@ -376,14 +377,14 @@ sls_status mesh_download(const sls_mesh *M, double *xy_out, bool dst_is_device)
         const bool stage = !dst_is_device && !M->f32;
         double *d = dst_is_device ? xy_out : (stage ? M->xy[M->cur ^ 1] : nullptr);
         sls_status st;
-        if (!d && (st = dev_alloc((void **)&d, cbytes, "download")) != SLS_OK) return st;
+        if (!d && (st = dev_alloc(M, (void **)&d, cbytes, "download")) != SLS_OK) return st;
         cudaError_t e = launch_unpermute_to_aos(src, M->opt.layout, M->f32, M->n, M->perm, d,
                                                 device_sm_count() * 4, M->stream);
         if (e == cudaSuccess && !dst_is_device)
             e = cudaMemcpyAsync(xy_out, d, cbytes, cudaMemcpyDeviceToHost, M->stream);
         if (e == cudaSuccess && stage) e = cudaMemcpyAsync(d, src, cbytes, cudaMemcpyDeviceToDevice, M->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
-        if (!dst_is_device && !stage) cudaFree(d);
+        if (!dst_is_device && !stage) pool_free(d, M->stream);
         if (e != cudaSuccess) return cuda_fail(e, "download coordinates");
         return SLS_OK;
     }
@@ -429,7 +430,7 @@ sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
         const size_t ebytes = (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)M->n;
         double *d = const_cast<double *>(xy);
         sls_status st;
-        if (!src_is_device && (st = dev_alloc((void **)&d, cbytes, "upload")) != SLS_OK) return st;
+        if (!src_is_device && (st = dev_alloc(M, (void **)&d, cbytes, "upload")) != SLS_OK) return st;
         cudaError_t e = cudaSuccess;
         if (!src_is_device) e = cudaMemcpyAsync(d, xy, cbytes, cudaMemcpyHostToDevice, M->stream);
         if (e == cudaSuccess)
@@ -438,7 +439,7 @@ sls_status mesh_set_coords(sls_mesh *M, const double *xy, bool src_is_device)
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(M->xy[M->cur ^ 1], M->xy[M->cur], ebytes, cudaMemcpyDeviceToDevice, M->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
-        if (!src_is_device) cudaFree(d);
+        if (!src_is_device) pool_free(d, M->stream);
         if (e != cudaSuccess) return cuda_fail(e, "set coordinates");
         return SLS_OK;
     }
@@ -489,7 +490,7 @@ sls_status mesh_transfer_nodes(sls_mesh *M, const int32_t *idx, int64_t k, doubl
     if (M->opt.form != 0) return fail(SLS_ERR_INVALID, "node gather/scatter needs a Form-A mesh");
     if (k == 0) return SLS_OK;
     if (!M->xfer_bad) {
-        sls_status st = dev_alloc((void **)&M->xfer_bad, sizeof(unsigned), "transfer flag");
+        sls_status st = dev_alloc(M, (void **)&M->xfer_bad, sizeof(unsigned), "transfer flag");
         if (st != SLS_OK) return st;
     }
     const int grid = device_sm_count() * 4;
@@ -520,18 +521,18 @@ sls_status mesh_histogram(const sls_mesh *M, int nbins, double lo, double hi, in
     const double *hx = M->xy[M->cur];
     int hlayout = M->opt.layout;
     if (M->f32) {
-        if ((st = dev_alloc((void **)&wide, sizeof(double) * 2 * (size_t)M->n, "histogram")) != SLS_OK) return st;
+        if ((st = dev_alloc(M, (void **)&wide, sizeof(double) * 2 * (size_t)M->n, "histogram")) != SLS_OK) return st;
         cudaError_t e0 = launch_widen(reinterpret_cast<const float *>(M->xy[M->cur]), wide, M->n, M->opt.layout,
                                       device_sm_count() * 4, M->stream);
         if (e0 != cudaSuccess) {
-            cudaFree(wide);
+            pool_free(wide, M->stream);
             return cuda_fail(e0, "widen");
         }
         hx = wide;
         hlayout = 0;
     }
-    if ((st = dev_alloc((void **)&d_counts, sizeof(unsigned long long) * (nbins + 2), "histogram")) != SLS_OK) {
-        cudaFree(wide);
+    if ((st = dev_alloc(M, (void **)&d_counts, sizeof(unsigned long long) * (nbins + 2), "histogram")) != SLS_OK) {
+        pool_free(wide, M->stream);
         return st;
     }
     d_key = d_counts + nbins;
@@ -546,8 +547,8 @@ sls_status mesh_histogram(const sls_mesh *M, int nbins, double lo, double hi, in
         e = cudaMemcpyAsync(h.data(), d_counts, sizeof(unsigned long long) * (nbins + 2),
                             cudaMemcpyDeviceToHost, M->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
-    cudaFree(d_counts);
-    cudaFree(wide);
+    pool_free(d_counts, M->stream);
+    pool_free(wide, M->stream);
     if (e != cudaSuccess) return cuda_fail(e, "histogram");
     for (int b = 0; b < nbins; ++b) counts[b] = (int64_t)h[b];
     unsigned long long key = h[nbins];

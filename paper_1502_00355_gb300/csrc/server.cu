@@ -88,7 +88,6 @@ struct sls_server {
     int device = 0;
     cudaStream_t stream = nullptr, retire_stream = nullptr;
     std::vector<cudaStream_t> build_streams;
-    cudaMemPool_t pool = nullptr;
 
     std::mutex mu;
     std::condition_variable cv_build, cv_sched, cv_done, cv_retire;
@@ -182,9 +181,9 @@ sls_status build_job(ServerJob &J, bool group, cudaStream_t s, size_t *footprint
     auto cuda_err = [&](cudaError_t e, const char *what) { return cleanup(cuda_fail(e, what)); };
     cudaError_t e = cudaSuccess;
     for (void **p : {(void **)&J.d_xy[0], (void **)&J.d_xy[1]})
-        if (e == cudaSuccess) e = cudaMallocAsync(p, cbytes, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_tri, sizeof(int32_t) * 3 * (size_t)m, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&J.d_stats, sizeof(PassStats) * (size_t)std::max(1, J.max_iter), s);
+        if (e == cudaSuccess) e = pool_alloc(p, cbytes, s);
+    if (e == cudaSuccess) e = pool_alloc((void **)&d_tri, sizeof(int32_t) * 3 * (size_t)m, s);
+    if (e == cudaSuccess) e = pool_alloc((void **)&J.d_stats, sizeof(PassStats) * (size_t)std::max(1, J.max_iter), s);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return cleanup(fail(SLS_ERR_OOM, "device allocation failed"));
@@ -205,8 +204,8 @@ sls_status build_job(ServerJob &J, bool group, cudaStream_t s, size_t *footprint
         da.adj_words = hm.node_off[n];
         da.n_free = hm.n_free;
         da.diag = hm.diag;
-        e = cudaMallocAsync((void **)&da.node_off, sizeof(uint32_t) * (size_t)(n + 1), s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&da.adj, sizeof(uint32_t) * std::max<uint64_t>(1, da.adj_words), s);
+        e = pool_alloc((void **)&da.node_off, sizeof(uint32_t) * (size_t)(n + 1), s);
+        if (e == cudaSuccess) e = pool_alloc((void **)&da.adj, sizeof(uint32_t) * std::max<uint64_t>(1, da.adj_words), s);
         J.d_off = da.node_off;  // freed with the job on any failure below
         J.d_adj = da.adj;
         if (e == cudaSuccess)
@@ -685,10 +684,6 @@ sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_opt
         if (S->stream) cudaStreamDestroy(S->stream);
         if (S->retire_stream) cudaStreamDestroy(S->retire_stream);
         return fail(SLS_ERR_CUDA, "stream or event creation failed");
-    }
-    if (cudaDeviceGetDefaultMemPool(&S->pool, S->device) == cudaSuccess) {
-        uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
-        cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     S->block = (opt != nullptr && opt->block_size >= 32 && opt->block_size <= 128) ? opt->block_size : 128;
     S->grid = device_sm_count() * batch_pass_occupancy(o.layout, S->block);
