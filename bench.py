@@ -43,16 +43,16 @@ CSRC = os.path.join(ROOT, "paper_1502_00355_gb300", "csrc")
 PROFILE_FIGURES = {
     "pass_screened": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh",
-                  "mesh_build_gpu.cu"],
-        "sha256": "f76ef0d18df380e9bf954a7820437e56e57ab0fec84c1cced71b4fe23c0a6a0f",
+                  "numbering.cu"],
+        "sha256": "497b818d69c0a2357c211928368e5f3135c8f7e8884067d5b3a7eb2d031cce46",
         "dram_bytes_per_node": (309189376 + 54080512) / (2048 * 2048),
         "fp64_warp_inst_per_32_nodes": (2132648 + 795086 + 157073) / (2048 * 2048 / 32),
         "source": "profiles/pass_screened_grid2048.md (2048x2048 capture, per node)",
     },
     "batch_pass": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu",
-                  "mesh_build_gpu.cu"],
-        "sha256": "c1e451ee9557dc81957df52d4afab0759f314275d9106164982c60a77744858a",
+                  "numbering.cu"],
+        "sha256": "22c8dc49084b29f110cba8b7090033e98e5e46231ec496f1a5bc3f129267452c",
         "dram_per_alg_byte": (1007816192 + 171327488) / 994046024,
         "source": "profiles/batch_pass_batch256.md (round 0 of a 256-mesh batch, scaled by algorithmic bytes)",
     },
@@ -858,7 +858,7 @@ def run_single(args):
            "bytes_per_pass": bytes_pass, "bytes_source": "16n + 16n_free + 8(n+1) + 4nnz + 12m + 12m + n",
            "bytes_per_pass_library_encoding": bytes_ours}
     roofline = {"bound": "hbm", **hbm, "pass_ms": pass_ms}
-    if fig:
+    if args.precision == 64 and args.form == "A":
         # The FP64 pipe: every FP64 warp instruction occupies it for all 32
         # lanes.  Peak from the unit count and clock: 2 FP64 lane operations
         # per clock per SM (the FMA pipe's sustained peak) x SMs x max SM clock.
@@ -873,15 +873,17 @@ def run_single(args):
         # meshes: words = n + sum over free nodes of (deg + ntri))
         sum_deg_free = (adjacency_words(mesh) - mesh.n) // 2
         fp64_alg = 2 * sum_deg_free + 5 * g.n_free
-        fp64_issued = fig["fp64_warp_inst_per_32_nodes"] * mesh.n  # warp instructions x 32 lanes / 32 nodes
         t = pass_ms * 1e-3
         fp64 = {"achieved": fp64_alg / t / 1e12, "peak": fp64_peak / 1e12, "unit": "T FP64 op/s",
                 "frac": fp64_alg / t / fp64_peak, "ops_per_pass": fp64_alg,
                 "ops_source": "per free node 2(deg-1) + 2 + 2 + 3",
                 "peak_source": f"2 FP64 lane operations per clock per SM x {sms} SMs x {clk_max:.0f} MHz",
-                "pipe_occupancy": fp64_issued / t / fp64_peak,
-                "issued_lane_slots_per_pass": fp64_issued, "issued_source": fig["source"],
                 "measured_dgemm": fp64_dgemm / 1e12}
+        if fig:
+            # issued FP64 lane slots from the capture: warp instructions x 32 lanes / 32 nodes
+            fp64_issued = fig["fp64_warp_inst_per_32_nodes"] * mesh.n
+            fp64.update({"pipe_occupancy": fp64_issued / t / fp64_peak,
+                         "issued_lane_slots_per_pass": fp64_issued, "issued_source": fig["source"]})
         roofline["hbm"] = dict(hbm)
         roofline["fp64"] = fp64
         if fp64["frac"] > hbm["frac"]:
