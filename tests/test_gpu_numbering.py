@@ -42,7 +42,8 @@ def _run(sls, mesh, iters, tol, **opts):
 
 @pytest.mark.parametrize("name", sorted(MESHES))
 @pytest.mark.parametrize("opts", [dict(), dict(layout="soa"), dict(copy_back=True), dict(kernel="fp64"),
-                                  dict(strict=True)], ids=["aos", "soa", "copy_back", "fp64", "strict"])
+                                  dict(strict=True), dict(host_build=True)],
+                         ids=["aos", "soa", "copy_back", "fp64", "strict", "host_build"])
 def test_grouped_equals_given_and_oracle(sls, name, opts):
     mesh = MESHES[name]()
     xy, info, acc, hist = _run(sls, mesh, 40, 1e-9, numbering="grouped", **opts)
