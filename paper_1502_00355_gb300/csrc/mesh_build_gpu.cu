@@ -644,6 +644,47 @@ __global__ void remap_ids_kernel(int32_t *ids, int64_t count, const uint32_t *__
         ids[t] = (int32_t)inv[ids[t]];
 }
 
+// Form B: inside every window of 128 positions of a colour class's id range
+// (aligned to the class's start, as its ranged launches step through it) the
+// class's nodes by (incident triangles, degree), ties by position: the same
+// evening of a warp's loop lengths as Form A's grouped numbering, without
+// mixing classes.  perm_in / perm_out: new position -> caller's id.
+__global__ void __launch_bounds__(128) class_window_kernel(const uint32_t *__restrict__ perm_in,
+                                                           const uint32_t *__restrict__ node_off,
+                                                           const uint32_t *__restrict__ adj,
+                                                           const int64_t *__restrict__ class_off,
+                                                           const int64_t *__restrict__ win_off, int nclass,
+                                                           uint32_t *__restrict__ perm_out)
+{
+    __shared__ uint32_t key[128];
+    const int t = threadIdx.x;
+    const int64_t nwin = win_off[nclass];
+    for (int64_t w = blockIdx.x; w < nwin; w += gridDim.x) {
+        int c = 0;
+        while (c + 1 < nclass && win_off[c + 1] <= w) ++c;
+        const int64_t base = class_off[c] + 128 * (w - win_off[c]);
+        const int64_t end = class_off[c + 1];
+        const int len = end - base < 128 ? (int)(end - base) : 128;
+        uint32_t k = 0xffffffffu, id = 0u;
+        if (t < len) {
+            id = perm_in[base + t];
+            const uint32_t meta = __ldg(adj + __ldg(node_off + id));
+            k = (meta_ntri(meta) << 16) | meta_degree(meta);
+        }
+        key[t] = k;
+        __syncthreads();
+        if (t < len) {
+            int r = 0;
+            for (int u = 0; u < len; ++u) {
+                const uint32_t ku = key[u];
+                r += (ku < k || (ku == k && u < t)) ? 1 : 0;
+            }
+            perm_out[base + r] = id;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 // Renumbers the mesh by M->perm (new id -> caller's id, a permutation of
@@ -732,6 +773,32 @@ sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
     if ((int64_t)nfixed + M->n_free != n) return fail(SLS_ERR_INVALID, "node count mismatch in the renumbering");
     compact_kernel<<<grid, block, 0, s>>>(flag, scan, n, M->n_free, M->perm);
     GB_TRY(cudaGetLastError(), "renumbering");
+    const int nc = (int)M->colour_off.size() - 1;
+    if (nc > 0 && M->n_free > 0 && (M->opt.numbering == 2 || (M->opt.numbering == 0 && n >= (int64_t(1) << 20)))) {
+        // each class's windows grouped by loop length (see class_window_kernel)
+        std::vector<int64_t> offs(2 * ((size_t)nc + 1));
+        for (int c = 0; c <= nc; ++c) {
+            offs[c] = M->colour_off[(size_t)c];
+            offs[(size_t)nc + 1 + c] = c == 0 ? 0 : offs[(size_t)nc + c] + (offs[c] - offs[c - 1] + 127) / 128;
+        }
+        DevBuf b_perm2, b_offs;
+        uint32_t *perm2 = nullptr;
+        int64_t *d_offs = nullptr;
+        if ((st = dalloc(b_perm2, (size_t)n, &perm2, "renumbering", Alloc{false, s})) != SLS_OK) return st;
+        if ((st = dalloc(b_offs, offs.size(), &d_offs, "renumbering", Alloc{false, s})) != SLS_OK) return st;
+        GB_TRY(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice, s),
+               "renumbering");
+        GB_TRY(cudaMemcpyAsync(perm2, M->perm, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s),
+               "renumbering");
+        const int64_t nwin = offs[2 * (size_t)nc + 1];
+        const int64_t cap = (int64_t)device_sm_count() * 16;
+        class_window_kernel<<<(unsigned)(nwin < cap ? nwin : cap), 128, 0, s>>>(M->perm, M->node_off, M->adj, d_offs,
+                                                                               d_offs + nc + 1, nc, perm2);
+        GB_TRY(cudaGetLastError(), "renumbering");
+        GB_TRY(cudaStreamSynchronize(s), "renumbering");  // offs is read from host memory
+        b_perm2.p = M->perm;  // the plain class order goes back to the pool
+        M->perm = perm2;
+    }
     if ((st = apply_renumbering(M, s)) != SLS_OK) return st;
     pool_free(M->node_order, s);
     M->node_order = nullptr;

@@ -61,6 +61,18 @@ def test_form_b_strict_derived_boundary_and_tolerance(sls, kernel):
     assert got[1]["converged"] == 1
 
 
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+def test_form_b_class_windows_grouped(sls, layout):
+    # numbering = 2: each colour class's windows of 128 ids listed by loop
+    # length inside the library (a Delaunay mesh of degrees 3 to about 12)
+    mesh = meshgen.delaunay_random(6000, 11, numbering="random")
+    got, ref = _run_both(sls, mesh, 30, tol=1e-9, numbering="grouped", layout=layout)
+    _check(got, ref, f"grouped classes {layout}")
+    got, ref = _run_both(sls, meshgen.jittered_grid(70, 45, 0.35, 12, numbering="random"), 8, strict=True,
+                         boundary="derived", numbering="grouped")
+    _check(got, ref, "grouped classes strict derived")
+
+
 @pytest.mark.parametrize("numbering", ["morton", "random"])
 def test_medium_grid_form_b(sls, numbering):
     mesh = meshgen.medium_grid(numbering)
