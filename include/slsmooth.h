@@ -115,12 +115,14 @@ typedef struct sls_options {
                               and the screened kernel (SLS_KERNEL_AUTO or _FILTERED); costs
                               140 bytes of device memory per 32 nodes.  The batched and
                               allocation-free forms compute every tile; the server rejects it. */
-    int32_t numbering;     /* Form A: 0 (default) lets the library renumber a mesh of at least
+    int32_t numbering;     /* FP64: 0 (default) lets the library renumber a mesh of at least
                               2^20 nodes, 1 keeps the caller's numbering, 2 renumbers at any
-                              size.  Renumbered, every window of 128 consecutive ids lists its
-                              nodes by incident-triangle count, then degree (fixed nodes last,
-                              ties by id), so that the 32 lanes of a warp run loops of similar
-                              length (the pass's loops run to the warp's longest).  The windows
+                              size (binary32 meshes keep it: their pass gains nothing).
+                              Form A: every window of 128 consecutive ids lists its nodes by
+                              incident-triangle count, then degree (fixed nodes last, ties by
+                              id); Form B: the same inside each colour class's range.  The 32
+                              lanes of a warp then run loops of similar length (the pass's
+                              loops run to the warp's longest).  The windows
                               stay where they are, so the gathers keep their locality.  Costs
                               two kernels and 8 bytes per node at creation, which only larger
                               meshes repay.  Not done with skip_unchanged (its 32-node tiles

@@ -92,11 +92,15 @@ void pool_free(void *p, cudaStream_t s);
 // (old -> new) allocated as `async` says, the caller's to free.
 sls_status group_adjacency(int64_t n, uint32_t **node_off, uint32_t *adj, bool async, cudaStream_t s,
                            uint32_t **perm_out, uint32_t **inv_out);
-// Whether options o renumber a Form-A mesh of n nodes (grouped numbering).
-inline bool groups_nodes(const sls_options &o, int64_t n)
+// Whether options o group the nodes of a mesh of n nodes by loop length
+// (FP64 only: the binary32 pass's loops are per lane, and there the grouping
+// only costs locality).
+inline bool groups_by_length(const sls_options &o, int64_t n)
 {
-    return o.form == 0 && !o.skip_unchanged && (o.numbering == 2 || (o.numbering == 0 && n >= (int64_t(1) << 20)));
+    return o.precision != 32 && !o.skip_unchanged && (o.numbering == 2 || (o.numbering == 0 && n >= (int64_t(1) << 20)));
 }
+// Whether options o renumber a Form-A mesh of n nodes (grouped numbering).
+inline bool groups_nodes(const sls_options &o, int64_t n) { return o.form == 0 && groups_by_length(o, n); }
 // Device adjacency build of a mesh handle; SLS_ERR_NOT_FOUND = use the host build.
 sls_status build_device_mesh(sls_mesh *M, const double *d_xy, const int32_t *d_tri, const uint8_t *h_boundary,
                              cudaStream_t s);

@@ -774,7 +774,7 @@ sls_status renumber_classes(sls_mesh *M, cudaStream_t s)
     compact_kernel<<<grid, block, 0, s>>>(flag, scan, n, M->n_free, M->perm);
     GB_TRY(cudaGetLastError(), "renumbering");
     const int nc = (int)M->colour_off.size() - 1;
-    if (nc > 0 && M->n_free > 0 && (M->opt.numbering == 2 || (M->opt.numbering == 0 && n >= (int64_t(1) << 20)))) {
+    if (nc > 0 && M->n_free > 0 && groups_by_length(M->opt, n)) {
         // each class's windows grouped by loop length (see class_window_kernel)
         std::vector<int64_t> offs(2 * ((size_t)nc + 1));
         for (int c = 0; c <= nc; ++c) {

@@ -64,6 +64,7 @@ def test_grouped_equals_given_and_oracle(sls, name, opts):
 
 
 def test_binary32_grouped(sls):
+    # binary32 meshes keep the caller's numbering even when asked: equal runs
     mesh = MESHES["grid_ragged"]()
     a = _run(sls, mesh, 25, 0.0, precision=32, numbering="grouped")
     b = _run(sls, mesh, 25, 0.0, precision=32, numbering="given")
