@@ -421,8 +421,7 @@ class ResultPrint:
 
     def __call__(self, xy: np.ndarray) -> int:
         v = np.ascontiguousarray(xy).view(np.uint64).ravel()
-        with np.errstate(over="ignore"):
-            return int(np.sum(v * self.w[:v.size], dtype=np.uint64))
+        return int(np.dot(v, self.w[:v.size]))  # one pass, wrapping uint64 arithmetic
 
 
 def serve_stream(args, world: int, rank: int):
