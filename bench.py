@@ -502,19 +502,25 @@ def run_serve(args):
     left = [clients]
     left_lock = threading.Lock()
     busy_retries = [0] * clients
+    host_s = {"submit": [0.0] * clients, "get_mesh": [0.0] * clients, "try_wait": [0.0] * pollers,
+              "fingerprint": [0.0] * pollers}
     if world > 1:
         dist.barrier()
     t_start = time.perf_counter()
 
     def submitter(c):
         for local, k in enumerate(range(c, len(reqs), clients)):
+            t0 = time.perf_counter()
             m = pres[c].get(local)
+            host_s["get_mesh"][c] += time.perf_counter() - t0
             delay = arrivals[k] - (time.perf_counter() - t_start)
             if delay > 0:
                 time.sleep(delay)
             while True:
                 try:
+                    t0 = time.perf_counter()
                     jid = srv.submit(m.xy, m.tri, m.boundary, max_iter=caps[k], tol=TOL)
+                    host_s["submit"][c] += time.perf_counter() - t0
                     break
                 except sls.SlsError as e:
                     if e.code != 6:  # SLS_ERR_BUSY: the queue is full, try again shortly
@@ -523,9 +529,14 @@ def run_serve(args):
                     time.sleep(0.0005)
             p = k % pollers
             with locks[p]:
-                pending[p][jid] = (k, np.empty((sizes[k], 2), np.float64))
+                pending[p][jid] = k
         with left_lock:
             left[0] -= 1
+
+    # each poller receives its results into one scratch buffer of the largest
+    # size (touched once here, so no result pays for fresh pages): the results
+    # are only fingerprinted, not kept
+    scratch = [np.zeros((max(sizes), 2), np.float64) for _ in range(pollers)]
 
     def poller(p):
         while True:
@@ -538,12 +549,17 @@ def run_serve(args):
                     with locks[p]:
                         if not pending[p]:
                             return
-            for jid, (k, buf) in items:
+            for jid, k in items:
+                buf = scratch[p][:sizes[k]]
+                t0 = time.perf_counter()
                 info = srv.try_wait(jid, buf)
+                host_s["try_wait"][p] += time.perf_counter() - t0
                 if info is None:
                     continue
                 done_t[k] = time.perf_counter() - t_start
+                t0 = time.perf_counter()
                 prints[k] = fp(buf)
+                host_s["fingerprint"][p] += time.perf_counter() - t0
                 iters[k] = info["iterations"]
                 with locks[p]:
                     del pending[p][jid]
@@ -569,6 +585,7 @@ def run_serve(args):
     if world > 1:
         dist.barrier()
     fifo_lat, busy, same = [], 0.0, True
+    out = scratch[0]  # the results land in a buffer touched before, as the served ones do
     t_start = time.perf_counter()
     for k in range(len(reqs)):
         m = pre.get(k)
@@ -578,7 +595,7 @@ def run_serve(args):
         t0 = time.perf_counter()
         with sls.Mesh(m.xy, m.tri, m.boundary, numbering=args.lib_numbering) as g:
             inf = g.smooth(caps[k], TOL)
-            xy = g.coords()
+            xy = g.coords(out=out[:sizes[k]])
         busy += time.perf_counter() - t0
         fifo_lat.append(1e3 * (time.perf_counter() - t_start - arrivals[k]))
         same = same and fp(xy) == prints[k] and inf["iterations"] == iters[k]
@@ -615,7 +632,8 @@ def run_serve(args):
                       "req_per_s": len(reqs) * world / (wall_ms * 1e-3),
                       "node_updates_per_s_busy_rank0": st["node_updates_per_s"],
                       "server_p50_ms_from_submit": st["p50_ms"], "server_p99_ms_from_submit": st["p99_ms"],
-                      "busy_retries_rank0": busy_retries[0]},
+                      "busy_retries_rank0": busy_retries[0],
+                      "host_thread_s_rank0": {k: round(sum(v), 3) for k, v in host_s.items()}},
            "fifo": {"p50_ms": f50, "p99_ms": f99, "node_updates_per_s": fifo, "wall_s": fifo_ms * 1e-3,
                     "node_updates_per_s_busy": fifo_busy, "busy_s": busy_ms * 1e-3},
            "speedup_vs_fifo": served / fifo,
