@@ -25,6 +25,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -706,24 +707,36 @@ sls_status sls_submit(sls_server *S, const double *xy, int64_t n, const int32_t 
     // what the job holds at least once built: coordinates and offsets alone
     const size_t least = 2 * sizeof(double) * 2 * (size_t)n + sizeof(uint32_t) * (size_t)(n + 1);
     if (least > S->budget) return fail(SLS_ERR_REJECTED, "job larger than the server's memory budget");
-    auto J = std::make_shared<ServerJob>();
-    J->t_submit = Clock::now();
-    // copy the inputs before taking the server's lock, which every thread needs
-    J->xy.assign(xy, xy + 2 * n);
-    J->tri.assign(tri, tri + 3 * m);
-    if (boundary) {
-        J->boundary.assign(boundary, boundary + n);
-        J->has_boundary = true;
+    const auto t_submit = Clock::now();
+    {
+        // take the queue place first, so that a full queue costs no copy
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->max_queue > 0 && S->holding >= S->max_queue)
+            return fail(SLS_ERR_BUSY, "server queue is full");
+        S->holding += 1;
     }
+    std::shared_ptr<ServerJob> J;
+    try {
+        // copy the inputs outside the server's lock, which every thread needs
+        J = std::make_shared<ServerJob>();
+        J->xy.assign(xy, xy + 2 * n);
+        J->tri.assign(tri, tri + 3 * m);
+        if (boundary) {
+            J->boundary.assign(boundary, boundary + n);
+            J->has_boundary = true;
+        }
+    } catch (const std::bad_alloc &) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->holding -= 1;
+        return fail(SLS_ERR_OOM, "host allocation failed");
+    }
+    J->t_submit = t_submit;
     J->n = n;
     J->m = m;
     J->max_iter = max_iter;
     J->tol = tol_rel;
     J->reserved = admission_bound(n, m, max_iter);
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->max_queue > 0 && S->holding >= S->max_queue)
-        return fail(SLS_ERR_BUSY, "server queue is full");
-    S->holding += 1;
     J->id = S->next_id++;
     S->jobs[J->id] = J;
     S->queued.push_back(J);
