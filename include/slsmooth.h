@@ -304,7 +304,9 @@ sls_status sls_batch_destroy(sls_batch *batch);
  * server's throughput is held by its builds, which the renumbering lengthens
  * (measured: 2.5% more node-updates per second of round time, fewer
  * requests per second).  Jobs take their device memory from the library's
- * pool (see sls_trim_memory). */
+ * pool (see sls_trim_memory); their inputs and results wait in page-locked
+ * host memory, of which the server keeps up to 4 GiB for reuse until it is
+ * destroyed. */
 sls_status sls_server_create(size_t hbm_budget, int32_t max_queue, const sls_options *opt,
                              sls_server **out);
 

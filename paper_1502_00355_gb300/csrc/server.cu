@@ -22,7 +22,9 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
+#include <cstdlib>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -47,13 +49,88 @@ constexpr int64_t kServerChunk = 0;
 
 enum JobState { kQueued, kBuilding, kActive, kRetiring, kDone, kFailed };
 
+// Page-locked host blocks for the jobs' inputs and results, kept for reuse.
+// A copy between the device and page-locked memory is one DMA that needs no
+// CPU staging, so builds upload and results come back without a builder or
+// the retire thread copying through the driver's bounce buffers; pinning
+// memory is slow, so freed blocks are cached (up to kPinnedKeep bytes) for
+// later jobs of a similar size.  Blocks come in powers of two from 64 KiB.
+// When the driver refuses to pin more, plain host memory serves instead.
+class PinnedCache {
+public:
+    static constexpr size_t kPinnedKeep = size_t(4) << 30;
+
+    struct Block {
+        void *p = nullptr;
+        size_t cap = 0;
+        bool pinned = false;
+    };
+
+    Block get(size_t bytes)
+    {
+        size_t cap = size_t(1) << 16;
+        while (cap < bytes) cap <<= 1;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            auto it = free_.find(cap);
+            if (it != free_.end()) {
+                Block b{it->second, cap, true};
+                free_.erase(it);
+                kept_ -= cap;
+                return b;
+            }
+        }
+        Block b{nullptr, cap, false};
+        if (cudaMallocHost(&b.p, cap) == cudaSuccess) {
+            b.pinned = true;
+        } else {
+            cudaGetLastError();
+            b.p = std::malloc(cap);
+            if (!b.p) throw std::bad_alloc();
+        }
+        return b;
+    }
+
+    void put(Block &b)
+    {
+        if (!b.p) return;
+        if (b.pinned) {
+            std::unique_lock<std::mutex> lk(mu_);
+            if (kept_ + b.cap <= kPinnedKeep) {
+                free_.emplace(b.cap, b.p);
+                kept_ += b.cap;
+                b = Block{};
+                return;
+            }
+            lk.unlock();
+            cudaFreeHost(b.p);
+        } else {
+            std::free(b.p);
+        }
+        b = Block{};
+    }
+
+    ~PinnedCache()
+    {
+        for (auto &kv : free_) cudaFreeHost(kv.second);
+    }
+
+private:
+    std::mutex mu_;
+    std::multimap<size_t, void *> free_;
+    size_t kept_ = 0;
+};
+
 struct ServerJob {
     uint64_t id = 0;
-    // inputs, released once the job is on the device
-    std::vector<double> xy;
-    std::vector<int32_t> tri;
-    std::vector<uint8_t> boundary;
-    bool has_boundary = false;
+    // inputs (one page-locked block: coordinates, triangles, boundary flags),
+    // released once the job is on the device
+    std::shared_ptr<PinnedCache> cache;  // where the host blocks go back to
+    PinnedCache::Block in;
+    const double *xy = nullptr;
+    const int32_t *tri = nullptr;
+    const uint8_t *boundary = nullptr;  // NULL: derived from open edges
+    cudaEvent_t in_done = nullptr;      // the uploads from `in` are complete
     int64_t n = 0, m = 0;
     double diag = 0.0;
     int32_t max_iter = 0;
@@ -75,15 +152,35 @@ struct ServerJob {
     JobState state = kQueued;
     sls_status status = SLS_OK;
     std::string error;
-    std::vector<double> result;
+    PinnedCache::Block result;  // 2n doubles once done
     sls_info info{};
     Clock::time_point t_submit, t_done;
+
+    void release_inputs()
+    {
+        if (in_done) {
+            cudaEventSynchronize(in_done);
+            cudaEventDestroy(in_done);
+            in_done = nullptr;
+        }
+        if (cache) cache->put(in);
+        xy = nullptr;
+        tri = nullptr;
+        boundary = nullptr;
+    }
+
+    ~ServerJob()
+    {
+        release_inputs();
+        if (cache) cache->put(result);
+    }
 };
 
 }  // namespace
 
 struct sls_server {
     sls_options opt{};
+    std::shared_ptr<PinnedCache> pinned = std::make_shared<PinnedCache>();
     size_t budget = 0, used = 0;
     int32_t max_queue = 0;
     int device = 0;
@@ -190,17 +287,18 @@ sls_status build_job(ServerJob &J, bool group, cudaStream_t s, size_t *footprint
         return cleanup(fail(SLS_ERR_OOM, "device allocation failed"));
     }
     if (e != cudaSuccess) return cuda_err(e, "device allocation");
-    e = cudaMemcpyAsync(J.d_xy[0], J.xy.data(), cbytes, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(J.d_xy[0], J.xy, cbytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_tri, J.tri.data(), sizeof(int32_t) * 3 * (size_t)m, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(d_tri, J.tri, sizeof(int32_t) * 3 * (size_t)m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&J.in_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(J.in_done, s);
     if (e != cudaSuccess) return cuda_err(e, "upload");
     DeviceAdjacency da;
-    sls_status st = build_device_adjacency(n, m, J.d_xy[0], d_tri, J.has_boundary ? J.boundary.data() : nullptr,
-                                           true, s, da);
+    sls_status st = build_device_adjacency(n, m, J.d_xy[0], d_tri, J.boundary, true, s, da);
     if (st == SLS_ERR_NOT_FOUND) {
         // a node in more triangles than the device build handles: host build
         HostMesh hm;
-        st = build_host_mesh(J.xy.data(), n, J.tri.data(), m, J.has_boundary ? J.boundary.data() : nullptr, hm, 1);
+        st = build_host_mesh(J.xy, n, J.tri, m, J.boundary, hm, 1);
         if (st != SLS_OK) return cleanup(st);
         da.adj_words = hm.node_off[n];
         da.n_free = hm.n_free;
@@ -260,13 +358,8 @@ void builder_loop(sls_server *S, cudaStream_t s)
         J->build_stream = s;
         const sls_status st = build_job(*J, S->opt.numbering == 2, s, &fp);
         const std::string err = st == SLS_OK ? std::string() : std::string(sls_last_error());
+        J->release_inputs();  // once its uploads are done; outside the lock
         std::lock_guard<std::mutex> lk(S->mu);
-        J->xy.clear();
-        J->xy.shrink_to_fit();
-        J->tri.clear();
-        J->tri.shrink_to_fit();
-        J->boundary.clear();
-        J->boundary.shrink_to_fit();
         S->holding -= 1;
         if (st == SLS_OK) {
             S->used = S->used - J->reserved + fp;  // the scratch and the bound's slack return
@@ -386,7 +479,16 @@ void retire_loop(sls_server *S)
         for (cudaEvent_t ev : evs) ok = ok && cudaStreamWaitEvent(S->retire_stream, ev, 0) == cudaSuccess;
         for (auto &Jp : batch) {
             ServerJob &J = *Jp;
-            J.result.resize(2 * (size_t)J.n);
+            const size_t rbytes = sizeof(double) * 2 * (size_t)J.n;
+            if (J.result.cap < rbytes) {
+                J.cache->put(J.result);
+                try {
+                    J.result = J.cache->get(rbytes);
+                } catch (const std::bad_alloc &) {
+                    ok = false;
+                    continue;
+                }
+            }
             const double *res = J.d_xy[J.iterations & 1];
             if (J.d_perm) {
                 // back to the caller's numbering, through the idle array
@@ -395,8 +497,8 @@ void retire_loop(sls_server *S)
                                                    S->retire_stream) == cudaSuccess;
                 res = d;
             }
-            ok = ok && cudaMemcpyAsync(J.result.data(), res, sizeof(double) * J.result.size(),
-                                       cudaMemcpyDeviceToHost, S->retire_stream) == cudaSuccess;
+            ok = ok && cudaMemcpyAsync(J.result.p, res, rbytes, cudaMemcpyDeviceToHost, S->retire_stream) ==
+                           cudaSuccess;
         }
         ok = ok && cudaStreamSynchronize(S->retire_stream) == cudaSuccess;  // one wait for the batch
         if (!ok) cudaGetLastError();
@@ -719,11 +821,17 @@ sls_status sls_submit(sls_server *S, const double *xy, int64_t n, const int32_t 
     try {
         // copy the inputs outside the server's lock, which every thread needs
         J = std::make_shared<ServerJob>();
-        J->xy.assign(xy, xy + 2 * n);
-        J->tri.assign(tri, tri + 3 * m);
+        J->cache = S->pinned;
+        const size_t bx = sizeof(double) * 2 * (size_t)n, bt = sizeof(int32_t) * 3 * (size_t)m;
+        J->in = S->pinned->get(bx + bt + (boundary ? (size_t)n : 0));
+        char *base = static_cast<char *>(J->in.p);
+        std::memcpy(base, xy, bx);
+        std::memcpy(base + bx, tri, bt);
+        J->xy = reinterpret_cast<const double *>(base);
+        J->tri = reinterpret_cast<const int32_t *>(base + bx);
         if (boundary) {
-            J->boundary.assign(boundary, boundary + n);
-            J->has_boundary = true;
+            std::memcpy(base + bx + bt, boundary, (size_t)n);
+            J->boundary = reinterpret_cast<const uint8_t *>(base + bx + bt);
         }
     } catch (const std::bad_alloc &) {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -764,7 +872,7 @@ sls_status sls_wait(sls_server *S, uint64_t job, double timeout_s, double *xy_ou
     // the copy of a large result must not hold up the scheduler and the
     // builders: the job is ours alone once it left the table
     lk.unlock();
-    if (xy_out) std::memcpy(xy_out, J->result.data(), sizeof(double) * J->result.size());
+    if (xy_out) std::memcpy(xy_out, J->result.p, sizeof(double) * 2 * (size_t)J->n);
     if (info) *info = J->info;
     return SLS_OK;
 }
