@@ -681,7 +681,7 @@ def main():
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--ref-passes", type=int, default=3)
     ap.add_argument("--cpu-passes", type=int, default=5)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="64: FP64 (the headline); 32: binary32, the paper's precision")
