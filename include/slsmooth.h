@@ -284,11 +284,11 @@ sls_status sls_batch_destroy(sls_batch *batch);
 /* ---- served form: jobs arrive over time (continuous batching) -----------
  * A scheduler thread admits queued jobs in arrival order while a bound on
  * their device footprint (coordinates, adjacency, statistics and the
- * adjacency build's scratch, about 58n + 84m bytes) fits the memory budget;
+ * adjacency build's scratch, about 66n + 84m bytes) fits the memory budget;
  * a job is also admitted when the server holds nothing else.  Builder
  * threads, each with its own stream, upload admitted jobs and build their
- * adjacency on the device (stream-ordered allocations from the device's
- * default memory pool, so the running rounds are never synchronised; a mesh
+ * adjacency on the device (stream-ordered allocations from the library's
+ * memory pool, so the running rounds are never synchronised; a mesh
  * with a node in more than 32 triangles is built on the host).  The
  * scheduler runs every built job's next pass in one launch per round and
  * retires each job at its own iteration cap or tolerance. */
