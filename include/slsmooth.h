@@ -284,7 +284,7 @@ sls_status sls_batch_destroy(sls_batch *batch);
 /* ---- served form: jobs arrive over time (continuous batching) -----------
  * A scheduler thread admits queued jobs in arrival order while a bound on
  * their device footprint (coordinates, adjacency, statistics and the
- * adjacency build's scratch, about 66n + 84m bytes) fits the memory budget;
+ * adjacency build's scratch, about 70n + 84m bytes) fits the memory budget;
  * a job is also admitted when the server holds nothing else.  Builder
  * threads, each with its own stream, upload admitted jobs and build their
  * adjacency on the device (stream-ordered allocations from the library's
