@@ -298,12 +298,10 @@ sls_status sls_batch_destroy(sls_batch *batch);
  * built on the device (the jobs whose inputs the server still holds in host
  * memory) that sls_submit accepts (0 = unlimited); beyond it sls_submit
  * returns SLS_ERR_BUSY.  opt: FP64 Form A with the AoS layout only
- * (SLS_ERR_INVALID otherwise).  With opt's numbering = 2 every job is
- * renumbered as a single mesh is (results in the caller's numbering; 4 bytes
- * per node more while held); 0 and 1 keep the caller's numbering, because the
- * server's throughput is held by its builds, which the renumbering lengthens
- * (measured: 2.5% more node-updates per second of round time, fewer
- * requests per second).  Jobs take their device memory from the library's
+ * (SLS_ERR_INVALID otherwise).  opt's numbering applies to every job as to
+ * a single mesh (by default jobs of 2^20 nodes or more are renumbered;
+ * results in the caller's numbering; 4 bytes per node more while held).
+ * Jobs take their device memory from the library's
  * pool (see sls_trim_memory); their inputs and results wait in page-locked
  * host memory, of which the server keeps up to 4 GiB for reuse until it is
  * destroyed. */

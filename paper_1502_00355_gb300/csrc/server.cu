@@ -356,7 +356,7 @@ void builder_loop(sls_server *S, cudaStream_t s)
         }
         size_t fp = 0;
         J->build_stream = s;
-        const sls_status st = build_job(*J, S->opt.numbering == 2, s, &fp);
+        const sls_status st = build_job(*J, groups_nodes(S->opt, J->n), s, &fp);
         const std::string err = st == SLS_OK ? std::string() : std::string(sls_last_error());
         J->release_inputs();  // once its uploads are done; outside the lock
         std::lock_guard<std::mutex> lk(S->mu);
