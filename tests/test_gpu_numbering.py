@@ -135,3 +135,26 @@ def test_numbering_option_checked(sls):
     with pytest.raises(sls.SlsError) as e:
         sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, numbering=3)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("kernel", ["auto", "fp64"])
+def test_grouped_edge_meshes(sls, kernel):
+    # a node of degree 40 (past the fast path's 16 and the device build's 32
+    # triangles: host build, exact path), the dart whose centre inverts a
+    # triangle, and a lone triangle with nothing free
+    k = 40
+    ang = np.linspace(0, 2 * np.pi, k, endpoint=False)
+    fan = meshgen.Mesh(xy=np.vstack([np.c_[np.cos(ang) * (1 + 0.3 * np.sin(5 * ang)), np.sin(ang)], [[0.05, -0.02]]]),
+                       tri=np.array([[k, j, (j + 1) % k] for j in range(k)], dtype=np.int32),
+                       boundary=(np.arange(k + 1) < k).astype(np.uint8))
+    dart = meshgen.Mesh(xy=np.array([[4.0, 0.0], [-1.0, 1.0], [2.0, 0.0], [-1.0, -1.0], [2.5, 0.0]]),
+                        tri=np.array([[4, 0, 1], [4, 1, 2], [4, 2, 3], [4, 3, 0]], dtype=np.int32),
+                        boundary=np.array([1, 1, 1, 1, 0], np.uint8))
+    one = meshgen.Mesh(xy=np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), tri=np.array([[0, 1, 2]], np.int32),
+                       boundary=np.ones(3, np.uint8))
+    for name, mesh, iters in (("fan-40", fan, 3), ("dart", dart, 2), ("one", one, 4)):
+        xy, info, acc, _ = _run(sls, mesh, iters, 0.0, numbering="grouped", kernel=kernel)
+        rxy, rinfo, racc = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.boundary).smooth(mesh.xy, iters)
+        assert np.array_equal(xy, rxy), name
+        assert np.array_equal(acc, racc), name
+        assert info["accepted_last"] == rinfo["accepted_last"] and info["maxd2_last"] == rinfo["maxd2_last"], name
