@@ -83,3 +83,35 @@ def test_fails_loudly_without_a_gpu(L):
     for host_build in (True, False):
         st, msg = _create(L, xy, [[0, 1, 2]], host_build=host_build)
         assert st == 4 and msg  # SLS_ERR_CUDA with a message: no silent CPU path
+
+
+def _c_layout(struct: str, fields) -> dict:
+    """sizeof and field offsets of a header struct, from a C program built
+    against the header with the system compiler."""
+    import subprocess
+    import tempfile
+    body = "\n".join(f'    printf("{f} %zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src = f"""#include <stddef.h>
+#include <stdio.h>
+#include "slsmooth.h"
+int main(void) {{
+    printf("sizeof %zu\\n", sizeof({struct}));
+{body}
+    return 0;
+}}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+@pytest.mark.parametrize("pystruct, cname", [(sls.Options, "sls_options"), (sls.Info, "sls_info")])
+def test_binding_structs_match_the_header(pystruct, cname):
+    fields = [f for f, _ in pystruct._fields_]
+    lay = _c_layout(cname, fields)
+    assert lay["sizeof"] == C.sizeof(pystruct)
+    for f in fields:
+        assert lay[f] == getattr(pystruct, f).offset, f
