@@ -58,9 +58,12 @@ def _run_split(mesh, world, iters, tol, **options):
 
 @pytest.mark.parametrize("world", [2, 4])
 @pytest.mark.parametrize("layout", ["aos", "soa"])
-def test_subdomains_equal_the_whole_mesh(sls, world, layout):
+@pytest.mark.parametrize("numbering", ["given", "grouped"])
+def test_subdomains_equal_the_whole_mesh(sls, world, layout, numbering):
+    # with numbering = grouped every subdomain is renumbered inside the
+    # library, and the exchange lists (caller's ids) go through its maps
     mesh = meshgen.jittered_grid(300, 200, 0.35, 5, numbering="morton", pull_fraction=0.05, pull_centres=64)
-    xy, info = _run_split(mesh, world, 60, 1e-9, layout=layout)
+    xy, info = _run_split(mesh, world, 60, 1e-9, layout=layout, numbering=numbering)
     with sls.Mesh(mesh.xy, mesh.tri, mesh.boundary, layout=layout) as g:
         ref = g.smooth(60, 1e-9)
         ref_xy = g.coords()
