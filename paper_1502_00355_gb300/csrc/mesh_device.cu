@@ -236,18 +236,12 @@ static void set_l2_window(const sls_mesh *M, const void *base, size_t bytes)
     if (cudaStreamSetAttribute(M->stream, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess) cudaGetLastError();
 }
 
-// One pass (or one colour class of a Form-B sweep) over `nodes` node slots:
-// the grid is the mesh's persistent grid, or fewer blocks when the slots do
-// not fill it (a small colour class would otherwise start blocks that find
-// no tile and still pay their start and their statistics atomics).
-static cudaError_t launch_pass(const sls_mesh *M, const PassArgs &a, int64_t nodes)
+static cudaError_t launch_pass(const sls_mesh *M, const PassArgs &a)
 {
     if (M->opt.l2_window) set_l2_window(M, a.in, (M->f32 ? sizeof(float) : sizeof(double)) * 2 * (size_t)M->n);
-    const int64_t need = (nodes + M->block - 1) / M->block;
-    const int grid = need < (int64_t)M->grid ? (int)std::max<int64_t>(need, 1) : M->grid;
-    if (M->f32) return launch_pass_f32(a, M->opt.layout, M->block, grid, M->stream);
-    return M->screened ? launch_pass_screened(a, M->opt.layout, M->block, grid, M->stream)
-                       : launch_pass_fp64(a, M->opt.layout, M->block, grid, M->stream);
+    if (M->f32) return launch_pass_f32(a, M->opt.layout, M->block, M->grid, M->stream);
+    return M->screened ? launch_pass_screened(a, M->opt.layout, M->block, M->grid, M->stream)
+                       : launch_pass_fp64(a, M->opt.layout, M->block, M->grid, M->stream);
 }
 
 sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &info)
@@ -304,7 +298,7 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
                     a.ranged = 1;
                     a.first = nseg > 0 ? M->colour_off[c] : 0;
                     a.count = nseg > 0 ? M->colour_off[c + 1] - M->colour_off[c] : 0;
-                    SLS_CUDA_TRY(launch_pass(M, a, a.count), "pass kernel");
+                    SLS_CUDA_TRY(launch_pass(M, a), "pass kernel");
                     ++kernels;
                 }
                 continue;
@@ -321,7 +315,7 @@ sls_status mesh_run(sls_mesh *M, int32_t max_iter, double tol_rel, sls_info &inf
                 a.accm = M->accm;
                 a.skip = q > 0 ? 1 : 0;
             }
-            SLS_CUDA_TRY(launch_pass(M, a, M->n), "pass kernel");
+            SLS_CUDA_TRY(launch_pass(M, a), "pass kernel");
             ++kernels;
             if (cb) {
                 SLS_CUDA_TRY(M->f32 ? launch_copy_back_f32(reinterpret_cast<const float *>(M->xy[src ^ 1]),
