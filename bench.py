@@ -680,7 +680,7 @@ def main():
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--ref-passes", type=int, default=3)
-    ap.add_argument("--cpu-passes", type=int, default=5)
+    ap.add_argument("--cpu-passes", type=int, default=80)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
