@@ -44,16 +44,16 @@ PROFILE_FIGURES = {
     "pass_screened": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh",
                   "numbering.cu"],
-        "sha256": "497b818d69c0a2357c211928368e5f3135c8f7e8884067d5b3a7eb2d031cce46",
-        "dram_bytes_per_node": (309189376 + 54080512) / (2048 * 2048),
+        "sha256": "db9df0c964a12160525e9538431b1f0be20dcc278b1dfac8ff092a618a9895ef",
+        "dram_bytes_per_node": (309215744 + 54800128) / (2048 * 2048),
         "fp64_warp_inst_per_32_nodes": (2132648 + 795086 + 157073) / (2048 * 2048 / 32),
         "source": "profiles/pass_screened_grid2048.md (2048x2048 capture, per node)",
     },
     "batch_pass": {
         "files": ["pass_screened.cu", "screen.cuh", "node_exact.cuh", "div_small.cuh", "device.cuh", "batch.cu",
                   "numbering.cu"],
-        "sha256": "22c8dc49084b29f110cba8b7090033e98e5e46231ec496f1a5bc3f129267452c",
-        "dram_per_alg_byte": (1007816192 + 171327488) / 994046024,
+        "sha256": "716f3492b8a2cc0ea034315c6b2a5adf884f3866f6fbc7a78722a5074c3f14d3",
+        "dram_per_alg_byte": (1008215808 + 171628032) / 994046024,
         "source": "profiles/batch_pass_batch256.md (round 0 of a 256-mesh batch, scaled by algorithmic bytes)",
     },
 }
