@@ -358,6 +358,7 @@ void builder_loop(sls_server *S, cudaStream_t s)
         J->build_stream = s;
         const sls_status st = build_job(*J, groups_nodes(S->opt, J->n), s, &fp);
         const std::string err = st == SLS_OK ? std::string() : std::string(sls_last_error());
+        if (st != SLS_OK) cudaStreamSynchronize(s);  // a failed build may leave an upload in flight
         J->release_inputs();  // once its uploads are done; outside the lock
         std::lock_guard<std::mutex> lk(S->mu);
         S->holding -= 1;
