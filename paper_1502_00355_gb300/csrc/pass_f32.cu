@@ -98,7 +98,12 @@ __device__ __forceinline__ float alpha_at(const float *in, int64_t n, const uint
     }
 }
 
-constexpr int kRingMax = 16;  // rings up to this size live in shared memory
+// Rings up to this size live in shared memory (larger ones are read from
+// global memory).  12 slots keep five blocks' buffers within the 132 KB
+// shared-memory carve-out, which leaves the gathers about twice the L1 of
+// 16 slots (2.4% faster on jittered grids; a Delaunay mesh of random points
+// has about 1.4 nodes in 10,000 above 12).
+constexpr int kRingMax = 12;
 
 // One pass over every node (a.order null) or over the listed nodes (one
 // colour class of Form B, in place).  a.in / a.out hold floats.  Each thread
